@@ -1,0 +1,333 @@
+"""ctypes front-end of the FP64 CPU oracle (`gs_oracle.c`).
+
+TEST INFRASTRUCTURE ONLY: imported by the test-suite, by the smoke check and
+by the CPU-baseline leg of the benchmark, never by the product path.  It does
+not import the CUDA package and the CUDA package does not import it.
+
+Each wrapper takes NumPy arrays (any float dtype; converted to float64) and
+returns NumPy arrays.  The paper passages each step follows are cited in the
+C source next to each function.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gs_oracle.c")
+_LIB = os.path.join(_HERE, "libgs_oracle.so")
+
+BAND = 1e-4      # relative band around a threshold inside which FP32 may decide differently
+BAND_T = 2e-3    # same for the transmittance stop test (a product of many FP32 factors)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, no fast-math, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+               "-o", _LIB, _SRC, "-lm"]
+        subprocess.check_call(cmd)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        _declare(_lib)
+    return _lib
+
+
+_dp = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+_ip = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+_lp = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+_u8 = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
+_u32 = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
+_u64 = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
+
+
+def _declare(L):
+    i, l, d = C.c_int, C.c_long, C.c_double
+    L.gso_visibility.restype = l
+    L.gso_visibility.argtypes = [i, _dp, i, _dp, _ip, d, _ip, _lp, l, _u8]
+    L.gso_decode.restype = i
+    L.gso_decode.argtypes = [i, i, i, i, i, _dp, _dp, _dp, _dp, _ip, _dp, i, _dp, _ip, l, _ip,
+                             _lp, d, _dp, _dp, _dp, _dp, _dp, _u8]
+    L.gso_project.restype = i
+    L.gso_project.argtypes = [l, i, i, _lp, _dp, _ip, _dp, _dp, _dp, _dp, d, _dp, _dp, _dp, _dp,
+                              _ip, _ip, _ip, _u8, _ip]
+    L.gso_bin_sort.restype = l
+    L.gso_bin_sort.argtypes = [l, i, i, _lp, _ip, _u32, _ip, l, _u64, _u32, _u32]
+    L.gso_render.restype = i
+    L.gso_render.argtypes = [i, _ip, l, i, _lp, _dp, _dp, _dp, _dp, _u32, _ip, _ip, i, _u32,
+                             _u32, _dp, d, d, _dp, _dp, _ip, C.POINTER(C.c_long), _u8,
+                             C.POINTER(C.c_uint64)]
+    L.gso_l1.restype = d
+    L.gso_l1.argtypes = [i, _ip, _dp, _dp, _dp]
+    L.gso_render_bwd.restype = i
+    L.gso_render_bwd.argtypes = [i, _ip, l, _dp, _dp, _dp, _dp, _u32, _u32, _dp, _dp, _dp,
+                                 _dp, _dp, _dp]
+    L.gso_project_bwd.restype = i
+    L.gso_project_bwd.argtypes = [l, i, i, _lp, _dp, _ip, _dp, _dp, _dp, _ip, _dp, _dp, _dp,
+                                  _dp, _dp]
+    L.gso_decode_bwd.restype = i
+    L.gso_decode_bwd.argtypes = [i, i, i, i, i, _dp, _dp, _dp, _dp, _ip, _dp, i, _dp, _ip, l,
+                                 _ip, _lp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+    L.gso_mlp_size.restype = l
+    L.gso_mlp_size.argtypes = [i, i, i]
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, np.float64))
+
+
+def _i32(a):
+    return np.ascontiguousarray(np.asarray(a, np.int32))
+
+
+def tiles_of(wh):
+    """(TX, TY, tile_base, total tiles) for each view of a 16x16 tiling."""
+    wh = np.asarray(wh, np.int64).reshape(-1, 2)
+    tx = (wh[:, 0] + 15) // 16
+    ty = (wh[:, 1] + 15) // 16
+    n = tx * ty
+    base = np.concatenate([[0], np.cumsum(n)[:-1]])
+    return tx, ty, base, int(n.sum())
+
+
+# --------------------------------------------------------------------------
+@dataclass
+class Decoded:
+    av_anchor: np.ndarray   # [R] int32
+    view_start: np.ndarray  # [V+1] int64 (rows)
+    row_flag: np.ndarray    # [R] uint8
+    k: int
+    mu: np.ndarray = None
+    scale: np.ndarray = None
+    quat: np.ndarray = None
+    opacity: np.ndarray = None
+    colour: np.ndarray = None
+    cand_flag: np.ndarray = None
+
+
+def visibility(xyz, cams, wh, band=BAND):
+    xyz = _f64(xyz); cams = _f64(cams); wh = _i32(wh)
+    N, V = xyz.shape[0], cams.shape[0]
+    cap = N * V
+    av = np.zeros(max(cap, 1), np.int32)
+    vs = np.zeros(V + 1, np.int64)
+    fl = np.zeros(max(cap, 1), np.uint8)
+    r = lib().gso_visibility(N, xyz, V, cams, wh, band, av, vs, cap, fl)
+    assert r >= 0
+    return av[:r].copy(), vs, fl[:r].copy()
+
+
+def decode(scene, band=BAND, rows=None):
+    """Visibility (a0) + decode (a1) of every (view, anchor) row."""
+    s = scene
+    if rows is None:
+        av, vs, rf = visibility(s.xyz, s.cams, s.wh, band)
+    else:
+        av, vs, rf = rows
+    R = av.shape[0]
+    C_ = R * s.k
+    mu = np.zeros((C_, 3)); sc = np.zeros((C_, 3)); q = np.zeros((C_, 4))
+    op = np.zeros(C_); col = np.zeros((C_, 3)); cf = np.zeros(max(C_, 1), np.uint8)
+    lib().gso_decode(s.N, s.F, s.k, s.hidden, s.M, _f64(s.xyz), _f64(s.feat),
+                     _f64(s.log_scaling), _f64(s.offsets), _i32(s.part), _f64(s.mlp),
+                     s.V, _f64(s.cams), _i32(s.wh), R, _i32(av), vs, band, mu, sc, q, op, col, cf)
+    return Decoded(av, vs, rf, s.k, mu, sc, q, op, col, cf[:C_])
+
+
+@dataclass
+class Projected:
+    mean2d: np.ndarray
+    conic: np.ndarray
+    cov2d: np.ndarray
+    depth: np.ndarray
+    rect: np.ndarray      # [C,4] int32 x0,y0,x1,y1
+    tiles: np.ndarray
+    status: np.ndarray
+    flag: np.ndarray
+    fp64_branch: np.ndarray
+
+    @property
+    def depth_bits(self):
+        return self.depth.astype(np.float32).view(np.uint32)
+
+
+def project(mu, scale, quat, opacity, cams, wh, view_start, k=1, band=BAND):
+    C_ = mu.shape[0]
+    V = np.asarray(cams).shape[0]
+    out = Projected(np.zeros((C_, 2)), np.zeros((C_, 3)), np.zeros((C_, 3)), np.zeros(C_),
+                    np.zeros((C_, 4), np.int32), np.zeros(C_, np.int32), np.zeros(C_, np.int32),
+                    np.zeros(C_, np.uint8), np.zeros(C_, np.int32))
+    lib().gso_project(C_, k, V, np.ascontiguousarray(view_start, np.int64), _f64(cams), _i32(wh),
+                      _f64(mu), _f64(scale), _f64(quat), _f64(opacity), band, out.mean2d,
+                      out.conic, out.cov2d, out.depth, out.rect, out.tiles, out.status, out.flag,
+                      out.fp64_branch)
+    return out
+
+
+def bin_sort(depth_bits, rect, wh, view_start, k=1):
+    depth_bits = np.ascontiguousarray(depth_bits, np.uint32)
+    rect = _i32(rect)
+    C_ = depth_bits.shape[0]
+    V = np.asarray(wh).reshape(-1, 2).shape[0]
+    P = int(((rect[:, 2] - rect[:, 0]) * (rect[:, 3] - rect[:, 1])).sum()) if C_ else 0
+    _, _, _, T = tiles_of(wh)
+    keys = np.zeros(max(P, 1), np.uint64)
+    vals = np.zeros(max(P, 1), np.uint32)
+    ranges = np.zeros(2 * T, np.uint32)
+    n = lib().gso_bin_sort(C_, k, V, np.ascontiguousarray(view_start, np.int64), _i32(wh),
+                           depth_bits, rect, P, keys, vals, ranges)
+    assert n == P
+    return keys[:P].copy(), vals[:P].copy(), ranges.reshape(T, 2)
+
+
+@dataclass
+class Rendered:
+    image: np.ndarray      # flat [sum_v 3*H*W], per view planar [3,H,W]
+    T_final: np.ndarray    # flat [sum_v H*W]
+    last: np.ndarray
+    pix_flag: np.ndarray
+    nev: int
+    hash: int
+
+    def view_image(self, wh, v):
+        wh = np.asarray(wh).reshape(-1, 2)
+        base = int(sum(3 * int(w) * int(h) for w, h in wh[:v]))
+        w, h = (int(x) for x in wh[v])
+        return self.image[base:base + 3 * w * h].reshape(3, h, w)
+
+
+def render(wh, view_start, k, mean2d, conic, opacity, colour, depth_bits, rect, status,
+           mode=0, ranges=None, vals=None, bg=(0.0, 0.0, 0.0), band=BAND, band_t=BAND_T):
+    wh = _i32(wh).reshape(-1, 2)
+    V = wh.shape[0]
+    npix = int((wh[:, 0].astype(np.int64) * wh[:, 1]).sum())
+    C_ = np.asarray(opacity).shape[0]
+    if ranges is None:
+        ranges = np.zeros((1, 2), np.uint32)
+        vals = np.zeros(1, np.uint32)
+    image = np.zeros(3 * npix); Tf = np.zeros(npix); last = np.zeros(npix, np.int32)
+    pf = np.zeros(npix, np.uint8)
+    nev = C.c_long(0); h = C.c_uint64(0)
+    lib().gso_render(V, wh, C_, k, np.ascontiguousarray(view_start, np.int64), _f64(mean2d),
+                     _f64(conic), _f64(opacity), _f64(colour),
+                     np.ascontiguousarray(depth_bits, np.uint32), _i32(rect), _i32(status), mode,
+                     np.ascontiguousarray(ranges, np.uint32).reshape(-1),
+                     np.ascontiguousarray(vals, np.uint32), _f64(bg), band, band_t, image, Tf,
+                     last, C.byref(nev), pf, C.byref(h))
+    return Rendered(image, Tf, last, pf, int(nev.value), int(h.value))
+
+
+def l1(wh, image, target):
+    image = _f64(image).reshape(-1); target = _f64(target).reshape(-1)
+    d = np.zeros_like(image)
+    L = lib().gso_l1(np.asarray(wh).reshape(-1, 2).shape[0], _i32(wh), image, target, d)
+    return L, d
+
+
+def render_bwd(wh, mean2d, conic, opacity, colour, ranges, vals, dimage, bg=(0.0, 0.0, 0.0)):
+    wh = _i32(wh).reshape(-1, 2)
+    C_ = np.asarray(opacity).shape[0]
+    dm = np.zeros((C_, 2)); dk = np.zeros((C_, 3)); do = np.zeros(C_); dc = np.zeros((C_, 3))
+    lib().gso_render_bwd(wh.shape[0], wh, C_, _f64(mean2d), _f64(conic), _f64(opacity),
+                         _f64(colour), np.ascontiguousarray(ranges, np.uint32).reshape(-1),
+                         np.ascontiguousarray(vals, np.uint32), _f64(bg), _f64(dimage), dm, dk,
+                         do, dc)
+    return dm, dk, do, dc
+
+
+def project_bwd(mu, scale, quat, status, cams, wh, view_start, dmean2d, dconic, k=1):
+    C_ = mu.shape[0]
+    V = np.asarray(cams).shape[0]
+    dmu = np.zeros((C_, 3)); ds = np.zeros((C_, 3)); dq = np.zeros((C_, 4))
+    lib().gso_project_bwd(C_, k, V, np.ascontiguousarray(view_start, np.int64), _f64(cams),
+                          _i32(wh), _f64(mu), _f64(scale), _f64(quat), _i32(status),
+                          _f64(dmean2d), _f64(dconic), dmu, ds, dq)
+    return dmu, ds, dq
+
+
+def decode_bwd(scene, dec: Decoded, dmu, dscale, dquat, dopacity, dcolour):
+    s = scene
+    N = s.N
+    dxyz = np.zeros((N, 3)); dfeat = np.zeros((N, s.F)); dls = np.zeros((N, 6))
+    doff = np.zeros((N, s.k, 3)); dmlp = np.zeros_like(_f64(s.mlp))
+    lib().gso_decode_bwd(N, s.F, s.k, s.hidden, s.M, _f64(s.xyz), _f64(s.feat),
+                         _f64(s.log_scaling), _f64(s.offsets), _i32(s.part), _f64(s.mlp), s.V,
+                         _f64(s.cams), _i32(s.wh), dec.av_anchor.shape[0], _i32(dec.av_anchor),
+                         dec.view_start, _f64(dmu), _f64(dscale), _f64(dquat), _f64(dopacity),
+                         _f64(dcolour), dxyz, dfeat, dls, doff, dmlp)
+    return dict(xyz=dxyz, feat=dfeat, log_scaling=dls, offsets=doff, mlp=dmlp)
+
+
+def mlp_size(F, k, hidden):
+    return int(lib().gso_mlp_size(F, k, hidden))
+
+
+# --------------------------------------------------------------------------
+# Whole-path helpers (forward and reverse) used by the self-checks and the
+# CPU baseline.
+
+@dataclass
+class Forward:
+    dec: Decoded | None
+    prj: Projected
+    keys: np.ndarray
+    vals: np.ndarray
+    ranges: np.ndarray
+    ren: Rendered
+    colour: np.ndarray
+    opacity: np.ndarray
+    view_start_c: np.ndarray   # candidate offsets per view, in rows
+    k: int
+
+
+def forward_explicit(scene, bg=(0.0, 0.0, 0.0), mode=0):
+    s = scene
+    vs = np.array([0, s.mu.shape[0]], np.int64)
+    prj = project(s.mu, s.scale, s.quat, s.opacity, s.cams, s.wh, vs, 1)
+    keys, vals, ranges = bin_sort(prj.depth_bits, prj.rect, s.wh, vs, 1)
+    ren = render(s.wh, vs, 1, prj.mean2d, prj.conic, s.opacity, s.colour, prj.depth_bits,
+                 prj.rect, prj.status, mode, ranges, vals, bg)
+    return Forward(None, prj, keys, vals, ranges, ren, _f64(s.colour), _f64(s.opacity), vs, 1)
+
+
+def forward_anchor(scene, bg=(0.0, 0.0, 0.0), mode=0):
+    s = scene
+    dec = decode(s)
+    prj = project(dec.mu, dec.scale, dec.quat, dec.opacity, s.cams, s.wh, dec.view_start, s.k)
+    keys, vals, ranges = bin_sort(prj.depth_bits, prj.rect, s.wh, dec.view_start, s.k)
+    ren = render(s.wh, dec.view_start, s.k, prj.mean2d, prj.conic, dec.opacity, dec.colour,
+                 prj.depth_bits, prj.rect, prj.status, mode, ranges, vals, bg)
+    return Forward(dec, prj, keys, vals, ranges, ren, dec.colour, dec.opacity, dec.view_start,
+                   s.k)
+
+
+def targets_flat(scene):
+    return np.concatenate([t.reshape(-1) for t in scene.targets]).astype(np.float64)
+
+
+def loss_and_grads_anchor(scene, bg=(0.0, 0.0, 0.0), dimage=None):
+    """L1 loss of the anchor path and its gradient w.r.t. every anchor
+    parameter and MLP weight (oracle end to end)."""
+    s = scene
+    fw = forward_anchor(s, bg)
+    L, dimg = l1(s.wh, fw.ren.image, targets_flat(s))
+    if dimage is not None:
+        dimg = dimage
+    dm, dk, do, dc = render_bwd(s.wh, fw.prj.mean2d, fw.prj.conic, fw.opacity, fw.colour,
+                                fw.ranges, fw.vals, dimg, bg)
+    dmu, ds, dq = project_bwd(fw.dec.mu, fw.dec.scale, fw.dec.quat, fw.prj.status, s.cams, s.wh,
+                              fw.dec.view_start, dm, dk, s.k)
+    g = decode_bwd(s, fw.dec, dmu, ds, dq, do, dc)
+    return L, g, fw
