@@ -1,0 +1,257 @@
+/*
+ * gs.h -- C ABI of libgs, the CUDA (sm_103a) library for differentiable
+ * rendering of an anchor-grid Gaussian map, forward and backward.
+ *
+ * The mapping iteration of the paper (Sec. III-B "System Overview": the
+ * Gaussian mapper runs refinement against Eq. 3 on keyframes sampled as in
+ * Sec. IV-A) renders its anchor map (Sec. III-A, Scaffold-GS anchors with the
+ * partitioned decoders of Sec. III-D / Eq. 6) with a differentiable tile
+ * rasterizer (Eq. 1) and back-propagates the photometric loss.  The calls
+ * below are the steps of that pass:
+ *
+ *   gs_decode      visible (view, anchor) rows -> k 3D Gaussians per row
+ *   gs_project     3D Gaussians -> 2D splats (EWA conic, depth, tile rect)
+ *   gs_bin_sort    splats -> (tile, depth)-sorted splat ids + tile ranges
+ *   gs_render_fwd  Eq. 1 per 16x16 tile, front to back
+ *   gs_l1_loss     L1 term of Eq. 3 and its gradient
+ *   gs_render_bwd  reverse of Eq. 1 and of the projection
+ *   gs_decode_bwd  reverse of the decoders (Eq. 6, Eq. 2), summed over views
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every pointer inside the structs is a DEVICE pointer unless it says HOST.
+ *   Buffers are caller-owned, contiguous and laid out as documented; the
+ *   library never allocates, frees or synchronises, and every call is
+ *   enqueued on the given CUDA stream (`stream` is a cudaStream_t; NULL is
+ *   the legacy default stream).  Every call is safe to capture in a CUDA
+ *   graph.
+ * - Sizes that depend on data (visible rows, pairs) live in device memory;
+ *   capacities are fixed by the caller.  A kernel that would exceed a
+ *   capacity writes nothing past it, records GS_ERR_CAPACITY and the size it
+ *   needed in the caller's device `gs_status`, and every later call that is
+ *   given the same status word returns early on the device.  Zero the status
+ *   word (cudaMemsetAsync) before a pass and read it after the stream
+ *   synchronises; on GS_ERR_CAPACITY grow the buffers and run the pass again.
+ * - Return value: GS_OK, or a host-detected error (bad argument, launch
+ *   failure) in which case nothing was enqueued or the enqueue failed.
+ * - Views: a HOST array of gs_view (resolution) plus a DEVICE array of
+ *   gs_camera (intrinsics and world->camera pose), V <= GS_MAX_VIEWS.  Pixel
+ *   (u, v) is sampled at integer coordinates.  Views are tiled in 16x16
+ *   tiles; tiles and pixels of all views are numbered view-major (view v's
+ *   tiles start at the sum of the tile counts of views 0..v-1, row-major
+ *   inside a view).  Images are FP32, view-major, each view planar [3][H][W].
+ * - Rows and candidates: decoding emits one row per visible (view, anchor)
+ *   pair, view-major and in anchor order inside a view.  Row r carries k
+ *   candidate Gaussians with ids r*k + i (i < k).  Explicit Gaussians use
+ *   k = 1 and one row per Gaussian.  `view_start[v]` (device, int32[V+1]) is
+ *   the first row of view v and view_start[V] the number of rows.
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GS_OK 0
+#define GS_ERR_INVALID_ARG (-1)
+#define GS_ERR_CAPACITY (-2)
+#define GS_ERR_CUDA (-3)
+#define GS_ERR_TIMEOUT (-4)
+#define GS_ERR_UNSUPPORTED (-5)
+
+#define GS_TILE 16
+#define GS_MAX_VIEWS 64
+
+/* decoder arithmetic */
+#define GS_PREC_FP32 0   /* FP32 SIMT decode */
+#define GS_PREC_BF16 1   /* BF16 tensor-core decode, FP32 accumulation */
+
+/* Intrinsics and world->camera pose (p_cam = R x_world + t, R row-major). */
+typedef struct gs_camera {
+    float fx, fy, cx, cy;
+    float R[9];
+    float t[3];
+} gs_camera; /* 64 bytes */
+
+/* Resolution of one view (HOST). */
+typedef struct gs_view {
+    int32_t width, height;
+} gs_view;
+
+/* Device status word.  code: 0 or a GS_ERR_* recorded on the device;
+ * where: the call that recorded it (1 decode, 2 project, 3 bin_sort,
+ * 4 render_fwd, 5 render_bwd, 6 decode_bwd); needed: the capacity that
+ * would have sufficed (rows for decode, pairs for bin_sort). */
+typedef struct gs_status {
+    int32_t code;
+    int32_t where;
+    int64_t needed;
+} gs_status;
+
+/* Anchor map (Sec. III-A): N anchors with position x_a, feature f_a (F
+ * floats), log-scaling l_a (6 floats: [0:3] scale the offsets, [3:6] bound the
+ * Gaussian scales), k offsets each, and a partition id (Eq. 6), anchors
+ * sorted by partition.  MLP sets: M packed FP32 vectors of
+ * gs_mlp_floats(F, k, hidden) floats each; per partition the heads
+ * (opacity: k outputs, colour: 3k, covariance: 7k) follow each other, each as
+ * W1[hidden][F+4], b1[hidden], W2[dout][hidden], b2[dout], row-major.  The
+ * decoder input is [f_a, (x_a - x_c)/|x_a - x_c|, |x_a - x_c|] (Eq. 2). */
+typedef struct gs_anchors {
+    int32_t N, F, k, hidden, M;
+    const float *xyz;          /* [N][3] */
+    const float *feat;         /* [N][F] */
+    const float *log_scaling;  /* [N][6] */
+    const float *offsets;      /* [N][k][3] */
+    const int32_t *part;       /* [N], non-decreasing, < M */
+    const float *mlp;          /* [M][gs_mlp_floats] */
+} gs_anchors;
+
+/* 3D Gaussians, candidate-indexed (id = row*k + i), capacity cap_rows*k. */
+typedef struct gs_gauss3d {
+    int32_t k;
+    int64_t cap_rows;
+    int32_t *row_anchor;   /* [cap_rows] anchor of each row (NULL for explicit Gaussians) */
+    int32_t *view_start;   /* [V+1] */
+    float *mu;             /* [C][3] */
+    float *scale;          /* [C][3] */
+    float *quat;           /* [C][4] (w, x, y, z), unit */
+    float *opacity;        /* [C]; <= 0 marks a candidate that decoding culled */
+    float *colour;         /* [C][3] */
+} gs_gauss3d;
+
+/* Gradients w.r.t. the 3D Gaussians, same indexing. */
+typedef struct gs_gauss3d_grad {
+    float *dmu, *dscale, *dquat, *dopacity, *dcolour;
+} gs_gauss3d_grad;
+
+/* Projected splats, candidate-indexed.  `rec` holds one 48-byte record per
+ * candidate: float[12] = mean_x, mean_y, conic_a, conic_b, conic_c, opacity,
+ * r, g, b, depth, then two uint32 words x0 | x1 << 16 and y0 | y1 << 16 (the
+ * tile rectangle [x0,x1) x [y0,y1) inside the candidate's view).  `tiles` is
+ * the number of tiles the rectangle covers, 0 for a culled candidate.  The
+ * power of pixel p is -(a dx^2 + c dy^2)/2 - b dx dy with (dx, dy) = mean - p. */
+typedef struct gs_splats {
+    float *rec;       /* [C][12], 16-byte aligned */
+    int32_t *tiles;   /* [C] */
+} gs_splats;
+
+/* Per-splat gradients of the rendering (view space), candidate-indexed:
+ * float[9] = d mean_x, d mean_y, d conic_a, d conic_b, d conic_c, d opacity,
+ * d r, d g, d b. */
+typedef struct gs_splat_grad {
+    float *g;         /* [C][9] */
+} gs_splat_grad;
+
+/* Sorted binning of splats into tiles. */
+typedef struct gs_bins {
+    int64_t cap_pairs;
+    uint32_t *vals;      /* [cap_pairs] splat id of each (tile, splat) pair, sorted */
+    uint64_t *keys;      /* [cap_pairs] or NULL: (global tile << 32) | float bits of depth */
+    uint32_t *ranges;    /* [T_total][2] pair range [start, end) of each tile */
+    uint32_t *n_pairs;   /* [1] number of pairs */
+} gs_bins;
+
+/* Gradients w.r.t. the anchor map (accumulated over all views). */
+typedef struct gs_anchor_grad {
+    float *dxyz, *dfeat, *dlog_scaling, *doffsets; /* like the inputs */
+    float *dmlp;                                    /* [M][gs_mlp_floats] */
+} gs_anchor_grad;
+
+/* --- sizes ------------------------------------------------------------- */
+/* Floats in one packed partition MLP set. */
+int64_t gs_mlp_floats(int32_t F, int32_t k, int32_t hidden);
+/* Total 16x16 tiles / pixels of a view set. */
+int64_t gs_total_tiles(const gs_view *views, int32_t V);
+int64_t gs_total_pixels(const gs_view *views, int32_t V);
+/* Workspace bytes of each call that takes one (0 for the others). */
+size_t gs_decode_workspace(int32_t N, int32_t V, int32_t M, int64_t cap_rows);
+size_t gs_bin_sort_workspace(const gs_view *views, int32_t V, int64_t cap_cand, int64_t cap_pairs);
+size_t gs_decode_bwd_workspace(int32_t N, int32_t V, int32_t M, int64_t cap_rows);
+const char *gs_status_string(int32_t code);
+
+/* --- the pass ---------------------------------------------------------- */
+
+/* Anchor visibility and decoding (Sec. III-A, Eq. 2, Eq. 6).  A row is made
+ * for every (view, anchor) whose centre is in front of z = 0.2 and projects
+ * inside the image grown by 15 % per side.  Each row's partition MLP gives, for
+ * i < k: opacity = tanh(z_o), colour = sigmoid(z_c), scale = exp(l[3:6]) *
+ * sigmoid(z_s), quat = z_q / |z_q|, mu = x_a + offset_i * exp(l[0:3]).
+ * precision: GS_PREC_FP32 or GS_PREC_BF16 (features and weights rounded to
+ * BF16 for the two MLP layers, FP32 accumulation and epilogue).  Capacity:
+ * out->cap_rows rows; overflow -> GS_ERR_CAPACITY with the row count needed.
+ * Workspace: gs_decode_workspace bytes, 256-byte aligned. */
+int gs_decode(const gs_anchors *A, const gs_camera *cams, const gs_view *views, int32_t V,
+              int32_t precision, gs_gauss3d *out, void *ws, size_t ws_bytes, gs_status *status,
+              void *stream);
+
+/* EWA projection of every candidate (3DGS preliminaries, Sec. III-A): p = R mu
+ * + t, culled if opacity <= 0 or p_z <= 0.2; Sigma3 = R_q S^2 R_q^T; Sigma2 =
+ * J R Sigma3 R^T J^T + 0.3 I with x/z, y/z clamped to 1.3x the half field of
+ * view; culled if det <= 0; conic = Sigma2^-1 (FP64 when det < 1e-3 a c);
+ * radius ceil(3 sqrt(lambda_max)), lambda_max = m + sqrt(max(0.1, m^2 - det));
+ * rect x0 = floor((mx - r)/16), x1 = floor((mx + r)/16) + 1 clamped to the
+ * view, same in y; culled if empty.  Reads the row count from
+ * g->view_start[V] on the device; writes cap_rows*k records at most. */
+int gs_project(const gs_gauss3d *g, const gs_camera *cams, const gs_view *views, int32_t V,
+               gs_splats *out, gs_status *status, void *stream);
+
+/* Tile binning and sort: one pair per (covered tile, splat), ordered by
+ * (global tile, float bits of depth, splat id) -- exactly the order of a sort
+ * on the 64-bit key (tile << 32 | depth bits) with ties broken by id.  Also
+ * writes [start, end) per tile (empty tiles [0, 0)).  k and view_start as in
+ * gs_gauss3d.  Capacity: bins->cap_pairs; overflow -> GS_ERR_CAPACITY with the
+ * pair count needed.  Workspace: gs_bin_sort_workspace bytes. */
+int gs_bin_sort(const gs_splats *sp, int32_t k, const int32_t *view_start, int64_t cap_rows,
+                const gs_view *views, int32_t V, gs_bins *bins, void *ws, size_t ws_bytes,
+                gs_status *status, void *stream);
+
+/* Eq. 1 per pixel over its tile's sorted list: T = 1; for each splat,
+ * alpha = min(0.99, o exp(power)), skipped if power > 0 or alpha < 1/255;
+ * stop before a splat whose T(1 - alpha) < 1e-4; C += c alpha T; T *= 1 -
+ * alpha.  image = C + T bg.  bg: HOST float[3].  T_final (float per pixel) and
+ * last (int32 per pixel: 1-based list position of the last composited splat)
+ * are optional outputs (NULL to skip); gs_render_bwd can use them or
+ * recompute them.  n_eval (device int64[1], NULL to skip) receives the number
+ * of (pixel, splat) evaluations. */
+int gs_render_fwd(const gs_splats *sp, const gs_bins *bins, const gs_view *views, int32_t V,
+                  const float *bg, float *image, float *T_final, int32_t *last, int64_t *n_eval,
+                  gs_status *status, void *stream);
+
+/* L = sum over views of mean |C - C_target| (L1 term of Eq. 3), written to
+ * loss (device float[1], overwritten); dL/dC = sign(C - C_target)/(3 H W)
+ * written to d_image (same layout as image). */
+int gs_l1_loss(const float *image, const float *target, const gs_view *views, int32_t V,
+               float *loss, float *d_image, void *stream);
+
+/* Reverse of Eq. 1 and of the projection.  Per pixel, from the back: with
+ * w_i = alpha_i T_i and B_i the colour composited behind splat i (plus
+ * T_final bg), dL/dc_i = w_i g, dL/dalpha_i = g.(c_i T_i - B_i/(1 - alpha_i)),
+ * then through alpha = o exp(power) (no gradient where the 0.99 clamp is
+ * active) to mean and conic; per-splat sums are reduced across each warp
+ * before global atomics.  Then the projection chain rule gives d mu, d scale,
+ * d quat; d opacity, d colour pass through.  T_final/last: the forward's
+ * optional outputs, or NULL to recompute them.  sgrad: per-splat view-space
+ * gradients (workspace-like output, overwritten).  out: overwritten for every
+ * candidate (zeros for culled ones). */
+int gs_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *sp,
+                  const gs_bins *bins, const gs_view *views, int32_t V, const float *bg,
+                  const float *d_image, const float *T_final, const int32_t *last,
+                  gs_splat_grad *sgrad, gs_gauss3d_grad *out, gs_status *status, void *stream);
+
+/* Reverse of gs_decode, summed over views: through the activations (only for
+ * candidates with opacity > 0), both MLP layers (hidden activations
+ * recomputed, not stored) and the view inputs of Eq. 2.  out is overwritten.
+ * precision as in gs_decode.  Workspace: gs_decode_bwd_workspace bytes. */
+int gs_decode_bwd(const gs_anchors *A, const gs_camera *cams, const gs_view *views, int32_t V,
+                  int32_t precision, const gs_gauss3d *g, const gs_gauss3d_grad *dg,
+                  gs_anchor_grad *out, void *ws, size_t ws_bytes, gs_status *status,
+                  void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS_H */

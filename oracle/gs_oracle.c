@@ -273,8 +273,11 @@ static long view_of(long c, int k, int V, const long *view_start)
     return V - 1;
 }
 
+/* The rectangle decisions floor((m +- r)/16) and ceil(3 sqrt(lambda)) depend
+ * on values FP32 knows to a few ulp, so their band is 1/20 of the others. */
 static int near_int_edge(double x, double band)
 {
+    band *= 0.05;
     /* x close to an integer (a floor/ceil decision that FP32 may flip) */
     double f = x - floor(x);
     return f <= band * (fabs(x) + 1.0) || (1.0 - f) <= band * (fabs(x) + 1.0);
@@ -303,7 +306,7 @@ int gso_project(long C, int k, int V, const long *view_start, const double *cams
         if (!(opacity[c] > 0.0)) continue;
         double p[3];
         to_cam(cm, mu + 3 * c, p);
-        fl |= near_rel(p[2], O_NEAR, band);
+        fl |= near_rel(p[2], O_NEAR, band);   /* bit 0: the splat's presence may flip */
         if (!(p[2] > O_NEAR)) { if (flag) flag[c] = (unsigned char)fl; continue; }
         /* Sigma3 = Rq diag(s^2) Rq^T */
         double Rq[9], S3[9];
@@ -350,13 +353,13 @@ int gso_project(long C, int k, int V, const long *view_start, const double *cams
         double lam = mid + sqrt(disc > 0.1 ? disc : 0.1);
         double r3 = 3.0 * sqrt(lam);
         double r = ceil(r3);
-        fl |= near_int_edge(r3, band);
+        fl |= near_int_edge(r3, band) << 1;   /* bit 1: the tile rectangle may flip */
         double mx = cm->fx * p[0] / p[2] + cm->cx;
         double my = cm->fy * p[1] / p[2] + cm->cy;
         mean2d[2 * c] = mx; mean2d[2 * c + 1] = my;
         depth[c] = p[2];
         double ex[4] = {(mx - r) / O_TILE, (mx + r) / O_TILE, (my - r) / O_TILE, (my + r) / O_TILE};
-        for (int i = 0; i < 4; ++i) fl |= near_int_edge(ex[i], band);
+        for (int i = 0; i < 4; ++i) fl |= near_int_edge(ex[i], band) << 1;
         long x0 = (long)floor(ex[0]), x1 = (long)floor(ex[1]) + 1;
         long y0 = (long)floor(ex[2]), y1 = (long)floor(ex[3]) + 1;
         x0 = x0 < 0 ? 0 : (x0 > cm->TX ? cm->TX : x0);

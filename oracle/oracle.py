@@ -155,7 +155,7 @@ class Projected:
     rect: np.ndarray      # [C,4] int32 x0,y0,x1,y1
     tiles: np.ndarray
     status: np.ndarray
-    flag: np.ndarray
+    flag: np.ndarray          # bit 0: presence decision near a threshold; bit 1: tile rectangle
     fp64_branch: np.ndarray
 
     @property

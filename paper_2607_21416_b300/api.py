@@ -1,0 +1,282 @@
+"""Tensor-level binding of libgs: device buffers (PyTorch tensors) in, C-ABI
+calls out.  PyTorch supplies device memory and streams only; every step of the
+rendering path runs in libgs kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+# ---------------------------------------------------------------------------
+class Views:
+    """A batch of keyframes: resolutions (host) and cameras (device)."""
+
+    def __init__(self, cams, wh, device="cuda"):
+        cams = torch.as_tensor(np.asarray(cams, np.float32)).reshape(-1, 16)
+        wh = np.asarray(wh, np.int32).reshape(-1, 2)
+        self.V = int(wh.shape[0])
+        if self.V < 1 or self.V > L.GS_MAX_VIEWS:
+            raise ValueError("1..64 views per batch")
+        self.wh = wh
+        self.cams = cams.to(device).contiguous()
+        self._views = (L.gs_view * self.V)(*[L.gs_view(int(w), int(h)) for w, h in wh])
+        lib = L.load()
+        self.total_tiles = int(lib.gs_total_tiles(self._views, self.V))
+        self.total_pixels = int(lib.gs_total_pixels(self._views, self.V))
+        self.pix_base = np.concatenate([[0], np.cumsum(wh[:, 0].astype(np.int64) * wh[:, 1])])
+
+    @property
+    def ptr(self):
+        return self._views
+
+    def set_cams(self, cams):
+        self.cams.copy_(torch.as_tensor(np.asarray(cams, np.float32)).reshape(-1, 16))
+
+    def image_of(self, flat, v):
+        w, h = (int(x) for x in self.wh[v])
+        b = int(self.pix_base[v]) * 3
+        return flat[b:b + 3 * w * h].view(3, h, w)
+
+
+@dataclass
+class Anchors:
+    xyz: torch.Tensor
+    feat: torch.Tensor
+    log_scaling: torch.Tensor
+    offsets: torch.Tensor
+    part: torch.Tensor
+    mlp: torch.Tensor
+    F: int
+    k: int
+    hidden: int
+    M: int
+
+    @property
+    def N(self):
+        return int(self.xyz.shape[0])
+
+    @staticmethod
+    def from_scene(scene, device="cuda"):
+        t = lambda a, dt=torch.float32: torch.as_tensor(np.ascontiguousarray(a)).to(device, dt).contiguous()
+        return Anchors(t(scene.xyz), t(scene.feat), t(scene.log_scaling), t(scene.offsets),
+                       t(scene.part, torch.int32), t(scene.mlp), scene.F, scene.k, scene.hidden,
+                       scene.M)
+
+    def struct(self):
+        return L.gs_anchors(self.N, self.F, self.k, self.hidden, self.M, self.xyz.data_ptr(),
+                            self.feat.data_ptr(), self.log_scaling.data_ptr(),
+                            self.offsets.data_ptr(), self.part.data_ptr(), self.mlp.data_ptr())
+
+
+@dataclass
+class Gauss3D:
+    k: int
+    cap_rows: int
+    row_anchor: torch.Tensor | None
+    view_start: torch.Tensor
+    mu: torch.Tensor
+    scale: torch.Tensor
+    quat: torch.Tensor
+    opacity: torch.Tensor
+    colour: torch.Tensor
+
+    @staticmethod
+    def alloc(cap_rows, k, V, device="cuda"):
+        C_ = max(cap_rows * k, 1)
+        z = lambda *s: torch.zeros(*s, device=device, dtype=torch.float32)
+        return Gauss3D(k, cap_rows, torch.zeros(max(cap_rows, 1), device=device, dtype=torch.int32),
+                       torch.zeros(V + 1, device=device, dtype=torch.int32), z(C_, 3), z(C_, 3),
+                       z(C_, 4), z(C_), z(C_, 3))
+
+    @staticmethod
+    def explicit(mu, scale, quat, opacity, colour, device="cuda"):
+        t = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.float32)).to(device).contiguous()
+        G = int(np.asarray(mu).shape[0])
+        vs = torch.tensor([0, G], device=device, dtype=torch.int32)
+        return Gauss3D(1, G, None, vs, t(mu), t(scale), t(quat), t(opacity), t(colour))
+
+    def struct(self):
+        return L.gs_gauss3d(self.k, self.cap_rows,
+                            self.row_anchor.data_ptr() if self.row_anchor is not None else None,
+                            self.view_start.data_ptr(), self.mu.data_ptr(), self.scale.data_ptr(),
+                            self.quat.data_ptr(), self.opacity.data_ptr(), self.colour.data_ptr())
+
+
+@dataclass
+class Gauss3DGrad:
+    dmu: torch.Tensor
+    dscale: torch.Tensor
+    dquat: torch.Tensor
+    dopacity: torch.Tensor
+    dcolour: torch.Tensor
+
+    @staticmethod
+    def like(g: Gauss3D):
+        return Gauss3DGrad(torch.empty_like(g.mu), torch.empty_like(g.scale), torch.empty_like(g.quat),
+                           torch.empty_like(g.opacity), torch.empty_like(g.colour))
+
+    def struct(self):
+        return L.gs_gauss3d_grad(self.dmu.data_ptr(), self.dscale.data_ptr(), self.dquat.data_ptr(),
+                                 self.dopacity.data_ptr(), self.dcolour.data_ptr())
+
+
+@dataclass
+class Splats:
+    rec: torch.Tensor     # [C, 12] float32 (48-byte records)
+    tiles: torch.Tensor   # [C] int32
+
+    @staticmethod
+    def alloc(cap_cand, device="cuda"):
+        return Splats(torch.zeros(max(cap_cand, 1), 12, device=device, dtype=torch.float32),
+                      torch.zeros(max(cap_cand, 1), device=device, dtype=torch.int32))
+
+    def struct(self):
+        return L.gs_splats(self.rec.data_ptr(), self.tiles.data_ptr())
+
+
+@dataclass
+class Bins:
+    cap_pairs: int
+    vals: torch.Tensor     # int32 storage of uint32 ids
+    keys: torch.Tensor | None
+    ranges: torch.Tensor   # [T, 2] int32 storage of uint32
+    n_pairs: torch.Tensor  # [1] int32
+
+    @staticmethod
+    def alloc(cap_pairs, total_tiles, device="cuda", keys=False):
+        return Bins(cap_pairs, torch.zeros(max(cap_pairs, 1), device=device, dtype=torch.int32),
+                    torch.zeros(max(cap_pairs, 1), device=device, dtype=torch.int64) if keys else None,
+                    torch.zeros(max(total_tiles, 1), 2, device=device, dtype=torch.int32),
+                    torch.zeros(1, device=device, dtype=torch.int32))
+
+    def struct(self):
+        return L.gs_bins(self.cap_pairs, self.vals.data_ptr(),
+                         self.keys.data_ptr() if self.keys is not None else None,
+                         self.ranges.data_ptr(), self.n_pairs.data_ptr())
+
+
+@dataclass
+class AnchorGrad:
+    dxyz: torch.Tensor
+    dfeat: torch.Tensor
+    dlog_scaling: torch.Tensor
+    doffsets: torch.Tensor
+    dmlp: torch.Tensor
+
+    @staticmethod
+    def like(a: Anchors):
+        return AnchorGrad(torch.empty_like(a.xyz), torch.empty_like(a.feat),
+                          torch.empty_like(a.log_scaling), torch.empty_like(a.offsets),
+                          torch.empty_like(a.mlp))
+
+    def struct(self):
+        return L.gs_anchor_grad(self.dxyz.data_ptr(), self.dfeat.data_ptr(),
+                                self.dlog_scaling.data_ptr(), self.doffsets.data_ptr(),
+                                self.dmlp.data_ptr())
+
+
+def new_status(device="cuda"):
+    return torch.zeros(2, dtype=torch.int64, device=device)
+
+
+def read_status(status):
+    s = status.cpu().numpy()
+    code = int(np.int32(s[0] & 0xFFFFFFFF))
+    where = int(np.int32((s[0] >> 32) & 0xFFFFFFFF))
+    return code, where, int(s[1])
+
+
+def workspace(nbytes, device="cuda"):
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+# ---------------------------------------------------------------- the calls
+def decode(anchors: Anchors, views: Views, out: Gauss3D, ws, status, precision=L.GS_PREC_FP32,
+           stream=None):
+    lib = L.load()
+    a, g = anchors.struct(), out.struct()
+    L.check("gs_decode", lib.gs_decode(C.byref(a), _ptr(views.cams), views.ptr, views.V, precision,
+                                       C.byref(g), _ptr(ws), ws.numel(), _ptr(status),
+                                       _stream(stream)))
+
+
+def decode_workspace(anchors: Anchors, views: Views, cap_rows):
+    return int(L.load().gs_decode_workspace(anchors.N, views.V, anchors.M, cap_rows))
+
+
+def project(g: Gauss3D, views: Views, out: Splats, status, stream=None):
+    lib = L.load()
+    gs, sp = g.struct(), out.struct()
+    L.check("gs_project", lib.gs_project(C.byref(gs), _ptr(views.cams), views.ptr, views.V,
+                                         C.byref(sp), _ptr(status), _stream(stream)))
+
+
+def bin_sort_workspace(views: Views, cap_cand, cap_pairs):
+    return int(L.load().gs_bin_sort_workspace(views.ptr, views.V, cap_cand, cap_pairs))
+
+
+def bin_sort(sp: Splats, g: Gauss3D, views: Views, bins: Bins, ws, status, stream=None):
+    lib = L.load()
+    s, b = sp.struct(), bins.struct()
+    L.check("gs_bin_sort", lib.gs_bin_sort(C.byref(s), g.k, _ptr(g.view_start), g.cap_rows,
+                                           views.ptr, views.V, C.byref(b), _ptr(ws), ws.numel(),
+                                           _ptr(status), _stream(stream)))
+
+
+def _bg(bg):
+    return (C.c_float * 3)(*[float(x) for x in bg])
+
+
+def render_fwd(sp: Splats, bins: Bins, views: Views, bg, image, status, T_final=None, last=None,
+               n_eval=None, stream=None):
+    lib = L.load()
+    s, b = sp.struct(), bins.struct()
+    L.check("gs_render_fwd", lib.gs_render_fwd(C.byref(s), C.byref(b), views.ptr, views.V, _bg(bg),
+                                               _ptr(image), _ptr(T_final), _ptr(last), _ptr(n_eval),
+                                               _ptr(status), _stream(stream)))
+
+
+def l1_loss(image, target, views: Views, loss, d_image, stream=None):
+    lib = L.load()
+    L.check("gs_l1_loss", lib.gs_l1_loss(_ptr(image), _ptr(target), views.ptr, views.V, _ptr(loss),
+                                         _ptr(d_image), _stream(stream)))
+
+
+def render_bwd(g: Gauss3D, sp: Splats, bins: Bins, views: Views, bg, d_image, sgrad, out: Gauss3DGrad,
+               status, T_final=None, last=None, stream=None):
+    lib = L.load()
+    gs_, s, b = g.struct(), sp.struct(), bins.struct()
+    sg = L.gs_splat_grad(sgrad.data_ptr())
+    o = out.struct()
+    L.check("gs_render_bwd", lib.gs_render_bwd(C.byref(gs_), _ptr(views.cams), C.byref(s), C.byref(b),
+                                               views.ptr, views.V, _bg(bg), _ptr(d_image),
+                                               _ptr(T_final), _ptr(last), C.byref(sg), C.byref(o),
+                                               _ptr(status), _stream(stream)))
+
+
+def decode_bwd_workspace(anchors: Anchors, views: Views, cap_rows):
+    return int(L.load().gs_decode_bwd_workspace(anchors.N, views.V, anchors.M, cap_rows))
+
+
+def decode_bwd(anchors: Anchors, views: Views, g: Gauss3D, dg: Gauss3DGrad, out: AnchorGrad, ws,
+               status, precision=L.GS_PREC_FP32, stream=None):
+    lib = L.load()
+    a, gs_, d, o = anchors.struct(), g.struct(), dg.struct(), out.struct()
+    L.check("gs_decode_bwd", lib.gs_decode_bwd(C.byref(a), _ptr(views.cams), views.ptr, views.V,
+                                               precision, C.byref(gs_), C.byref(d), C.byref(o),
+                                               _ptr(ws), ws.numel(), _ptr(status), _stream(stream)))

@@ -1,0 +1,477 @@
+// binsort.cu -- (tile, depth) binning of splats and a stable LSD radix sort.
+//
+// Result order: (global tile, float bits of depth, splat id), i.e. the order
+// of a sort on the 64-bit key (tile << 32 | depth bits) with ties broken by
+// splat id.  It is reached without sorting 64-bit keys:
+//   1. compact the splats that cover a tile (deterministic scan), keeping
+//      candidate-id order;
+//   2. stable radix sort of those splats on their 32-bit depth bits (ties
+//      keep id order);
+//   3. scan the tile counts in depth order and emit one (tile id, splat id)
+//      pair per covered tile;
+//   4. stable radix sort of the pairs on the tile id (only the bits the tile
+//      count needs), which keeps depth-then-id order inside each tile;
+//   5. tile ranges [start, end) and, on request, the 64-bit keys.
+// Every size is read from device memory, so the sequence is graph-capturable.
+#include "gs_internal.cuh"
+
+namespace gs {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;   // 2048 elements
+constexpr int kSortWarps = kSortThreads / 32;
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Tiles [t0, t1) of 2048 elements owned by block b of nb for n elements.
+__device__ __forceinline__ void block_tiles(uint32_t n, int b, int nb, uint32_t *t0, uint32_t *t1)
+{
+    const uint32_t ntiles = (n + kSortTile - 1) / kSortTile;
+    const uint32_t per = (ntiles + nb - 1) / nb;
+    *t0 = min(ntiles, per * (uint32_t)b);
+    *t1 = min(ntiles, per * (uint32_t)(b + 1));
+}
+
+// 256-thread block exclusive scan (returns exclusive prefix, writes total).
+__device__ __forceinline__ uint32_t scan256(uint32_t x, uint32_t *s_warp, uint32_t *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t v = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) s_warp[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < kSortWarps ? s_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < kSortWarps; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < kSortWarps) s_warp[lane] = w;
+    }
+    __syncthreads();
+    uint32_t ex = v - x + (warp > 0 ? s_warp[warp - 1] : 0);
+    *total = s_warp[kSortWarps - 1];
+    __syncthreads();
+    return ex;
+}
+
+// --------------------------------------------------------------- radix sort
+__global__ void __launch_bounds__(kSortThreads) radix_upsweep(const uint32_t *__restrict__ keys,
+                                                              const uint32_t *__restrict__ n_ptr, int shift,
+                                                              uint32_t *__restrict__ hist,
+                                                              const gs_status *st)
+{
+    if (has_error(st)) return;
+    __shared__ uint32_t s_h[kSortWarps][256];
+    for (int i = threadIdx.x; i < kSortWarps * 256; i += kSortThreads) (&s_h[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t n = *n_ptr;
+    uint32_t t0, t1;
+    block_tiles(n, blockIdx.x, gridDim.x, &t0, &t1);
+    const int warp = threadIdx.x >> 5;
+    const uint32_t e0 = t0 * kSortTile, e1 = min(n, t1 * kSortTile);
+    for (uint32_t i = e0 + threadIdx.x; i < e1; i += kSortThreads)
+        atomicAdd(&s_h[warp][(keys[i] >> shift) & 0xffu], 1u);
+    __syncthreads();
+    uint32_t sum = 0;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) sum += s_h[w][threadIdx.x];
+    hist[threadIdx.x * gridDim.x + blockIdx.x] = sum;
+}
+
+// One block per digit: exclusive scan of hist[d][0..nb) in place; totals[d].
+__global__ void __launch_bounds__(1024) radix_scan_rows(uint32_t *__restrict__ hist, int nb,
+                                                        uint32_t *__restrict__ totals, const gs_status *st)
+{
+    if (has_error(st)) return;
+    __shared__ uint32_t s_warp[32];
+    const int d = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = threadIdx.x < nb ? hist[d * nb + threadIdx.x] : 0;
+    uint32_t v = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) s_warp[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = s_warp[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        s_warp[lane] = w;
+    }
+    __syncthreads();
+    uint32_t ex = v - x + (warp > 0 ? s_warp[warp - 1] : 0);
+    if (threadIdx.x < nb) hist[d * nb + threadIdx.x] = ex;
+    if (threadIdx.x == 0) totals[d] = s_warp[31];
+}
+
+__global__ void __launch_bounds__(kSortThreads) radix_downsweep(
+    const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
+    uint32_t *__restrict__ vout, const uint32_t *__restrict__ n_ptr, int shift,
+    const uint32_t *__restrict__ hist, const uint32_t *__restrict__ totals, const gs_status *st)
+{
+    if (has_error(st)) return;
+    __shared__ uint32_t s_keys[kSortTile];
+    __shared__ uint32_t s_vals[kSortTile];
+    __shared__ uint32_t s_wh[kSortWarps][257];
+    __shared__ uint32_t s_goff[256], s_tstart[256], s_tcnt[256];
+    __shared__ uint32_t s_warp[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t n = *n_ptr;
+    uint32_t t0, t1;
+    block_tiles(n, blockIdx.x, gridDim.x, &t0, &t1);
+    {   // global start of each digit for this block
+        uint32_t tot;
+        uint32_t pre = scan256(totals[tid], s_warp, &tot);
+        s_goff[tid] = pre + hist[tid * gridDim.x + blockIdx.x];
+    }
+    for (int i = tid; i < kSortWarps * 257; i += kSortThreads) (&s_wh[0][0])[i] = 0;
+    __syncthreads();
+    const unsigned ltm = lanemask_lt();
+    for (uint32_t t = t0; t < t1; ++t) {
+        const uint32_t tb = t * kSortTile;
+        uint32_t key[kSortItems], val[kSortItems], loc[kSortItems];
+        int dig[kSortItems];
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            const uint32_t i = tb + warp * (32 * kSortItems) + j * 32 + lane;
+            const bool ok = i < n;
+            key[j] = ok ? kin[i] : 0u;
+            val[j] = ok ? vin[i] : 0u;
+            dig[j] = ok ? (int)((key[j] >> shift) & 0xffu) : 256;
+        }
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            const unsigned peers = __match_any_sync(0xffffffffu, dig[j]);
+            const uint32_t rank = __popc(peers & ltm);
+            const uint32_t base = s_wh[warp][dig[j]];
+            __syncwarp();
+            if (rank == 0) s_wh[warp][dig[j]] = base + __popc(peers);
+            __syncwarp();
+            loc[j] = base + rank;
+        }
+        __syncthreads();
+        {   // per digit: prefix over warps, tile count, tile-local start
+            uint32_t run = 0;
+#pragma unroll
+            for (int w = 0; w < kSortWarps; ++w) {
+                const uint32_t c = s_wh[w][tid];
+                s_wh[w][tid] = run;
+                run += c;
+            }
+            s_tcnt[tid] = run;
+            uint32_t tot;
+            s_tstart[tid] = scan256(run, s_warp, &tot);
+        }
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            if (dig[j] < 256) {
+                const uint32_t p = s_tstart[dig[j]] + s_wh[warp][dig[j]] + loc[j];
+                s_keys[p] = key[j];
+                s_vals[p] = val[j];
+            }
+        }
+        __syncthreads();
+        const uint32_t cnt = min((uint32_t)kSortTile, n - tb);
+        for (uint32_t i = tid; i < cnt; i += kSortThreads) {
+            const uint32_t k = s_keys[i];
+            const uint32_t d = (k >> shift) & 0xffu;
+            const uint32_t g = s_goff[d] + (i - s_tstart[d]);
+            kout[g] = k;
+            vout[g] = s_vals[i];
+        }
+        __syncthreads();
+        s_goff[tid] += s_tcnt[tid];
+        for (int i = tid; i < kSortWarps * 257; i += kSortThreads) (&s_wh[0][0])[i] = 0;
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------ compaction / emission
+// Pass A of a two-pass scan over candidates: per-block count of covering splats.
+__global__ void __launch_bounds__(kSortThreads) count_valid_kernel(
+    const int32_t *__restrict__ tiles, const int32_t *__restrict__ view_start, int V, int k,
+    long long cap_cand, uint32_t *__restrict__ block_sums, const gs_status *st)
+{
+    if (has_error(st)) return;
+    const uint32_t C = (uint32_t)min((long long)__ldg(view_start + V) * k, cap_cand);
+    uint32_t t0, t1;
+    block_tiles(C, blockIdx.x, gridDim.x, &t0, &t1);
+    uint32_t n = 0;
+    for (uint32_t i = t0 * kSortTile + threadIdx.x; i < min(C, t1 * kSortTile); i += kSortThreads)
+        n += __ldg(tiles + i) > 0;
+    __shared__ uint32_t s_warp[32];
+    uint32_t tot;
+    scan256(n, s_warp, &tot);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+// Single block: exclusive scan of nb block sums (nb <= 1024); total -> *out_n.
+__global__ void __launch_bounds__(1024) scan_block_sums(uint32_t *__restrict__ sums, int nb,
+                                                        uint32_t *__restrict__ out_n, long long cap,
+                                                        gs_status *st, int where)
+{
+    if (has_error(st)) return;
+    __shared__ unsigned long long s_warp[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long x = threadIdx.x < nb ? sums[threadIdx.x] : 0ull;
+    unsigned long long v = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) s_warp[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long w = s_warp[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        s_warp[lane] = w;
+    }
+    __syncthreads();
+    unsigned long long ex = v - x + (warp > 0 ? s_warp[warp - 1] : 0ull);
+    if (threadIdx.x < nb) sums[threadIdx.x] = (uint32_t)ex;
+    if (threadIdx.x == 0) {
+        unsigned long long total = s_warp[31];
+        if ((long long)total > cap) {
+            set_error(st, GS_ERR_CAPACITY, where);
+            set_needed(st, (long long)total);
+            *out_n = 0;
+        } else {
+            *out_n = (uint32_t)total;
+        }
+    }
+}
+
+// Pass B: write the covering splats' ids and depth keys in id order.
+__global__ void __launch_bounds__(kSortThreads) compact_valid_kernel(
+    const int32_t *__restrict__ tiles, const float4 *__restrict__ rec,
+    const int32_t *__restrict__ view_start, int V, int k, long long cap_cand,
+    const uint32_t *__restrict__ block_off, uint32_t *__restrict__ ids, uint32_t *__restrict__ dkeys,
+    const gs_status *st)
+{
+    if (has_error(st)) return;
+    const uint32_t C = (uint32_t)min((long long)__ldg(view_start + V) * k, cap_cand);
+    uint32_t t0, t1;
+    block_tiles(C, blockIdx.x, gridDim.x, &t0, &t1);
+    __shared__ uint32_t s_warp[32];
+    uint32_t base = block_off[blockIdx.x];
+    for (uint32_t tb = t0 * kSortTile; tb < min(C, t1 * kSortTile); tb += kSortThreads) {
+        const uint32_t i = tb + threadIdx.x;
+        const uint32_t ok = (i < C) && __ldg(tiles + i) > 0;
+        uint32_t tot;
+        const uint32_t off = scan256(ok, s_warp, &tot);
+        if (ok) {
+            ids[base + off] = i;
+            dkeys[base + off] = __float_as_uint(__ldg(&rec[3 * (size_t)i + 2]).y);
+        }
+        base += tot;
+    }
+}
+
+// Pairs: per-block sums of tile counts in depth order.
+__global__ void __launch_bounds__(kSortThreads) count_pairs_kernel(
+    const uint32_t *__restrict__ ids, const uint32_t *__restrict__ n_ptr, const int32_t *__restrict__ tiles,
+    uint32_t *__restrict__ block_sums, const gs_status *st)
+{
+    if (has_error(st)) return;
+    const uint32_t S = *n_ptr;
+    uint32_t t0, t1;
+    block_tiles(S, blockIdx.x, gridDim.x, &t0, &t1);
+    unsigned long long n = 0;
+    for (uint32_t i = t0 * kSortTile + threadIdx.x; i < min(S, t1 * kSortTile); i += kSortThreads)
+        n += (uint32_t)__ldg(tiles + ids[i]);
+    // the per-block total fits 32 bits when the whole total does (checked later)
+    __shared__ uint32_t s_warp[32];
+    uint32_t tot;
+    scan256((uint32_t)n, s_warp, &tot);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+// Emission: every covering splat (in depth order) writes its (tile, id) pairs.
+__global__ void __launch_bounds__(kSortThreads) emit_pairs_kernel(
+    const uint32_t *__restrict__ ids, const uint32_t *__restrict__ n_ptr, const int32_t *__restrict__ tiles,
+    const float4 *__restrict__ rec, const int32_t *__restrict__ view_start, int k,
+    const uint32_t *__restrict__ block_off, uint32_t *__restrict__ tkeys, uint32_t *__restrict__ tvals,
+    ViewTable vt, const gs_status *st)
+{
+    if (has_error(st)) return;
+    const uint32_t S = *n_ptr;
+    uint32_t t0, t1;
+    block_tiles(S, blockIdx.x, gridDim.x, &t0, &t1);
+    __shared__ uint32_t s_warp[32];
+    uint32_t base = block_off[blockIdx.x];
+    for (uint32_t tb = t0 * kSortTile; tb < min(S, t1 * kSortTile); tb += kSortThreads) {
+        const uint32_t i = tb + threadIdx.x;
+        uint32_t id = 0, cnt = 0;
+        if (i < S) {
+            id = ids[i];
+            cnt = (uint32_t)__ldg(tiles + id);
+        }
+        uint32_t tot;
+        uint32_t off = base + scan256(cnt, s_warp, &tot);
+        if (cnt) {
+            const float4 r2 = __ldg(&rec[3 * (size_t)id + 2]);
+            const uint32_t rx = __float_as_uint(r2.z), ry = __float_as_uint(r2.w);
+            const int x0 = rx & 0xffff, x1 = rx >> 16, y0 = ry & 0xffff, y1 = ry >> 16;
+            const int v = view_of_row(view_start, vt.V, (int)(id / (uint32_t)k));
+            const uint32_t tbase = (uint32_t)vt.tile_base[v];
+            const int TXv = vt.TX[v];
+            for (int y = y0; y < y1; ++y)
+                for (int x = x0; x < x1; ++x) {
+                    tkeys[off] = tbase + (uint32_t)(y * TXv + x);
+                    tvals[off] = id;
+                    ++off;
+                }
+        }
+        base += tot;
+    }
+}
+
+__global__ void __launch_bounds__(256) ranges_kernel(const uint32_t *__restrict__ tkeys,
+                                                     const uint32_t *__restrict__ n_ptr,
+                                                     uint32_t *__restrict__ ranges, const gs_status *st)
+{
+    if (has_error(st)) return;
+    const uint32_t P = *n_ptr;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
+        const uint32_t t = tkeys[i];
+        if (i == 0 || tkeys[i - 1] != t) ranges[2 * t] = i;
+        if (i == P - 1 || tkeys[i + 1] != t) ranges[2 * t + 1] = i + 1;
+    }
+}
+
+__global__ void __launch_bounds__(256) keys_kernel(const uint32_t *__restrict__ tkeys,
+                                                   const uint32_t *__restrict__ vals,
+                                                   const uint32_t *__restrict__ n_ptr,
+                                                   const float4 *__restrict__ rec,
+                                                   unsigned long long *__restrict__ keys, const gs_status *st)
+{
+    if (has_error(st)) return;
+    const uint32_t P = *n_ptr;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
+        const uint32_t d = __float_as_uint(__ldg(&rec[3 * (size_t)vals[i] + 2]).y);
+        keys[i] = ((unsigned long long)tkeys[i] << 32) | d;
+    }
+}
+
+// ------------------------------------------------------------------ driver
+struct SortLayout {
+    size_t ids_a, ids_b, dk_a, dk_b, tk_a, tk_b, tv_b, hist, totals, sums, counts, total;
+    int nb;
+};
+
+static int sort_blocks() { return std::min(1024, sm_count() * 2); }
+
+static SortLayout layout(long long cap_cand, long long cap_pairs)
+{
+    SortLayout L;
+    L.nb = sort_blocks();
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes, 256); return at; };
+    L.ids_a = take(sizeof(uint32_t) * std::max<long long>(cap_cand, 1));
+    L.ids_b = take(sizeof(uint32_t) * std::max<long long>(cap_cand, 1));
+    L.dk_a = take(sizeof(uint32_t) * std::max<long long>(cap_cand, 1));
+    L.dk_b = take(sizeof(uint32_t) * std::max<long long>(cap_cand, 1));
+    L.tk_a = take(sizeof(uint32_t) * std::max<long long>(cap_pairs, 1));
+    L.tk_b = take(sizeof(uint32_t) * std::max<long long>(cap_pairs, 1));
+    L.tv_b = take(sizeof(uint32_t) * std::max<long long>(cap_pairs, 1));
+    L.hist = take(sizeof(uint32_t) * 256 * 1024);
+    L.totals = take(sizeof(uint32_t) * 256);
+    L.sums = take(sizeof(uint32_t) * 1024);
+    L.counts = take(sizeof(uint32_t) * 4);
+    L.total = o;
+    return L;
+}
+
+size_t bin_sort_workspace_bytes(const ViewTable &vt, long long cap_cand, long long cap_pairs)
+{
+    (void)vt;
+    return layout(cap_cand, cap_pairs).total;
+}
+
+static void radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, const uint32_t *n_ptr,
+                       int bits, uint32_t *hist, uint32_t *totals, int nb, gs_status *st, cudaStream_t s,
+                       uint32_t **k_out, uint32_t **v_out)
+{
+    for (int shift = 0; shift < bits; shift += 8) {
+        radix_upsweep<<<nb, kSortThreads, 0, s>>>(k0, n_ptr, shift, hist, st);
+        radix_scan_rows<<<256, 1024, 0, s>>>(hist, nb, totals, st);
+        radix_downsweep<<<nb, kSortThreads, 0, s>>>(k0, v0, k1, v1, n_ptr, shift, hist, totals, st);
+        std::swap(k0, k1);
+        std::swap(v0, v1);
+    }
+    *k_out = k0;
+    *v_out = v0;
+}
+
+int launch_bin_sort(const gs_splats *sp, int k, const int32_t *view_start, long long cap_rows,
+                    const ViewTable &vt, gs_bins *bins, void *ws, size_t ws_bytes, gs_status *st,
+                    cudaStream_t s)
+{
+    const long long cap_cand = cap_rows * k;
+    const SortLayout L = layout(cap_cand, bins->cap_pairs);
+    if (ws_bytes < L.total) return GS_ERR_INVALID_ARG;
+    char *w = reinterpret_cast<char *>(ws);
+    uint32_t *ids_a = (uint32_t *)(w + L.ids_a), *ids_b = (uint32_t *)(w + L.ids_b);
+    uint32_t *dk_a = (uint32_t *)(w + L.dk_a), *dk_b = (uint32_t *)(w + L.dk_b);
+    uint32_t *tk_a = (uint32_t *)(w + L.tk_a), *tk_b = (uint32_t *)(w + L.tk_b);
+    uint32_t *tv_b = (uint32_t *)(w + L.tv_b);
+    uint32_t *hist = (uint32_t *)(w + L.hist), *totals = (uint32_t *)(w + L.totals);
+    uint32_t *sums = (uint32_t *)(w + L.sums), *counts = (uint32_t *)(w + L.counts);
+    const float4 *rec = reinterpret_cast<const float4 *>(sp->rec);
+    const int nb = L.nb;
+    uint32_t *n_splats = counts, *n_pairs = bins->n_pairs;
+
+    // 1. compact covering splats
+    count_valid_kernel<<<nb, kSortThreads, 0, s>>>(sp->tiles, view_start, vt.V, k, cap_cand, sums, st);
+    scan_block_sums<<<1, 1024, 0, s>>>(sums, nb, n_splats, cap_cand, st, 3);
+    compact_valid_kernel<<<nb, kSortThreads, 0, s>>>(sp->tiles, rec, view_start, vt.V, k, cap_cand, sums,
+                                                     ids_a, dk_a, st);
+    // 2. depth sort (32 bits)
+    uint32_t *dk_s, *ids_s;
+    radix_sort(dk_a, ids_a, dk_b, ids_b, n_splats, 32, hist, totals, nb, st, s, &dk_s, &ids_s);
+    // 3. pair emission in depth order
+    count_pairs_kernel<<<nb, kSortThreads, 0, s>>>(ids_s, n_splats, sp->tiles, sums, st);
+    scan_block_sums<<<1, 1024, 0, s>>>(sums, nb, n_pairs, bins->cap_pairs, st, 3);
+    int tile_bits = 1;
+    while ((1ll << tile_bits) < (long long)vt.total_tiles) ++tile_bits;
+    const int passes = (tile_bits + 7) / 8;
+    // choose the emission buffers so that the last pass lands in bins->vals
+    uint32_t *ek = tk_a, *ev = (passes % 2 == 0) ? bins->vals : tv_b;
+    uint32_t *ok = tk_b, *ov = (passes % 2 == 0) ? tv_b : bins->vals;
+    emit_pairs_kernel<<<nb, kSortThreads, 0, s>>>(ids_s, n_splats, sp->tiles, rec, view_start, k, sums, ek,
+                                                  ev, vt, st);
+    // 4. stable sort on the tile id
+    uint32_t *tk_s, *tv_s;
+    radix_sort(ek, ev, ok, ov, n_pairs, tile_bits, hist, totals, nb, st, s, &tk_s, &tv_s);
+    // 5. ranges (+ optional 64-bit keys)
+    cudaMemsetAsync(bins->ranges, 0, sizeof(uint32_t) * 2 * (size_t)vt.total_tiles, s);
+    const int g = sm_count() * 8;
+    ranges_kernel<<<g, 256, 0, s>>>(tk_s, n_pairs, bins->ranges, st);
+    if (bins->keys)
+        keys_kernel<<<g, 256, 0, s>>>(tk_s, tv_s, n_pairs, rec, reinterpret_cast<unsigned long long *>(bins->keys), st);
+    return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+}  // namespace gs

@@ -1,0 +1,208 @@
+// gs_api.cu -- extern "C" entry points of libgs: argument checks, view
+// tables and dispatch to the kernels.  Nothing here allocates or syncs.
+#include <cstring>
+
+#include "gs_internal.cuh"
+
+namespace gs {
+
+bool make_view_table(const gs_view *views, int V, ViewTable *vt)
+{
+    if (V < 1 || V > GS_MAX_VIEWS || !views) return false;
+    std::memset(vt, 0, sizeof(*vt));
+    vt->V = V;
+    long long tb = 0, pb = 0;
+    for (int v = 0; v < V; ++v) {
+        const int W = views[v].width, H = views[v].height;
+        if (W <= 0 || H <= 0 || W > 65535 * kTile || H > 65535 * kTile) return false;
+        vt->W[v] = W; vt->H[v] = H;
+        vt->TX[v] = (W + kTile - 1) / kTile;
+        vt->TY[v] = (H + kTile - 1) / kTile;
+        vt->tile_base[v] = (int)tb;
+        vt->pix_base[v] = pb;
+        tb += (long long)vt->TX[v] * vt->TY[v];
+        pb += (long long)W * H;
+        if (tb > (1ll << 30)) return false;
+    }
+    vt->tile_base[V] = (int)tb;
+    vt->pix_base[V] = pb;
+    vt->total_tiles = (int)tb;
+    vt->total_pixels = pb;
+    return true;
+}
+
+int sm_count()
+{
+    static int cache[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!cache[dev]) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        cache[dev] = n > 0 ? n : 1;
+    }
+    return cache[dev];
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+static bool check_anchors(const gs_anchors *A)
+{
+    if (!A || A->N < 0 || A->F < 1 || A->F > 64 || A->k < 1 || A->k > 16 || A->hidden < 1 || A->hidden > 64 ||
+        A->M < 1)
+        return false;
+    if (A->N > 0 && (!A->xyz || !A->feat || !A->log_scaling || !A->offsets || !A->part || !A->mlp)) return false;
+    return true;
+}
+
+static bool check_gauss(const gs_gauss3d *g)
+{
+    return g && g->k >= 1 && g->cap_rows >= 0 && g->view_start && g->mu && g->scale && g->quat && g->opacity &&
+           g->colour && g->cap_rows * (long long)g->k < (1ll << 31);
+}
+
+static int launch_status()
+{
+    return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+extern "C" {
+
+int64_t gs_mlp_floats(int32_t F, int32_t k, int32_t hidden)
+{
+    const int64_t din = F + 4;
+    const int64_t douts[3] = {k, 3 * (int64_t)k, 7 * (int64_t)k};
+    int64_t s = 0;
+    for (int i = 0; i < 3; ++i) s += hidden * din + hidden + douts[i] * hidden + douts[i];
+    return s;
+}
+
+int64_t gs_total_tiles(const gs_view *views, int32_t V)
+{
+    ViewTable vt;
+    return make_view_table(views, V, &vt) ? vt.total_tiles : -1;
+}
+
+int64_t gs_total_pixels(const gs_view *views, int32_t V)
+{
+    ViewTable vt;
+    return make_view_table(views, V, &vt) ? vt.total_pixels : -1;
+}
+
+size_t gs_decode_workspace(int32_t N, int32_t V, int32_t M, int64_t cap_rows)
+{
+    (void)M; (void)cap_rows;
+    return decode_workspace_bytes(N, V);
+}
+
+size_t gs_bin_sort_workspace(const gs_view *views, int32_t V, int64_t cap_cand, int64_t cap_pairs)
+{
+    ViewTable vt;
+    if (!make_view_table(views, V, &vt)) return 0;
+    return bin_sort_workspace_bytes(vt, cap_cand, cap_pairs);
+}
+
+size_t gs_decode_bwd_workspace(int32_t N, int32_t V, int32_t M, int64_t cap_rows)
+{
+    return decode_bwd_workspace_bytes(N, V, M, cap_rows);
+}
+
+const char *gs_status_string(int32_t code)
+{
+    switch (code) {
+    case GS_OK: return "ok";
+    case GS_ERR_INVALID_ARG: return "invalid argument";
+    case GS_ERR_CAPACITY: return "capacity exceeded";
+    case GS_ERR_CUDA: return "CUDA error";
+    case GS_ERR_TIMEOUT: return "bounded wait timed out";
+    case GS_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+    }
+}
+
+int gs_decode(const gs_anchors *A, const gs_camera *cams, const gs_view *views, int32_t V, int32_t precision,
+              gs_gauss3d *out, void *ws, size_t ws_bytes, gs_status *status, void *stream)
+{
+    ViewTable vt;
+    if (!check_anchors(A) || !cams || !status || !check_gauss(out) || !out->row_anchor ||
+        !make_view_table(views, V, &vt) || out->k != A->k)
+        return GS_ERR_INVALID_ARG;
+    if (precision != GS_PREC_FP32 && precision != GS_PREC_BF16) return GS_ERR_INVALID_ARG;
+    if (ws_bytes < decode_workspace_bytes(A->N, V) || (!ws && ws_bytes > 0)) return GS_ERR_INVALID_ARG;
+    return launch_decode(A, cams, vt, precision, out, ws, status, (cudaStream_t)stream);
+}
+
+int gs_project(const gs_gauss3d *g, const gs_camera *cams, const gs_view *views, int32_t V, gs_splats *out,
+               gs_status *status, void *stream)
+{
+    ViewTable vt;
+    if (!check_gauss(g) || !cams || !out || !out->rec || !out->tiles || !status || !make_view_table(views, V, &vt))
+        return GS_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(out->rec) & 15) != 0) return GS_ERR_INVALID_ARG;
+    return launch_project(g, cams, vt, out, status, (cudaStream_t)stream);
+}
+
+int gs_bin_sort(const gs_splats *sp, int32_t k, const int32_t *view_start, int64_t cap_rows, const gs_view *views,
+                int32_t V, gs_bins *bins, void *ws, size_t ws_bytes, gs_status *status, void *stream)
+{
+    ViewTable vt;
+    if (!sp || !sp->rec || !sp->tiles || k < 1 || !view_start || cap_rows < 0 || !bins || !bins->vals ||
+        !bins->ranges || !bins->n_pairs || bins->cap_pairs < 0 || bins->cap_pairs > 0xffffffffll || !status ||
+        !make_view_table(views, V, &vt) || cap_rows * (long long)k >= (1ll << 31))
+        return GS_ERR_INVALID_ARG;
+    if (!ws) return GS_ERR_INVALID_ARG;
+    return launch_bin_sort(sp, k, view_start, cap_rows, vt, bins, ws, ws_bytes, status, (cudaStream_t)stream);
+}
+
+int gs_render_fwd(const gs_splats *sp, const gs_bins *bins, const gs_view *views, int32_t V, const float *bg,
+                  float *image, float *T_final, int32_t *last, int64_t *n_eval, gs_status *status, void *stream)
+{
+    ViewTable vt;
+    if (!sp || !sp->rec || !bins || !bins->vals || !bins->ranges || !bg || !image || !status ||
+        !make_view_table(views, V, &vt) || (T_final == nullptr) != (last == nullptr))
+        return GS_ERR_INVALID_ARG;
+    return launch_render_fwd(sp, bins, vt, bg, image, T_final, last, reinterpret_cast<long long *>(n_eval), status,
+                             (cudaStream_t)stream);
+}
+
+int gs_l1_loss(const float *image, const float *target, const gs_view *views, int32_t V, float *loss,
+               float *d_image, void *stream)
+{
+    ViewTable vt;
+    if (!image || !target || !loss || !d_image || !make_view_table(views, V, &vt)) return GS_ERR_INVALID_ARG;
+    return launch_l1(image, target, vt, loss, d_image, (cudaStream_t)stream);
+}
+
+int gs_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *sp, const gs_bins *bins,
+                  const gs_view *views, int32_t V, const float *bg, const float *d_image, const float *T_final,
+                  const int32_t *last, gs_splat_grad *sgrad, gs_gauss3d_grad *out, gs_status *status,
+                  void *stream)
+{
+    ViewTable vt;
+    if (!check_gauss(g) || !cams || !sp || !sp->rec || !sp->tiles || !bins || !bins->vals || !bins->ranges ||
+        !bg || !d_image || !sgrad || !sgrad->g || !out || !out->dmu || !out->dscale || !out->dquat ||
+        !out->dopacity || !out->dcolour || !status || !make_view_table(views, V, &vt) ||
+        (T_final == nullptr) != (last == nullptr))
+        return GS_ERR_INVALID_ARG;
+    return launch_render_bwd(g, cams, sp, bins, vt, bg, d_image, T_final, last, sgrad, out, status,
+                             (cudaStream_t)stream);
+}
+
+int gs_decode_bwd(const gs_anchors *A, const gs_camera *cams, const gs_view *views, int32_t V, int32_t precision,
+                  const gs_gauss3d *g, const gs_gauss3d_grad *dg, gs_anchor_grad *out, void *ws, size_t ws_bytes,
+                  gs_status *status, void *stream)
+{
+    ViewTable vt;
+    if (!check_anchors(A) || !cams || !check_gauss(g) || !g->row_anchor || !dg || !dg->dmu || !dg->dscale ||
+        !dg->dquat || !dg->dopacity || !dg->dcolour || !out || !out->dxyz || !out->dfeat || !out->dlog_scaling ||
+        !out->doffsets || !out->dmlp || !status || !make_view_table(views, V, &vt) || g->k != A->k)
+        return GS_ERR_INVALID_ARG;
+    if (precision != GS_PREC_FP32 && precision != GS_PREC_BF16) return GS_ERR_INVALID_ARG;
+    if (ws_bytes < decode_bwd_workspace_bytes(A->N, V, A->M, g->cap_rows)) return GS_ERR_INVALID_ARG;
+    return launch_decode_bwd(A, cams, vt, precision, g, dg, out, ws, status, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,52 @@
+// gs_internal.cuh -- argument blocks and launchers shared by the .cu files.
+#pragma once
+
+#include <algorithm>
+
+#include "gs_common.cuh"
+
+namespace gs {
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct DecodeArgs {
+    const float *xyz, *feat, *log_scaling, *offsets, *mlp;
+    const int32_t *part;
+    long long mlp_floats;
+    int F, k, H, M, V;
+    const gs_camera *cams;
+    const int32_t *view_start, *row_anchor;
+    float *mu, *scale, *quat, *opacity, *colour;
+    gs_status *st;
+    long long cap_rows;
+};
+
+size_t decode_workspace_bytes(int N, int V);
+int launch_decode(const gs_anchors *A, const gs_camera *cams, const ViewTable &vt, int precision,
+                  gs_gauss3d *out, void *ws, gs_status *st, cudaStream_t s);
+int launch_decode_bf16(const DecodeArgs &a, cudaStream_t s);
+
+int launch_project(const gs_gauss3d *g, const gs_camera *cams, const ViewTable &vt, gs_splats *out,
+                   gs_status *st, cudaStream_t s);
+
+size_t bin_sort_workspace_bytes(const ViewTable &vt, long long cap_cand, long long cap_pairs);
+int launch_bin_sort(const gs_splats *sp, int k, const int32_t *view_start, long long cap_rows,
+                    const ViewTable &vt, gs_bins *bins, void *ws, size_t ws_bytes, gs_status *st,
+                    cudaStream_t s);
+
+int launch_render_fwd(const gs_splats *sp, const gs_bins *bins, const ViewTable &vt, const float bg[3],
+                      float *image, float *T_final, int32_t *last, long long *n_eval, gs_status *st,
+                      cudaStream_t s);
+int launch_l1(const float *image, const float *target, const ViewTable &vt, float *loss, float *d_image,
+              cudaStream_t s);
+int launch_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *sp,
+                      const gs_bins *bins, const ViewTable &vt, const float bg[3], const float *d_image,
+                      const float *T_final, const int32_t *last, gs_splat_grad *sgrad,
+                      gs_gauss3d_grad *out, gs_status *st, cudaStream_t s);
+
+size_t decode_bwd_workspace_bytes(int N, int V, int M, long long cap_rows);
+int launch_decode_bwd(const gs_anchors *A, const gs_camera *cams, const ViewTable &vt, int precision,
+                      const gs_gauss3d *g, const gs_gauss3d_grad *dg, gs_anchor_grad *out, void *ws,
+                      gs_status *st, cudaStream_t s);
+
+}  // namespace gs

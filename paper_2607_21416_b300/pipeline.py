@@ -1,0 +1,154 @@
+"""One mapping iteration of the rendering path, built from the libgs calls.
+
+`RenderPass` owns capacity-sized device buffers for a keyframe batch and runs
+decode -> project -> bin/sort -> render -> L1 -> render backward -> decode
+backward on one CUDA stream with no host synchronisation in between, so the
+whole sequence can be captured into one CUDA graph.  Capacity overflow is
+detected on the device (status word) and handled by `ensure_capacity`, which
+grows the buffers outside any capture.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from . import api
+
+
+@dataclass
+class PassOutputs:
+    image: torch.Tensor
+    loss: torch.Tensor
+    d_image: torch.Tensor
+
+
+class RenderPass:
+    """Buffers + call sequence for one keyframe batch.
+
+    anchors: api.Anchors or None (explicit Gaussians passed to `set_explicit`).
+    store_state: keep the forward's per-pixel T_final / last contributor for
+    the backward (plain path) or recompute them inside the backward (batched
+    path, less HBM).
+    """
+
+    def __init__(self, views: api.Views, anchors: api.Anchors | None = None, k: int = 1,
+                 cap_rows: int | None = None, cap_pairs: int | None = None,
+                 precision: int = L.GS_PREC_FP32, store_state: bool = True,
+                 bg=(0.0, 0.0, 0.0), device="cuda", keys=False):
+        self.views = views
+        self.anchors = anchors
+        self.k = anchors.k if anchors is not None else k
+        self.precision = precision
+        self.store_state = store_state
+        self.bg = tuple(float(x) for x in bg)
+        self.device = device
+        self.want_keys = keys
+        V = views.V
+        if cap_rows is None:
+            cap_rows = (anchors.N * V) if anchors is not None else 1
+        self.cap_rows = int(cap_rows)
+        self.cap_pairs = int(cap_pairs) if cap_pairs is not None else max(4 * self.cap_rows * self.k, 1024)
+        self.status = api.new_status(device)
+        npix = views.total_pixels
+        self.image = torch.zeros(3 * npix, device=device)
+        self.d_image = torch.zeros(3 * npix, device=device)
+        self.loss = torch.zeros(1, device=device)
+        self.T_final = torch.zeros(npix, device=device) if store_state else None
+        self.last = torch.zeros(npix, device=device, dtype=torch.int32) if store_state else None
+        self.n_eval = torch.zeros(1, device=device, dtype=torch.int64)
+        self._alloc()
+
+    def _alloc(self):
+        dev, V = self.device, self.views.V
+        C_ = self.cap_rows * self.k
+        if self.anchors is not None:
+            self.g = api.Gauss3D.alloc(self.cap_rows, self.k, V, dev)
+            self.dec_ws = api.workspace(api.decode_workspace(self.anchors, self.views, self.cap_rows), dev)
+            self.agrad = api.AnchorGrad.like(self.anchors)
+            self.dbwd_ws = api.workspace(api.decode_bwd_workspace(self.anchors, self.views, self.cap_rows), dev)
+        self.splats = api.Splats.alloc(C_, dev)
+        self.bins = api.Bins.alloc(self.cap_pairs, self.views.total_tiles, dev, keys=self.want_keys)
+        self.sort_ws = api.workspace(api.bin_sort_workspace(self.views, C_, self.cap_pairs), dev)
+        self.sgrad = torch.zeros(max(C_, 1), 9, device=dev)
+        self.ggrad = None
+
+    def set_explicit(self, g: api.Gauss3D):
+        """Use explicit Gaussians (k = 1) instead of decoding anchors."""
+        if g.cap_rows * g.k > self.cap_rows * self.k:
+            self.cap_rows = g.cap_rows
+            self.k = g.k
+            self._alloc()
+        self.g = g
+
+    # ---------------------------------------------------------------- passes
+    def forward(self, count_evals=False, stream=None):
+        self.status.zero_()
+        if self.anchors is not None:
+            api.decode(self.anchors, self.views, self.g, self.dec_ws, self.status, self.precision, stream)
+        api.project(self.g, self.views, self.splats, self.status, stream)
+        api.bin_sort(self.splats, self.g, self.views, self.bins, self.sort_ws, self.status, stream)
+        api.render_fwd(self.splats, self.bins, self.views, self.bg, self.image, self.status,
+                       self.T_final if self.store_state else None,
+                       self.last if self.store_state else None,
+                       self.n_eval if count_evals else None, stream)
+        return self.image
+
+    def loss_l1(self, target, stream=None):
+        api.l1_loss(self.image, target, self.views, self.loss, self.d_image, stream)
+        return self.loss
+
+    def backward(self, d_image=None, stream=None):
+        if self.ggrad is None or self.ggrad.dmu.shape[0] != self.g.mu.shape[0]:
+            self.ggrad = api.Gauss3DGrad.like(self.g)
+        dimg = self.d_image if d_image is None else d_image
+        api.render_bwd(self.g, self.splats, self.bins, self.views, self.bg, dimg, self.sgrad, self.ggrad,
+                       self.status, self.T_final if self.store_state else None,
+                       self.last if self.store_state else None, stream)
+        if self.anchors is not None:
+            api.decode_bwd(self.anchors, self.views, self.g, self.ggrad, self.agrad, self.dbwd_ws,
+                           self.status, self.precision, stream)
+        return self.ggrad
+
+    def step(self, target, stream=None):
+        """forward + L1 + backward (one mapping iteration without the optimizer)."""
+        self.forward(stream=stream)
+        self.loss_l1(target, stream)
+        self.backward(stream=stream)
+        return self.loss
+
+    # ------------------------------------------------------------ capacity
+    def check(self):
+        code, where, needed = api.read_status(self.status)
+        return code, where, needed
+
+    def ensure_capacity(self, target=None, max_tries=4):
+        """Runs one pass and grows the buffers until no capacity error is left
+        (outside of any graph capture).  Returns the final status code."""
+        for _ in range(max_tries):
+            self.forward()
+            if target is not None:
+                self.loss_l1(target)
+                self.backward()
+            torch.cuda.synchronize()
+            code, where, needed = self.check()
+            if code == 0:
+                return 0
+            if code != L.GS_ERR_CAPACITY:
+                raise L.GsError(f"stage {where}", code)
+            if where == 1:
+                self.cap_rows = int(math.ceil(needed * 1.1)) + 16
+                self.cap_pairs = max(self.cap_pairs, 4 * self.cap_rows * self.k)
+            else:
+                self.cap_pairs = int(math.ceil(needed * 1.15)) + 1024
+            self._alloc()
+        return self.check()[0]
+
+    def n_rows(self):
+        return int(self.g.view_start[-1].item())
+
+    def n_pairs(self):
+        return int(self.bins.n_pairs.item())
