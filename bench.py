@@ -1,0 +1,417 @@
+#!/usr/bin/env python
+"""Mapping-iteration benchmark of the anchor-Gaussian rendering path.
+
+Workload (default): the 8-keyframe batch -- 200k anchors on a 1 km synthetic
+driving corridor, 8 keyframes of 1241x376 (fx = fy = 718) at 1 m spacing with
++-2 deg yaw jitter, k = 10 Gaussians per anchor, 2-layer decoders of width 32
+on 32-d features.  One step = one mapping iteration without the optimizer:
+decode -> project -> bin/sort -> composite -> L1 -> composite backward ->
+decode backward over all 8 keyframes.
+
+Arms:
+  default            the batched path: one CUDA graph per iteration (all views
+                     in every launch), per-pixel state recomputed in the
+                     backward.  Also times the plain path (views one at a
+                     time, state stored, no graph) for the speedup.
+  --impl reference   the FP64 CPU oracle on a bounded sample (one keyframe of
+                     the batch), on the host cores.
+
+Prints one JSON line (rank 0).  Timing: CUDA events recorded inside the
+captured graph (external events), L2 flushed (256 MB write) before every
+timed step outside the events, barrier + synchronize around the timed region,
+max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "keyframe_batch_200k_anchors_8x1241x376"
+METRIC = "mapping fwd+bwd Mpix/s (8-keyframe batch)"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    p.add_argument("--no-plain", action="store_true", help="skip timing the plain path")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    p.add_argument("--anchors", type=int, default=200000)
+    p.add_argument("--views", type=int, default=8)
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ ours
+def run_ours(args, rank, world, dist):
+    import torch
+
+    from paper_2607_21416_b300 import _lib as L
+    from paper_2607_21416_b300 import api, pipeline, scenes
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    prec = L.GS_PREC_BF16 if args.precision == "bf16" else L.GS_PREC_FP32
+    scene = scenes.keyframe_batch(seed=rank, n_anchors=args.anchors, n_views=args.views)
+    views = api.Views(scene.cams, scene.wh)
+    anchors = api.Anchors.from_scene(scene)
+    target_host = torch.from_numpy(np.concatenate([t.reshape(-1) for t in scene.targets])).pin_memory()
+    cams_host = torch.from_numpy(np.ascontiguousarray(scene.cams)).pin_memory()
+    target = target_host.to(dev)
+    npix = views.total_pixels
+
+    # ---- batched path: capacity first (outside capture), then one CUDA graph
+    rp = pipeline.RenderPass(views, anchors, cap_rows=int(1.2 * scene.N * 0.6 * views.V),
+                             precision=prec, store_state=False)
+    code = rp.ensure_capacity(target)
+    assert code == 0, f"capacity handling failed ({code})"
+    torch.cuda.synchronize()
+    n_rows, n_pairs = rp.n_rows(), rp.n_pairs()
+    counts = work_counts(rp)      # exact work of one iteration (untimed)
+    stream = torch.cuda.Stream()
+    names = ["decode", "project", "bin_sort", "render_fwd", "l1", "render_bwd", "decode_bwd"]
+    ev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(len(names) + 1)]
+
+    def step_with_events():
+        s = None
+        ev[0].record()
+        rp.status.zero_()
+        api.decode(anchors, views, rp.g, rp.dec_ws, rp.status, prec)
+        ev[1].record()
+        api.project(rp.g, views, rp.splats, rp.status)
+        ev[2].record()
+        api.bin_sort(rp.splats, rp.g, views, rp.bins, rp.sort_ws, rp.status)
+        ev[3].record()
+        api.render_fwd(rp.splats, rp.bins, views, rp.bg, rp.image, rp.status)
+        ev[4].record()
+        api.l1_loss(rp.image, target, views, rp.loss, rp.d_image)
+        ev[5].record()
+        if rp.ggrad is None:
+            rp.ggrad = api.Gauss3DGrad.like(rp.g)
+        api.render_bwd(rp.g, rp.splats, rp.bins, views, rp.bg, rp.d_image, rp.sgrad, rp.ggrad, rp.status)
+        ev[6].record()
+        api.decode_bwd(anchors, views, rp.g, rp.ggrad, rp.agrad, rp.dbwd_ws, rp.status, prec)
+        ev[7].record()
+        return s
+
+    # warm the launch path once eagerly (sets kernel attributes), then capture
+    with torch.cuda.stream(stream):
+        step_with_events()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        step_with_events()
+    torch.cuda.synchronize()
+    launches_before = int(L.load().gs_kernel_launches())
+    with torch.cuda.stream(stream):
+        step_with_events()     # one eager step only to count this library's launches per step
+    torch.cuda.synchronize()
+    launches_per_step = int(L.load().gs_kernel_launches()) - launches_before
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        flush.zero_()
+        graph.replay()
+    torch.cuda.synchronize()
+    code = api.read_status(rp.status)[0]
+    assert code == 0, f"device status {code}"
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    step_ms, stage_ms = [], {n: [] for n in names}
+    for _ in range(args.steps):
+        flush.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        step_ms.append(ev[0].elapsed_time(ev[-1]))
+        for i, n in enumerate(names):
+            stage_ms[n].append(ev[i].elapsed_time(ev[i + 1]))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = float(sum(step_ms))
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    mpix = npix * world * args.steps / (total_ms * 1e-3) / 1e6
+
+    # ---- end to end through the public API with host buffers
+    e2e_ms = []
+    loss_host = torch.zeros(1, pin_memory=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(max(3, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            target.copy_(target_host, non_blocking=True)
+            views.cams.copy_(cams_host, non_blocking=True)
+            graph.replay()
+            loss_host.copy_(rp.loss, non_blocking=True)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e_mpix = npix * world / (statistics.mean(e2e_ms) * 1e-3) / 1e6
+
+    # ---- plain FP32 path: views one at a time, state stored, eager launches
+    plain = None
+    if not args.no_plain:
+        passes = []
+        for v in range(views.V):
+            vv = api.Views(scene.cams[v:v + 1], scene.wh[v:v + 1])
+            p = pipeline.RenderPass(vv, anchors, cap_rows=int(1.2 * scene.N * 0.6), store_state=True)
+            tv = target[int(views.pix_base[v]) * 3:int(views.pix_base[v + 1]) * 3]
+            assert p.ensure_capacity(tv) == 0
+            passes.append((p, tv))
+        pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        pms = []
+        for it in range(args.warmup + max(3, args.steps // 2)):
+            flush.zero_()
+            torch.cuda.synchronize()
+            pe0.record()
+            for p, tv in passes:
+                p.step(tv)
+            pe1.record()
+            torch.cuda.synchronize()
+            if it >= args.warmup:
+                pms.append(pe0.elapsed_time(pe1))
+        plain = {"ms_per_step": statistics.mean(pms),
+                 "value": npix / (statistics.mean(pms) * 1e-3) / 1e6, "unit": "Mpix/s",
+                 "path": "FP32 decode, views looped, per-pixel state stored, eager launches"}
+        del passes
+
+    stages = {n: statistics.mean(v) for n, v in stage_ms.items()}
+    dom = max(("render_fwd", "render_bwd", "bin_sort", "decode", "decode_bwd"), key=lambda n: stages[n])
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = json.load(open(pk))
+    roof = roofline(dom, stages[dom], counts, n_pairs, n_rows, rp, scene, peaks)
+    return dict(value=mpix, ms_per_step=ms_per_step, stages=stages, clocks=clk, e2e_ms=e2e_ms,
+                e2e_mpix=e2e_mpix, plain=plain, roofline=roof, n_rows=n_rows, n_pairs=n_pairs,
+                counts=counts, launches=launches_per_step, npix=npix,
+                h2d=int(target_host.numel() * 4 + cams_host.numel() * 4), d2h=4)
+
+
+# FP32 operations of the method per (pixel, splat) evaluation, counted from
+# Eq. 1 and its reverse (one exp counted as one op):
+#   every examined pair: offset (2) + power (6) + exp (1) + alpha (2) = 11
+#   every composited pair, forward: T' (2) + weight and colour (4)     =  6
+#   every composited pair, reverse: T (2) + colour/alpha grads (14) +
+#                                  opacity/mean/conic grads (13)      = 29
+OPS_EXAMINED = 11
+OPS_COMPOSITED_FWD = 6
+OPS_COMPOSITED_BWD = 29
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 148, 128, 2032.0
+
+
+def roofline(dom, ms, counts, n_pairs, n_rows, rp, scene, peaks):
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    alu_peak = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12   # T FP32 lane ops/s (nominal)
+    ex, comp, rev = counts["examined"], counts["composited"], counts["reverse_examined"]
+    if dom == "render_fwd":
+        ops = ex * OPS_EXAMINED + comp * OPS_COMPOSITED_FWD
+        a = ops / (ms * 1e-3) / 1e12
+        return {"kernel": "render_fwd_kernel", "bound": "alu", "achieved": a, "peak": alu_peak,
+                "unit": "T FP32 ops/s", "frac": a / alu_peak, "traffic": None,
+                "work_per_launch": f"{ex} examined + {comp} composited pixel-splat pairs"}
+    if dom == "render_bwd":
+        ops = (ex * OPS_EXAMINED + comp * OPS_COMPOSITED_FWD          # recomputed forward
+               + rev * OPS_EXAMINED + comp * OPS_COMPOSITED_BWD)      # reverse traversal
+        a = ops / (ms * 1e-3) / 1e12
+        return {"kernel": "render_bwd_kernel (+project_bwd_kernel, same call)", "bound": "alu",
+                "achieved": a, "peak": alu_peak, "unit": "T FP32 ops/s", "frac": a / alu_peak,
+                "traffic": None,
+                "work_per_launch": f"{ex} examined + {rev} reverse-examined + {comp} composited pairs"}
+    if dom == "bin_sort":
+        S = n_rows * scene.k
+        byts = S * 4 * 2 + n_pairs * 8 * 2 + n_pairs * 4
+        a = byts / (ms * 1e-3) / 1e9
+        return {"kernel": "bin_sort", "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s",
+                "frac": a / hbm, "traffic": None, "work_per_launch": f"{n_pairs} pairs"}
+    flops = n_rows * 13952 * (1 if dom == "decode" else 2)
+    a = flops / (ms * 1e-3) / 1e12
+    pk = peaks.get("bf16_tflops_sustained", 1400.0)
+    return {"kernel": dom, "bound": "tensor", "achieved": a, "peak": pk, "unit": "TFLOP/s",
+            "frac": a / pk, "traffic": None, "work_per_launch": f"{n_rows} anchor-view rows"}
+
+
+def work_counts(rp):
+    """Exact pixel-splat counts of one forward (untimed): pairs examined,
+    pairs composited, and the reverse pass's examined pairs (sum of the last
+    composited list position over pixels)."""
+    import torch
+
+    from paper_2607_21416_b300 import api
+    T = torch.zeros(rp.views.total_pixels, device="cuda")
+    last = torch.zeros(rp.views.total_pixels, device="cuda", dtype=torch.int32)
+    api.render_fwd(rp.splats, rp.bins, rp.views, rp.bg, rp.image, rp.status, T, last, rp.n_eval)
+    torch.cuda.synchronize()
+    return {"examined": int(rp.n_eval[0].item()), "composited": int(rp.n_eval[1].item()),
+            "reverse_examined": int(last.to(torch.int64).sum().item())}
+
+
+# -------------------------------------------------------------- CPU oracle
+def cpu_oracle_sample(n_anchors=200000, n_views=8, seed=0, crop=None):
+    """The FP64 oracle (as it stands) on one keyframe of the batch: decode,
+    project, sort, composite, L1 and the full reverse pass.  `crop` = (i, n)
+    renders only the i-th of n vertical strips of the keyframe (a camera with
+    the principal point shifted and a narrower width).  Returns (Mpix/s,
+    seconds, pixels)."""
+    from oracle import oracle as O
+    from paper_2607_21416_b300 import scenes
+    s = scenes.keyframe_batch(seed=seed, n_anchors=n_anchors, n_views=n_views)
+    s.cams, s.wh, s.targets = s.cams[:1].copy(), s.wh[:1].copy(), s.targets[:1]
+    if crop is not None:
+        i, n = crop
+        W = int(s.wh[0, 0])
+        x0, x1 = W * i // n, W * (i + 1) // n
+        s.cams[0, 2] -= x0
+        s.wh[0, 0] = x1 - x0
+        s.targets = [s.targets[0][:, :, x0:x1].copy()]
+    t0 = time.perf_counter()
+    O.loss_and_grads_anchor(s)
+    dt = time.perf_counter() - t0
+    npix = int(s.wh[0, 0]) * int(s.wh[0, 1])
+    return npix / dt / 1e6, dt, npix
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        pix, secs = 0, 0.0
+        for i in range(args.warmup + args.steps):
+            v, dt, npix = cpu_oracle_sample(args.anchors, args.views, crop=(i % 8, 8))
+            if i >= args.warmup:
+                pix += npix
+                secs += dt
+        value = pix / secs / 1e6
+        sample = ("per step one of 8 vertical strips (155x376) of keyframe 0 of the 8-keyframe batch, "
+                  "cycled; all 200k anchors; forward + L1 + reverse pass; single-threaded FP64 oracle")
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mpix/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": secs / max(args.steps, 1) * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "sample": sample},
+                "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+                                 "sample": sample},
+                "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+        dist = tdist
+    else:
+        torch.cuda.set_device(0)
+    r = run_ours(args, rank, world, dist)
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        v, dt, npix = cpu_oracle_sample(args.anchors, args.views)
+        cpu = {"value": v, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+               "sample": f"one 1241x376 keyframe of the batch, all anchors, forward + L1 + reverse, "
+                         f"single-threaded FP64 ({dt:.1f} s)"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": r["value"], "unit": "Mpix/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if args.precision == "fp32" else "bf16-decode/f32",
+                "data": "synthetic (seeded driving-corridor scene; no dataset)",
+                "config": {"workload": WORKLOAD, "anchors": args.anchors, "keyframes": args.views,
+                           "resolution": "1241x376", "k": 10, "feature_dim": 32, "hidden": 32,
+                           "path": "batched, one CUDA graph per iteration, state recomputed",
+                           "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) before each step"},
+                "e2e": {"value": r["e2e_mpix"], "unit": "Mpix/s", "h2d_bytes_per_step": r["h2d"],
+                        "d2h_bytes_per_step": r["d2h"]},
+                "gpu_launches": r["launches"] * args.steps,
+                "roofline": r["roofline"], "cpu_baseline": cpu, "clocks": r["clocks"],
+                "stages_ms": r["stages"], "plain_path": r["plain"],
+                "speedup_vs_plain": (r["value"] / r["plain"]["value"]) if r["plain"] else None,
+                "counts": dict(rows=r["n_rows"], pairs=r["n_pairs"], pixels=r["npix"], **r["counts"])}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -135,6 +135,7 @@ typedef struct gs_gauss3d_grad {
  * the number of tiles the rectangle covers, 0 for a culled candidate.  The
  * power of pixel p is -(a dx^2 + c dy^2)/2 - b dx dy with (dx, dy) = mean - p. */
 typedef struct gs_splats {
+    int64_t cap;      /* capacity C in records */
     float *rec;       /* [C][12], 16-byte aligned */
     int32_t *tiles;   /* [C] */
 } gs_splats;
@@ -172,6 +173,9 @@ size_t gs_decode_workspace(int32_t N, int32_t V, int32_t M, int64_t cap_rows);
 size_t gs_bin_sort_workspace(const gs_view *views, int32_t V, int64_t cap_cand, int64_t cap_pairs);
 size_t gs_decode_bwd_workspace(int32_t N, int32_t V, int32_t M, int64_t cap_rows);
 const char *gs_status_string(int32_t code);
+/* Number of kernels this library has enqueued since it was loaded (host
+ * counter, all devices and threads); a diagnostic for launch accounting. */
+uint64_t gs_kernel_launches(void);
 
 /* --- the pass ---------------------------------------------------------- */
 
@@ -215,8 +219,9 @@ int gs_bin_sort(const gs_splats *sp, int32_t k, const int32_t *view_start, int64
  * alpha.  image = C + T bg.  bg: HOST float[3].  T_final (float per pixel) and
  * last (int32 per pixel: 1-based list position of the last composited splat)
  * are optional outputs (NULL to skip); gs_render_bwd can use them or
- * recompute them.  n_eval (device int64[1], NULL to skip) receives the number
- * of (pixel, splat) evaluations. */
+ * recompute them.  n_eval (device int64[2], NULL to skip) receives the number
+ * of (pixel, splat) pairs examined and the number composited (a counting
+ * variant of the kernel runs when it is given). */
 int gs_render_fwd(const gs_splats *sp, const gs_bins *bins, const gs_view *views, int32_t V,
                   const float *bg, float *image, float *T_final, int32_t *last, int64_t *n_eval,
                   gs_status *status, void *stream);

@@ -146,7 +146,7 @@ class Splats:
                       torch.zeros(max(cap_cand, 1), device=device, dtype=torch.int32))
 
     def struct(self):
-        return L.gs_splats(self.rec.data_ptr(), self.tiles.data_ptr())
+        return L.gs_splats(int(self.rec.shape[0]), self.rec.data_ptr(), self.tiles.data_ptr())
 
 
 @dataclass

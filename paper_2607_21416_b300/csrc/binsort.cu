@@ -73,8 +73,8 @@ __global__ void __launch_bounds__(kSortThreads) radix_upsweep(const uint32_t *__
                                                               const gs_status *st)
 {
     if (has_error(st)) return;
-    __shared__ uint32_t s_h[kSortWarps][256];
-    for (int i = threadIdx.x; i < kSortWarps * 256; i += kSortThreads) (&s_h[0][0])[i] = 0;
+    __shared__ uint32_t s_h[kSortWarps * 256];   // per-warp histograms, flat
+    for (int i = threadIdx.x; i < kSortWarps * 256; i += kSortThreads) s_h[i] = 0;
     __syncthreads();
     const uint32_t n = *n_ptr;
     uint32_t t0, t1;
@@ -82,11 +82,11 @@ __global__ void __launch_bounds__(kSortThreads) radix_upsweep(const uint32_t *__
     const int warp = threadIdx.x >> 5;
     const uint32_t e0 = t0 * kSortTile, e1 = min(n, t1 * kSortTile);
     for (uint32_t i = e0 + threadIdx.x; i < e1; i += kSortThreads)
-        atomicAdd(&s_h[warp][(keys[i] >> shift) & 0xffu], 1u);
+        atomicAdd(&s_h[warp * 256 + ((keys[i] >> shift) & 0xffu)], 1u);
     __syncthreads();
     uint32_t sum = 0;
 #pragma unroll
-    for (int w = 0; w < kSortWarps; ++w) sum += s_h[w][threadIdx.x];
+    for (int w = 0; w < kSortWarps; ++w) sum += s_h[w * 256 + threadIdx.x];
     hist[threadIdx.x * gridDim.x + blockIdx.x] = sum;
 }
 
@@ -129,7 +129,9 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep(
     if (has_error(st)) return;
     __shared__ uint32_t s_keys[kSortTile];
     __shared__ uint32_t s_vals[kSortTile];
-    __shared__ uint32_t s_wh[kSortWarps][257];
+    // per-warp digit counts (then per-warp exclusive prefixes), flat
+    // [warp][257]; column 256 collects the out-of-range lanes of a ragged tile
+    __shared__ uint32_t s_wh[kSortWarps * 257];
     __shared__ uint32_t s_goff[256], s_tstart[256], s_tcnt[256];
     __shared__ uint32_t s_warp[32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -141,7 +143,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep(
         uint32_t pre = scan256(totals[tid], s_warp, &tot);
         s_goff[tid] = pre + hist[tid * gridDim.x + blockIdx.x];
     }
-    for (int i = tid; i < kSortWarps * 257; i += kSortThreads) (&s_wh[0][0])[i] = 0;
+    for (int i = tid; i < kSortWarps * 257; i += kSortThreads) s_wh[i] = 0;
     __syncthreads();
     const unsigned ltm = lanemask_lt();
     for (uint32_t t = t0; t < t1; ++t) {
@@ -156,33 +158,40 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep(
             val[j] = ok ? vin[i] : 0u;
             dig[j] = ok ? (int)((key[j] >> shift) & 0xffu) : 256;
         }
+        // Stable in-warp ranking, round by round: the lowest lane of each
+        // digit group adds the group size to the warp's counter (shared-memory
+        // atomic, returning the old count) and hands the old count to its peers.
+        // Each leader needs its atomic's result before the shuffle, so the rounds
+        // are ordered by data dependence.
 #pragma unroll
         for (int j = 0; j < kSortItems; ++j) {
             const unsigned peers = __match_any_sync(0xffffffffu, dig[j]);
+            const int leader = __ffs(peers) - 1;
             const uint32_t rank = __popc(peers & ltm);
-            const uint32_t base = s_wh[warp][dig[j]];
-            __syncwarp();
-            if (rank == 0) s_wh[warp][dig[j]] = base + __popc(peers);
-            __syncwarp();
-            loc[j] = base + rank;
+            uint32_t old = 0;
+            if (rank == 0) old = atomicAdd(&s_wh[warp * 257 + dig[j]], (uint32_t)__popc(peers));
+            old = __shfl_sync(0xffffffffu, old, leader);
+            loc[j] = old + rank;
         }
         __syncthreads();
         {   // per digit: prefix over warps, tile count, tile-local start
             uint32_t run = 0;
 #pragma unroll
             for (int w = 0; w < kSortWarps; ++w) {
-                const uint32_t c = s_wh[w][tid];
-                s_wh[w][tid] = run;
+                const uint32_t c = s_wh[w * 257 + tid];
+                s_wh[w * 257 + tid] = run;
                 run += c;
             }
             s_tcnt[tid] = run;
             uint32_t tot;
             s_tstart[tid] = scan256(run, s_warp, &tot);
         }
+        __syncthreads();   // s_tstart is written after the scan's last barrier
 #pragma unroll
         for (int j = 0; j < kSortItems; ++j) {
             if (dig[j] < 256) {
-                const uint32_t p = s_tstart[dig[j]] + s_wh[warp][dig[j]] + loc[j];
+                const uint32_t p = s_tstart[dig[j]] + s_wh[warp * 257 + dig[j]] + loc[j];
+                if (!idx_ok(st, p, kSortTile, 33)) continue;
                 s_keys[p] = key[j];
                 s_vals[p] = val[j];
             }
@@ -193,12 +202,13 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep(
             const uint32_t k = s_keys[i];
             const uint32_t d = (k >> shift) & 0xffu;
             const uint32_t g = s_goff[d] + (i - s_tstart[d]);
+            if (!idx_ok(st, g, n, 32)) continue;
             kout[g] = k;
             vout[g] = s_vals[i];
         }
         __syncthreads();
         s_goff[tid] += s_tcnt[tid];
-        for (int i = tid; i < kSortWarps * 257; i += kSortThreads) (&s_wh[0][0])[i] = 0;
+        for (int i = tid; i < kSortWarps * 257; i += kSortThreads) s_wh[i] = 0;
         __syncthreads();
     }
 }
@@ -281,7 +291,7 @@ __global__ void __launch_bounds__(kSortThreads) compact_valid_kernel(
         const uint32_t ok = (i < C) && __ldg(tiles + i) > 0;
         uint32_t tot;
         const uint32_t off = scan256(ok, s_warp, &tot);
-        if (ok) {
+        if (ok && idx_ok(st, (long long)base + off, C, 31)) {
             ids[base + off] = i;
             dkeys[base + off] = __float_as_uint(__ldg(&rec[3 * (size_t)i + 2]).y);
         }
@@ -292,7 +302,7 @@ __global__ void __launch_bounds__(kSortThreads) compact_valid_kernel(
 // Pairs: per-block sums of tile counts in depth order.
 __global__ void __launch_bounds__(kSortThreads) count_pairs_kernel(
     const uint32_t *__restrict__ ids, const uint32_t *__restrict__ n_ptr, const int32_t *__restrict__ tiles,
-    uint32_t *__restrict__ block_sums, const gs_status *st)
+    uint32_t *__restrict__ block_sums, long long cap_cand, const gs_status *st)
 {
     if (has_error(st)) return;
     const uint32_t S = *n_ptr;
@@ -300,7 +310,7 @@ __global__ void __launch_bounds__(kSortThreads) count_pairs_kernel(
     block_tiles(S, blockIdx.x, gridDim.x, &t0, &t1);
     unsigned long long n = 0;
     for (uint32_t i = t0 * kSortTile + threadIdx.x; i < min(S, t1 * kSortTile); i += kSortThreads)
-        n += (uint32_t)__ldg(tiles + ids[i]);
+        if (idx_ok(st, ids[i], cap_cand, 34)) n += (uint32_t)__ldg(tiles + ids[i]);
     // the per-block total fits 32 bits when the whole total does (checked later)
     __shared__ uint32_t s_warp[32];
     uint32_t tot;
@@ -313,7 +323,7 @@ __global__ void __launch_bounds__(kSortThreads) emit_pairs_kernel(
     const uint32_t *__restrict__ ids, const uint32_t *__restrict__ n_ptr, const int32_t *__restrict__ tiles,
     const float4 *__restrict__ rec, const int32_t *__restrict__ view_start, int k,
     const uint32_t *__restrict__ block_off, uint32_t *__restrict__ tkeys, uint32_t *__restrict__ tvals,
-    ViewTable vt, const gs_status *st)
+    ViewTable vt, long long cap_cand, long long cap_pairs, const gs_status *st)
 {
     if (has_error(st)) return;
     const uint32_t S = *n_ptr;
@@ -326,7 +336,7 @@ __global__ void __launch_bounds__(kSortThreads) emit_pairs_kernel(
         uint32_t id = 0, cnt = 0;
         if (i < S) {
             id = ids[i];
-            cnt = (uint32_t)__ldg(tiles + id);
+            if (idx_ok(st, id, cap_cand, 35)) cnt = (uint32_t)__ldg(tiles + id);
         }
         uint32_t tot;
         uint32_t off = base + scan256(cnt, s_warp, &tot);
@@ -337,12 +347,18 @@ __global__ void __launch_bounds__(kSortThreads) emit_pairs_kernel(
             const int v = view_of_row(view_start, vt.V, (int)(id / (uint32_t)k));
             const uint32_t tbase = (uint32_t)vt.tile_base[v];
             const int TXv = vt.TX[v];
-            for (int y = y0; y < y1; ++y)
-                for (int x = x0; x < x1; ++x) {
-                    tkeys[off] = tbase + (uint32_t)(y * TXv + x);
-                    tvals[off] = id;
-                    ++off;
-                }
+            if ((long long)(x1 - x0) * (y1 - y0) != (long long)cnt || x1 > TXv || y1 > vt.TY[v]) {
+                idx_ok(st, (long long)id, -1, 36);
+                cnt = 0;
+            }
+            if (cnt && !idx_ok(st, (long long)off + cnt - 1, cap_pairs, 37)) cnt = 0;
+            if (cnt)
+                for (int y = y0; y < y1; ++y)
+                    for (int x = x0; x < x1; ++x) {
+                        tkeys[off] = tbase + (uint32_t)(y * TXv + x);
+                        tvals[off] = id;
+                        ++off;
+                    }
         }
         base += tot;
     }
@@ -350,12 +366,14 @@ __global__ void __launch_bounds__(kSortThreads) emit_pairs_kernel(
 
 __global__ void __launch_bounds__(256) ranges_kernel(const uint32_t *__restrict__ tkeys,
                                                      const uint32_t *__restrict__ n_ptr,
-                                                     uint32_t *__restrict__ ranges, const gs_status *st)
+                                                     uint32_t *__restrict__ ranges, int total_tiles,
+                                                     const gs_status *st)
 {
     if (has_error(st)) return;
     const uint32_t P = *n_ptr;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
         const uint32_t t = tkeys[i];
+        if (!idx_ok(st, t, total_tiles, 38)) continue;
         if (i == 0 || tkeys[i - 1] != t) ranges[2 * t] = i;
         if (i == P - 1 || tkeys[i + 1] != t) ranges[2 * t + 1] = i + 1;
     }
@@ -420,6 +438,7 @@ static void radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, c
         radix_downsweep<<<nb, kSortThreads, 0, s>>>(k0, v0, k1, v1, n_ptr, shift, hist, totals, st);
         std::swap(k0, k1);
         std::swap(v0, v1);
+        count_launches(3);
     }
     *k_out = k0;
     *v_out = v0;
@@ -448,11 +467,12 @@ int launch_bin_sort(const gs_splats *sp, int k, const int32_t *view_start, long 
     scan_block_sums<<<1, 1024, 0, s>>>(sums, nb, n_splats, cap_cand, st, 3);
     compact_valid_kernel<<<nb, kSortThreads, 0, s>>>(sp->tiles, rec, view_start, vt.V, k, cap_cand, sums,
                                                      ids_a, dk_a, st);
+    count_launches(3);
     // 2. depth sort (32 bits)
     uint32_t *dk_s, *ids_s;
     radix_sort(dk_a, ids_a, dk_b, ids_b, n_splats, 32, hist, totals, nb, st, s, &dk_s, &ids_s);
     // 3. pair emission in depth order
-    count_pairs_kernel<<<nb, kSortThreads, 0, s>>>(ids_s, n_splats, sp->tiles, sums, st);
+    count_pairs_kernel<<<nb, kSortThreads, 0, s>>>(ids_s, n_splats, sp->tiles, sums, cap_cand, st);
     scan_block_sums<<<1, 1024, 0, s>>>(sums, nb, n_pairs, bins->cap_pairs, st, 3);
     int tile_bits = 1;
     while ((1ll << tile_bits) < (long long)vt.total_tiles) ++tile_bits;
@@ -461,16 +481,20 @@ int launch_bin_sort(const gs_splats *sp, int k, const int32_t *view_start, long 
     uint32_t *ek = tk_a, *ev = (passes % 2 == 0) ? bins->vals : tv_b;
     uint32_t *ok = tk_b, *ov = (passes % 2 == 0) ? tv_b : bins->vals;
     emit_pairs_kernel<<<nb, kSortThreads, 0, s>>>(ids_s, n_splats, sp->tiles, rec, view_start, k, sums, ek,
-                                                  ev, vt, st);
+                                                  ev, vt, cap_cand, bins->cap_pairs, st);
+    count_launches(3);
     // 4. stable sort on the tile id
     uint32_t *tk_s, *tv_s;
     radix_sort(ek, ev, ok, ov, n_pairs, tile_bits, hist, totals, nb, st, s, &tk_s, &tv_s);
     // 5. ranges (+ optional 64-bit keys)
     cudaMemsetAsync(bins->ranges, 0, sizeof(uint32_t) * 2 * (size_t)vt.total_tiles, s);
     const int g = sm_count() * 8;
-    ranges_kernel<<<g, 256, 0, s>>>(tk_s, n_pairs, bins->ranges, st);
-    if (bins->keys)
+    ranges_kernel<<<g, 256, 0, s>>>(tk_s, n_pairs, bins->ranges, vt.total_tiles, st);
+    count_launches(1);
+    if (bins->keys) {
         keys_kernel<<<g, 256, 0, s>>>(tk_s, tv_s, n_pairs, rec, reinterpret_cast<unsigned long long *>(bins->keys), st);
+        count_launches(1);
+    }
     return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 

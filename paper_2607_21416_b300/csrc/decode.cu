@@ -17,14 +17,20 @@ constexpr int kVisThreads = 256;
 constexpr int kVisItems = 8;
 constexpr int kVisChunk = kVisThreads * kVisItems;
 
+// Explicit fmaf / __fmul_rn / __fdiv_rn so the counting and the writing
+// kernels take bit-identical decisions.
+__device__ __forceinline__ float dot3_rn(const float *r, float x, float y, float z, float t)
+{
+    return fmaf(r[2], z, fmaf(r[1], y, fmaf(r[0], x, t)));
+}
 __device__ __forceinline__ bool anchor_visible(const Cam &c, int W, int H, float x, float y, float z)
 {
-    float pz = c.R[6] * x + c.R[7] * y + c.R[8] * z + c.t[2];
+    const float pz = dot3_rn(c.R + 6, x, y, z, c.t[2]);
     if (!(pz > kNear)) return false;
-    float px = c.R[0] * x + c.R[1] * y + c.R[2] * z + c.t[0];
-    float py = c.R[3] * x + c.R[4] * y + c.R[5] * z + c.t[1];
-    float u = c.fx * px / pz + c.cx;
-    float v = c.fy * py / pz + c.cy;
+    const float px = dot3_rn(c.R, x, y, z, c.t[0]);
+    const float py = dot3_rn(c.R + 3, x, y, z, c.t[1]);
+    const float u = fmaf(c.fx, __fdiv_rn(px, pz), c.cx);
+    const float v = fmaf(c.fy, __fdiv_rn(py, pz), c.cy);
     return u >= -kMargin * W && u < (1.0f + kMargin) * W && v >= -kMargin * H &&
            v < (1.0f + kMargin) * H;
 }
@@ -234,8 +240,11 @@ __global__ void __launch_bounds__(128) decode_fp32_kernel(DecodeArgs a)
         float xc[3];
         cam_centre(c, xc);
         const int an = __ldg(a.row_anchor + r);
+        if (!idx_ok(a.st, an, a.N, 11)) continue;
+        const int pm = __ldg(a.part + an);
+        if (!idx_ok(a.st, pm, a.M, 12)) continue;
         HeadPtr hp[3];
-        head_ptrs(a.mlp + (size_t)__ldg(a.part + an) * msz, a.F, a.k, a.H, hp);
+        head_ptrs(a.mlp + (size_t)pm * msz, a.F, a.k, a.H, hp);
         float d[3], delta;
         build_input(a.feat, a.xyz, an, a.F, xc, s_u, nt, d, &delta);
         const size_t c0 = (size_t)r * a.k;
@@ -291,13 +300,14 @@ int launch_decode(const gs_anchors *A, const gs_camera *cams, const ViewTable &v
         vis_scan_kernel<<<1, 1024, 0, s>>>(counts, nchunks * V, nchunks, V, out->view_start, out->cap_rows, st);
         vis_write_kernel<<<dim3(nchunks, V), kVisThreads, 0, s>>>(A->xyz, N, cams, vt, counts, nchunks,
                                                                  out->row_anchor, out->cap_rows, st);
+        count_launches(3);
     } else {
         cudaMemsetAsync(out->view_start, 0, sizeof(int32_t) * (V + 1), s);
     }
     DecodeArgs a;
     a.xyz = A->xyz; a.feat = A->feat; a.log_scaling = A->log_scaling; a.offsets = A->offsets;
     a.part = A->part; a.mlp = A->mlp; a.mlp_floats = gs_mlp_floats(A->F, A->k, A->hidden);
-    a.F = A->F; a.k = A->k; a.H = A->hidden; a.M = A->M; a.V = V;
+    a.N = N; a.F = A->F; a.k = A->k; a.H = A->hidden; a.M = A->M; a.V = V;
     a.cams = cams; a.view_start = out->view_start; a.row_anchor = out->row_anchor;
     a.mu = out->mu; a.scale = out->scale; a.quat = out->quat; a.opacity = out->opacity;
     a.colour = out->colour; a.st = st; a.cap_rows = out->cap_rows;
@@ -310,6 +320,7 @@ int launch_decode(const gs_anchors *A, const gs_camera *cams, const ViewTable &v
         cudaFuncSetAttribute(decode_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return GS_ERR_UNSUPPORTED;
     decode_fp32_kernel<<<grid, nt, smem, s>>>(a);
+    count_launches(1);
     return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 

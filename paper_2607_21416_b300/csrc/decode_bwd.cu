@@ -64,7 +64,9 @@ __global__ void __launch_bounds__(kDbRows) decode_bwd_fp32_kernel(DecodeBwdArgs 
 #pragma unroll
             for (int i = 0; i < 3; ++i) xc[i] = -(c.R[i] * c.t[0] + c.R[3 + i] * c.t[1] + c.R[6 + i] * c.t[2]);
             an = __ldg(a.f.row_anchor + r);
+            if (!idx_ok(a.f.st, an, a.f.N, 61)) an = 0;
             m = __ldg(a.f.part + an);
+            if (!idx_ok(a.f.st, m, a.f.M, 62)) m = 0;
             for (int i = 0; i < F; ++i) s_u[i * kDbStride + tid] = __ldg(a.f.feat + (size_t)an * F + i);
             d[0] = __ldg(a.f.xyz + 3 * an) - xc[0];
             d[1] = __ldg(a.f.xyz + 3 * an + 1) - xc[1];
@@ -278,7 +280,7 @@ int launch_decode_bwd(const gs_anchors *A, const gs_camera *cams, const ViewTabl
     DecodeBwdArgs a;
     DecodeArgs &f = a.f;
     f.xyz = A->xyz; f.feat = A->feat; f.log_scaling = A->log_scaling; f.offsets = A->offsets;
-    f.part = A->part; f.mlp = A->mlp; f.mlp_floats = P; f.F = A->F; f.k = A->k; f.H = A->hidden;
+    f.part = A->part; f.mlp = A->mlp; f.mlp_floats = P; f.N = A->N; f.F = A->F; f.k = A->k; f.H = A->hidden;
     f.M = A->M; f.V = vt.V; f.cams = cams; f.view_start = g->view_start; f.row_anchor = g->row_anchor;
     f.mu = g->mu; f.scale = g->scale; f.quat = g->quat; f.opacity = g->opacity; f.colour = g->colour;
     f.st = st; f.cap_rows = g->cap_rows;
@@ -295,6 +297,7 @@ int launch_decode_bwd(const gs_anchors *A, const gs_camera *cams, const ViewTabl
     const int tiles = (int)std::max<long long>(1, (g->cap_rows + kDbRows - 1) / kDbRows);
     const int grid = std::min(tiles, sm_count());
     decode_bwd_fp32_kernel<<<grid, kDbRows, smem, s>>>(a);
+    count_launches(1);
     return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 

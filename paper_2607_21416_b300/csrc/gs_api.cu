@@ -1,5 +1,6 @@
 // gs_api.cu -- extern "C" entry points of libgs: argument checks, view
 // tables and dispatch to the kernels.  Nothing here allocates or syncs.
+#include <atomic>
 #include <cstring>
 
 #include "gs_internal.cuh"
@@ -30,6 +31,9 @@ bool make_view_table(const gs_view *views, int V, ViewTable *vt)
     vt->total_pixels = pb;
     return true;
 }
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 
 int sm_count()
 {
@@ -70,6 +74,8 @@ static int launch_status()
 }
 
 extern "C" {
+
+uint64_t gs_kernel_launches(void) { return (uint64_t)g_launches.load(std::memory_order_relaxed); }
 
 int64_t gs_mlp_floats(int32_t F, int32_t k, int32_t hidden)
 {
@@ -141,7 +147,8 @@ int gs_project(const gs_gauss3d *g, const gs_camera *cams, const gs_view *views,
     ViewTable vt;
     if (!check_gauss(g) || !cams || !out || !out->rec || !out->tiles || !status || !make_view_table(views, V, &vt))
         return GS_ERR_INVALID_ARG;
-    if ((reinterpret_cast<uintptr_t>(out->rec) & 15) != 0) return GS_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(out->rec) & 15) != 0 || out->cap < g->cap_rows * (long long)g->k)
+        return GS_ERR_INVALID_ARG;
     return launch_project(g, cams, vt, out, status, (cudaStream_t)stream);
 }
 
@@ -153,7 +160,8 @@ int gs_bin_sort(const gs_splats *sp, int32_t k, const int32_t *view_start, int64
         !bins->ranges || !bins->n_pairs || bins->cap_pairs < 0 || bins->cap_pairs > 0xffffffffll || !status ||
         !make_view_table(views, V, &vt) || cap_rows * (long long)k >= (1ll << 31))
         return GS_ERR_INVALID_ARG;
-    if (!ws) return GS_ERR_INVALID_ARG;
+    if (!ws || sp->cap < cap_rows * (long long)k || (reinterpret_cast<uintptr_t>(sp->rec) & 15) != 0)
+        return GS_ERR_INVALID_ARG;
     return launch_bin_sort(sp, k, view_start, cap_rows, vt, bins, ws, ws_bytes, status, (cudaStream_t)stream);
 }
 

@@ -66,6 +66,19 @@ __device__ __forceinline__ void set_needed(gs_status *st, long long n)
 {
     atomicMax(reinterpret_cast<unsigned long long *>(&st->needed), (unsigned long long)n);
 }
+// Defensive index check: records GS_ERR_INVALID_ARG with the site id and the
+// offending index in the status word and tells the caller to skip the access.
+__device__ __forceinline__ bool idx_ok(const gs_status *st, long long idx, long long lim, int site)
+{
+    if (idx >= 0 && idx < lim) return true;
+    gs_status *w = const_cast<gs_status *>(st);
+    if (atomicCAS(&w->code, 0, GS_ERR_INVALID_ARG) == 0) {
+        w->where = site;
+        w->needed = idx;
+    }
+    return false;
+}
+
 __device__ __forceinline__ bool has_error(const gs_status *st)
 {
     return *((volatile const int32_t *)&st->code) != 0;
@@ -93,5 +106,8 @@ inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 // Number of SMs of the current device (cached per device).
 int sm_count();
+
+// Host-side count of kernels this library has launched (gs_kernel_launches).
+void count_launches(int n);
 
 }  // namespace gs

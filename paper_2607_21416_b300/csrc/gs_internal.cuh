@@ -13,7 +13,7 @@ struct DecodeArgs {
     const float *xyz, *feat, *log_scaling, *offsets, *mlp;
     const int32_t *part;
     long long mlp_floats;
-    int F, k, H, M, V;
+    int N, F, k, H, M, V;
     const gs_camera *cams;
     const int32_t *view_start, *row_anchor;
     float *mu, *scale, *quat, *opacity, *colour;

@@ -136,6 +136,7 @@ int launch_project(const gs_gauss3d *g, const gs_camera *cams, const ViewTable &
     const long long need = (a.cap_cand + 255) / 256;
     const int grid = (int)std::max<long long>(1, std::min<long long>(need, (long long)sm_count() * 16));
     project_kernel<<<grid, 256, 0, s>>>(a, vt);
+    count_launches(1);
     return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 

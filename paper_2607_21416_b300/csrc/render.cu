@@ -49,6 +49,7 @@ __global__ void __launch_bounds__(kRT) render_fwd_kernel(const float4 *__restric
                                                          float bg0, float bg1, float bg2, float *__restrict__ image,
                                                          float *__restrict__ T_final, int32_t *__restrict__ last,
                                                          unsigned long long *__restrict__ n_eval,
+                                                         const uint32_t *__restrict__ n_pairs, long long cap_cand,
                                                          const gs_status *st)
 {
     if (has_error(st)) return;
@@ -58,16 +59,18 @@ __global__ void __launch_bounds__(kRT) render_fwd_kernel(const float4 *__restric
     const int t = blockIdx.x;
     const TileCoord tc = tile_coord(vt, t);
     const float fpx = (float)tc.px, fpy = (float)tc.py;
-    const uint32_t start = ranges[2 * t], end = ranges[2 * t + 1];
+    uint32_t start = ranges[2 * t], end = ranges[2 * t + 1];
+    if (end < start || (end > start && !idx_ok(st, (long long)end - 1, (long long)*n_pairs, 41))) end = start;
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
     int lastc = 0;
     bool done = !tc.inside;
-    unsigned long long nev = 0;
+    unsigned long long nev = 0, ncomp = 0;
     for (uint32_t b0 = start; b0 < end; b0 += kRT) {
         if (__syncthreads_count(done) == kRT) break;
         const uint32_t i = b0 + threadIdx.x;
         if (i < end) {
-            const size_t id = vals[i];
+            size_t id = vals[i];
+            if (!idx_ok(st, (long long)id, cap_cand, 42)) id = 0;
             const float4 r0 = __ldg(&rec[3 * id]);
             const float4 r1 = __ldg(&rec[3 * id + 1]);
             const float4 r2 = __ldg(&rec[3 * id + 2]);
@@ -95,13 +98,18 @@ __global__ void __launch_bounds__(kRT) render_fwd_kernel(const float4 *__restric
                 C2 = fmaf(s_c[j], w, C2);
                 T = Tn;
                 lastc = (int)(b0 - start) + j + 1;
+                if (COUNT) ++ncomp;
             }
         }
     }
     if (COUNT) {
-        // warp-reduce the evaluation count, one atomic per warp
-        for (int o = 16; o > 0; o >>= 1) nev += __shfl_down_sync(0xffffffffu, nev, o);
+        // warp-reduce the evaluation counts, one atomic per warp and counter
+        for (int o = 16; o > 0; o >>= 1) {
+            nev += __shfl_down_sync(0xffffffffu, nev, o);
+            ncomp += __shfl_down_sync(0xffffffffu, ncomp, o);
+        }
         if ((threadIdx.x & 31) == 0 && nev) atomicAdd(n_eval, nev);
+        if ((threadIdx.x & 31) == 0 && ncomp) atomicAdd(n_eval + 1, ncomp);
     }
     if (!tc.inside) return;
     const int v = tc.v;
@@ -145,7 +153,7 @@ __global__ void __launch_bounds__(kRT) render_bwd_kernel(
     const float4 *__restrict__ rec, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
     ViewTable vt, float bg0, float bg1, float bg2, const float *__restrict__ d_image,
     const float *__restrict__ T_final_in, const int32_t *__restrict__ last_in, float *__restrict__ sgrad,
-    const gs_status *st)
+    const uint32_t *__restrict__ n_pairs, long long cap_cand, const gs_status *st)
 {
     if (has_error(st)) return;
     __shared__ float4 s_a[kRT];
@@ -156,7 +164,8 @@ __global__ void __launch_bounds__(kRT) render_bwd_kernel(
     const int t = blockIdx.x;
     const TileCoord tc = tile_coord(vt, t);
     const float fpx = (float)tc.px, fpy = (float)tc.py;
-    const uint32_t start = ranges[2 * t], end = ranges[2 * t + 1];
+    uint32_t start = ranges[2 * t], end = ranges[2 * t + 1];
+    if (end < start || (end > start && !idx_ok(st, (long long)end - 1, (long long)*n_pairs, 51))) end = start;
     const int v = tc.v;
     const long long W = vt.W[v], H = vt.H[v];
     const long long pix = (long long)tc.py * W + tc.px;
@@ -175,7 +184,8 @@ __global__ void __launch_bounds__(kRT) render_bwd_kernel(
             if (__syncthreads_count(done) == kRT) break;
             const uint32_t i = b0 + threadIdx.x;
             if (i < end) {
-                const size_t id = vals[i];
+                size_t id = vals[i];
+                if (!idx_ok(st, (long long)id, cap_cand, 52)) id = 0;
                 s_a[threadIdx.x] = __ldg(&rec[3 * id]);
                 s_b[threadIdx.x] = __ldg(&rec[3 * id + 1]);
             }
@@ -216,7 +226,8 @@ __global__ void __launch_bounds__(kRT) render_bwd_kernel(
         {
             const int p = hi - 1 - (int)threadIdx.x;   // smem slot j <-> position hi-1-j
             if (p >= lo) {
-                const uint32_t id = vals[start + p];
+                uint32_t id = vals[start + p];
+                if (!idx_ok(st, (long long)id, cap_cand, 53)) id = 0;
                 s_id[threadIdx.x] = id;
                 s_a[threadIdx.x] = __ldg(&rec[3 * (size_t)id]);
                 s_b[threadIdx.x] = __ldg(&rec[3 * (size_t)id + 1]);
@@ -434,14 +445,17 @@ int launch_render_fwd(const gs_splats *sp, const gs_bins *bins, const ViewTable 
     if (vt.total_tiles == 0) return GS_OK;
     const float4 *rec = reinterpret_cast<const float4 *>(sp->rec);
     if (n_eval) {
-        cudaMemsetAsync(n_eval, 0, sizeof(long long), s);
+        cudaMemsetAsync(n_eval, 0, 2 * sizeof(long long), s);
         render_fwd_kernel<true><<<vt.total_tiles, kRT, 0, s>>>(rec, bins->vals, bins->ranges, vt, bg[0], bg[1],
                                                                bg[2], image, T_final, last,
-                                                               reinterpret_cast<unsigned long long *>(n_eval), st);
+                                                               reinterpret_cast<unsigned long long *>(n_eval),
+                                                               bins->n_pairs, sp->cap, st);
     } else {
         render_fwd_kernel<false><<<vt.total_tiles, kRT, 0, s>>>(rec, bins->vals, bins->ranges, vt, bg[0], bg[1],
-                                                                bg[2], image, T_final, last, nullptr, st);
+                                                                bg[2], image, T_final, last, nullptr,
+                                                                bins->n_pairs, sp->cap, st);
     }
+    count_launches(1);
     return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 
@@ -452,6 +466,7 @@ int launch_l1(const float *image, const float *target, const ViewTable &vt, floa
     const long long n = 3 * vt.total_pixels;
     const int grid = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, (long long)sm_count() * 8));
     l1_kernel<<<grid, 256, 0, s>>>(image, target, vt, loss, d_image);
+    count_launches(1);
     return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 
@@ -463,9 +478,12 @@ int launch_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splat
     const long long cap_cand = g->cap_rows * (long long)g->k;
     cudaMemsetAsync(sgrad->g, 0, sizeof(float) * 9 * (size_t)cap_cand, s);
     const float4 *rec = reinterpret_cast<const float4 *>(sp->rec);
-    if (vt.total_tiles > 0)
+    if (vt.total_tiles > 0) {
         render_bwd_kernel<<<vt.total_tiles, kRT, 0, s>>>(rec, bins->vals, bins->ranges, vt, bg[0], bg[1], bg[2],
-                                                          d_image, T_final, last, sgrad->g, st);
+                                                          d_image, T_final, last, sgrad->g, bins->n_pairs,
+                                                          std::min<long long>(sp->cap, cap_cand), st);
+        count_launches(1);
+    }
     ProjBwdArgs a;
     a.mu = g->mu; a.scale = g->scale; a.quat = g->quat; a.view_start = g->view_start; a.tiles = sp->tiles;
     a.cams = cams; a.sgrad = sgrad->g; a.k = g->k; a.V = vt.V; a.cap_cand = cap_cand;
@@ -473,6 +491,7 @@ int launch_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splat
     a.dcolour = out->dcolour; a.st = st;
     const int grid = (int)std::max<long long>(1, std::min<long long>((cap_cand + 255) / 256, (long long)sm_count() * 16));
     project_bwd_kernel<<<grid, 256, 0, s>>>(a, vt);
+    count_launches(1);
     return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 

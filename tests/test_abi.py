@@ -74,7 +74,7 @@ def test_bad_arguments_rejected_without_a_gpu(lib):
     assert lib.gs_decode(C.byref(a), None, views, 1, 0, C.byref(g), None, 0, None, None) == L.GS_ERR_INVALID_ARG
     assert lib.gs_project(None, None, views, 1, None, None, None) == L.GS_ERR_INVALID_ARG
     bad_views = (L.gs_view * 1)(L.gs_view(0, 48))
-    sp = L.gs_splats(16, 16)
+    sp = L.gs_splats(1, 16, 16)
     bins = L.gs_bins(10, 16, None, 16, 16)
     assert lib.gs_bin_sort(C.byref(sp), 1, C.c_void_p(16), 10, bad_views, 1, C.byref(bins), C.c_void_p(256),
                            1 << 20, C.c_void_p(16), None) == L.GS_ERR_INVALID_ARG
