@@ -146,13 +146,14 @@ def run_ours(args, rank, world, dist):
         ev[2].record()
         api.bin_sort(rp.splats, rp.g, views, rp.bins, rp.sort_ws, rp.status)
         ev[3].record()
-        api.render_fwd(rp.splats, rp.bins, views, rp.bg, rp.image, rp.status)
+        api.render_fwd(rp.splats, rp.bins, views, rp.bg, rp.image, rp.status, rp.render_ws, rp.chunk)
         ev[4].record()
         api.l1_loss(rp.image, target, views, rp.loss, rp.d_image)
         ev[5].record()
         if rp.ggrad is None:
             rp.ggrad = api.Gauss3DGrad.like(rp.g)
-        api.render_bwd(rp.g, rp.splats, rp.bins, views, rp.bg, rp.d_image, rp.sgrad, rp.ggrad, rp.status)
+        api.render_bwd(rp.g, rp.splats, rp.bins, views, rp.bg, rp.d_image, rp.sgrad, rp.ggrad, rp.status,
+                       rp.render_ws, rp.chunk)
         ev[6].record()
         api.decode_bwd(anchors, views, rp.g, rp.ggrad, rp.agrad, rp.dbwd_ws, rp.status, prec)
         ev[7].record()
@@ -315,7 +316,8 @@ def work_counts(rp):
     from paper_2607_21416_b300 import api
     T = torch.zeros(rp.views.total_pixels, device="cuda")
     last = torch.zeros(rp.views.total_pixels, device="cuda", dtype=torch.int32)
-    api.render_fwd(rp.splats, rp.bins, rp.views, rp.bg, rp.image, rp.status, T, last, rp.n_eval)
+    api.render_fwd(rp.splats, rp.bins, rp.views, rp.bg, rp.image, rp.status, rp.render_ws, rp.chunk, T, last,
+                   rp.n_eval)
     torch.cuda.synchronize()
     return {"examined": int(rp.n_eval[0].item()), "composited": int(rp.n_eval[1].item()),
             "reverse_examined": int(last.to(torch.int64).sum().item())}

@@ -172,6 +172,9 @@ int64_t gs_total_pixels(const gs_view *views, int32_t V);
 size_t gs_decode_workspace(int32_t N, int32_t V, int32_t M, int64_t cap_rows);
 size_t gs_bin_sort_workspace(const gs_view *views, int32_t V, int64_t cap_cand, int64_t cap_pairs);
 size_t gs_decode_bwd_workspace(int32_t N, int32_t V, int32_t M, int64_t cap_rows);
+/* Render workspace (shared by gs_render_fwd and gs_render_bwd): the chunk
+ * plan and per-chunk state of the tiles whose list is longer than `chunk`. */
+size_t gs_render_workspace(const gs_view *views, int32_t V, int64_t cap_pairs, int32_t chunk);
 const char *gs_status_string(int32_t code);
 /* Number of kernels this library has enqueued since it was loaded (host
  * counter, all devices and threads); a diagnostic for launch accounting. */
@@ -216,15 +219,21 @@ int gs_bin_sort(const gs_splats *sp, int32_t k, const int32_t *view_start, int64
 /* Eq. 1 per pixel over its tile's sorted list: T = 1; for each splat,
  * alpha = min(0.99, o exp(power)), skipped if power > 0 or alpha < 1/255;
  * stop before a splat whose T(1 - alpha) < 1e-4; C += c alpha T; T *= 1 -
- * alpha.  image = C + T bg.  bg: HOST float[3].  T_final (float per pixel) and
- * last (int32 per pixel: 1-based list position of the last composited splat)
- * are optional outputs (NULL to skip); gs_render_bwd can use them or
- * recompute them.  n_eval (device int64[2], NULL to skip) receives the number
+ * alpha.  image = C + T bg.  bg: HOST float[3].
+ * Work items: each tile's list is cut into chunks of `chunk` splats (0 selects
+ * 2048; otherwise 256 .. 2^24), one CTA each, so that a few very long tiles
+ * do not serialise the launch; a chunk starts from the product of the
+ * transmittances of the chunks in front of it, which reproduces the
+ * front-to-back order exactly.  ws / ws_bytes: gs_render_workspace bytes,
+ * 256-byte aligned; gs_render_bwd needs the same workspace, untouched, and
+ * the same `chunk`.  T_final (float per pixel) and last (int32 per pixel:
+ * 1-based list position of the last composited splat) are optional outputs
+ * (NULL to skip).  n_eval (device int64[2], NULL to skip) receives the number
  * of (pixel, splat) pairs examined and the number composited (a counting
  * variant of the kernel runs when it is given). */
 int gs_render_fwd(const gs_splats *sp, const gs_bins *bins, const gs_view *views, int32_t V,
-                  const float *bg, float *image, float *T_final, int32_t *last, int64_t *n_eval,
-                  gs_status *status, void *stream);
+                  const float *bg, int32_t chunk, void *ws, size_t ws_bytes, float *image,
+                  float *T_final, int32_t *last, int64_t *n_eval, gs_status *status, void *stream);
 
 /* L = sum over views of mean |C - C_target| (L1 term of Eq. 3), written to
  * loss (device float[1], overwritten); dL/dC = sign(C - C_target)/(3 H W)
@@ -239,13 +248,16 @@ int gs_l1_loss(const float *image, const float *target, const gs_view *views, in
  * active) to mean and conic; per-splat sums are reduced across each warp
  * before global atomics.  Then the projection chain rule gives d mu, d scale,
  * d quat; d opacity, d colour pass through.  T_final/last: the forward's
- * optional outputs, or NULL to recompute them.  sgrad: per-splat view-space
+ * optional outputs, or NULL to recompute them (tiles cut into several chunks
+ * always use the per-chunk state the forward left in ws; chunk and ws must be
+ * those of the forward).  sgrad: per-splat view-space
  * gradients (workspace-like output, overwritten).  out: overwritten for every
  * candidate (zeros for culled ones). */
 int gs_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *sp,
                   const gs_bins *bins, const gs_view *views, int32_t V, const float *bg,
-                  const float *d_image, const float *T_final, const int32_t *last,
-                  gs_splat_grad *sgrad, gs_gauss3d_grad *out, gs_status *status, void *stream);
+                  int32_t chunk, void *ws, size_t ws_bytes, const float *d_image,
+                  const float *T_final, const int32_t *last, gs_splat_grad *sgrad,
+                  gs_gauss3d_grad *out, gs_status *status, void *stream);
 
 /* Reverse of gs_decode, summed over views: through the activations (only for
  * candidates with opacity > 0), both MLP layers (hidden activations

@@ -77,12 +77,13 @@ EXPORTS = {
     "gs_decode": (C.c_int, [P(gs_anchors), vp, P(gs_view), i32, i32, P(gs_gauss3d), vp, sz, vp, vp]),
     "gs_project": (C.c_int, [P(gs_gauss3d), vp, P(gs_view), i32, P(gs_splats), vp, vp]),
     "gs_bin_sort": (C.c_int, [P(gs_splats), i32, vp, i64, P(gs_view), i32, P(gs_bins), vp, sz, vp, vp]),
-    "gs_render_fwd": (C.c_int, [P(gs_splats), P(gs_bins), P(gs_view), i32, P(C.c_float), vp, vp, vp,
-                                vp, vp, vp]),
+    "gs_render_workspace": (sz, [P(gs_view), i32, i64, i32]),
+    "gs_render_fwd": (C.c_int, [P(gs_splats), P(gs_bins), P(gs_view), i32, P(C.c_float), i32, vp, sz,
+                                vp, vp, vp, vp, vp, vp]),
     "gs_l1_loss": (C.c_int, [vp, vp, P(gs_view), i32, vp, vp, vp]),
     "gs_render_bwd": (C.c_int, [P(gs_gauss3d), vp, P(gs_splats), P(gs_bins), P(gs_view), i32,
-                                P(C.c_float), vp, vp, vp, P(gs_splat_grad), P(gs_gauss3d_grad), vp,
-                                vp]),
+                                P(C.c_float), i32, vp, sz, vp, vp, vp, P(gs_splat_grad),
+                                P(gs_gauss3d_grad), vp, vp]),
     "gs_decode_bwd": (C.c_int, [P(gs_anchors), vp, P(gs_view), i32, i32, P(gs_gauss3d),
                                 P(gs_gauss3d_grad), P(gs_anchor_grad), vp, sz, vp, vp]),
 }

@@ -242,13 +242,17 @@ def _bg(bg):
     return (C.c_float * 3)(*[float(x) for x in bg])
 
 
-def render_fwd(sp: Splats, bins: Bins, views: Views, bg, image, status, T_final=None, last=None,
-               n_eval=None, stream=None):
+def render_workspace(views: Views, cap_pairs, chunk=0):
+    return int(L.load().gs_render_workspace(views.ptr, views.V, cap_pairs, chunk))
+
+
+def render_fwd(sp: Splats, bins: Bins, views: Views, bg, image, status, ws, chunk=0, T_final=None,
+               last=None, n_eval=None, stream=None):
     lib = L.load()
     s, b = sp.struct(), bins.struct()
-    L.check("gs_render_fwd", lib.gs_render_fwd(C.byref(s), C.byref(b), views.ptr, views.V, _bg(bg),
-                                               _ptr(image), _ptr(T_final), _ptr(last), _ptr(n_eval),
-                                               _ptr(status), _stream(stream)))
+    L.check("gs_render_fwd", lib.gs_render_fwd(C.byref(s), C.byref(b), views.ptr, views.V, _bg(bg), chunk,
+                                               _ptr(ws), ws.numel(), _ptr(image), _ptr(T_final),
+                                               _ptr(last), _ptr(n_eval), _ptr(status), _stream(stream)))
 
 
 def l1_loss(image, target, views: Views, loss, d_image, stream=None):
@@ -258,15 +262,15 @@ def l1_loss(image, target, views: Views, loss, d_image, stream=None):
 
 
 def render_bwd(g: Gauss3D, sp: Splats, bins: Bins, views: Views, bg, d_image, sgrad, out: Gauss3DGrad,
-               status, T_final=None, last=None, stream=None):
+               status, ws, chunk=0, T_final=None, last=None, stream=None):
     lib = L.load()
     gs_, s, b = g.struct(), sp.struct(), bins.struct()
     sg = L.gs_splat_grad(sgrad.data_ptr())
     o = out.struct()
     L.check("gs_render_bwd", lib.gs_render_bwd(C.byref(gs_), _ptr(views.cams), C.byref(s), C.byref(b),
-                                               views.ptr, views.V, _bg(bg), _ptr(d_image),
-                                               _ptr(T_final), _ptr(last), C.byref(sg), C.byref(o),
-                                               _ptr(status), _stream(stream)))
+                                               views.ptr, views.V, _bg(bg), chunk, _ptr(ws), ws.numel(),
+                                               _ptr(d_image), _ptr(T_final), _ptr(last), C.byref(sg),
+                                               C.byref(o), _ptr(status), _stream(stream)))
 
 
 def decode_bwd_workspace(anchors: Anchors, views: Views, cap_rows):

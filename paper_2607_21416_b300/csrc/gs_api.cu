@@ -165,15 +165,30 @@ int gs_bin_sort(const gs_splats *sp, int32_t k, const int32_t *view_start, int64
     return launch_bin_sort(sp, k, view_start, cap_rows, vt, bins, ws, ws_bytes, status, (cudaStream_t)stream);
 }
 
-int gs_render_fwd(const gs_splats *sp, const gs_bins *bins, const gs_view *views, int32_t V, const float *bg,
-                  float *image, float *T_final, int32_t *last, int64_t *n_eval, gs_status *status, void *stream)
+static int chunk_len(int32_t chunk) { return chunk == 0 ? 2048 : chunk; }
+
+size_t gs_render_workspace(const gs_view *views, int32_t V, int64_t cap_pairs, int32_t chunk)
 {
     ViewTable vt;
-    if (!sp || !sp->rec || !bins || !bins->vals || !bins->ranges || !bg || !image || !status ||
+    if (!make_view_table(views, V, &vt) || cap_pairs < 0 || (chunk != 0 && (chunk < 256 || chunk > (1 << 24))))
+        return 0;
+    return render_workspace_bytes(vt, cap_pairs, chunk_len(chunk));
+}
+
+int gs_render_fwd(const gs_splats *sp, const gs_bins *bins, const gs_view *views, int32_t V, const float *bg,
+                  int32_t chunk, void *ws, size_t ws_bytes, float *image, float *T_final, int32_t *last,
+                  int64_t *n_eval, gs_status *status, void *stream)
+{
+    ViewTable vt;
+    if (!sp || !sp->rec || !bins || !bins->vals || !bins->ranges || !bins->n_pairs || !bg || !image || !status ||
         !make_view_table(views, V, &vt) || (T_final == nullptr) != (last == nullptr))
         return GS_ERR_INVALID_ARG;
-    return launch_render_fwd(sp, bins, vt, bg, image, T_final, last, reinterpret_cast<long long *>(n_eval), status,
-                             (cudaStream_t)stream);
+    if ((chunk != 0 && (chunk < 256 || chunk > (1 << 24))) || !ws ||
+        (reinterpret_cast<uintptr_t>(ws) & 255) != 0 ||
+        ws_bytes < render_workspace_bytes(vt, bins->cap_pairs, chunk_len(chunk)))
+        return GS_ERR_INVALID_ARG;
+    return launch_render_fwd(sp, bins, vt, bg, chunk_len(chunk), ws, image, T_final, last,
+                             reinterpret_cast<long long *>(n_eval), status, (cudaStream_t)stream);
 }
 
 int gs_l1_loss(const float *image, const float *target, const gs_view *views, int32_t V, float *loss,
@@ -185,18 +200,22 @@ int gs_l1_loss(const float *image, const float *target, const gs_view *views, in
 }
 
 int gs_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *sp, const gs_bins *bins,
-                  const gs_view *views, int32_t V, const float *bg, const float *d_image, const float *T_final,
-                  const int32_t *last, gs_splat_grad *sgrad, gs_gauss3d_grad *out, gs_status *status,
-                  void *stream)
+                  const gs_view *views, int32_t V, const float *bg, int32_t chunk, void *ws, size_t ws_bytes,
+                  const float *d_image, const float *T_final, const int32_t *last, gs_splat_grad *sgrad,
+                  gs_gauss3d_grad *out, gs_status *status, void *stream)
 {
     ViewTable vt;
     if (!check_gauss(g) || !cams || !sp || !sp->rec || !sp->tiles || !bins || !bins->vals || !bins->ranges ||
-        !bg || !d_image || !sgrad || !sgrad->g || !out || !out->dmu || !out->dscale || !out->dquat ||
-        !out->dopacity || !out->dcolour || !status || !make_view_table(views, V, &vt) ||
-        (T_final == nullptr) != (last == nullptr))
+        !bins->n_pairs || !bg || !d_image || !sgrad || !sgrad->g || !out || !out->dmu || !out->dscale ||
+        !out->dquat || !out->dopacity || !out->dcolour || !status || !make_view_table(views, V, &vt) ||
+        (T_final == nullptr) != (last == nullptr) || sp->cap < g->cap_rows * (long long)g->k)
         return GS_ERR_INVALID_ARG;
-    return launch_render_bwd(g, cams, sp, bins, vt, bg, d_image, T_final, last, sgrad, out, status,
-                             (cudaStream_t)stream);
+    if ((chunk != 0 && (chunk < 256 || chunk > (1 << 24))) || !ws ||
+        (reinterpret_cast<uintptr_t>(ws) & 255) != 0 ||
+        ws_bytes < render_workspace_bytes(vt, bins->cap_pairs, chunk_len(chunk)))
+        return GS_ERR_INVALID_ARG;
+    return launch_render_bwd(g, cams, sp, bins, vt, bg, chunk_len(chunk), ws, d_image, T_final, last, sgrad, out,
+                             status, (cudaStream_t)stream);
 }
 
 int gs_decode_bwd(const gs_anchors *A, const gs_camera *cams, const gs_view *views, int32_t V, int32_t precision,

@@ -34,15 +34,18 @@ int launch_bin_sort(const gs_splats *sp, int k, const int32_t *view_start, long 
                     const ViewTable &vt, gs_bins *bins, void *ws, size_t ws_bytes, gs_status *st,
                     cudaStream_t s);
 
-int launch_render_fwd(const gs_splats *sp, const gs_bins *bins, const ViewTable &vt, const float bg[3],
-                      float *image, float *T_final, int32_t *last, long long *n_eval, gs_status *st,
+struct RenderPlan;
+int render_max_items(const ViewTable &vt, long long cap_pairs, int L);
+size_t render_workspace_bytes(const ViewTable &vt, long long cap_pairs, int L);
+int launch_render_fwd(const gs_splats *sp, const gs_bins *bins, const ViewTable &vt, const float bg[3], int L,
+                      void *ws, float *image, float *T_final, int32_t *last, long long *n_eval, gs_status *st,
                       cudaStream_t s);
 int launch_l1(const float *image, const float *target, const ViewTable &vt, float *loss, float *d_image,
               cudaStream_t s);
-int launch_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *sp,
-                      const gs_bins *bins, const ViewTable &vt, const float bg[3], const float *d_image,
-                      const float *T_final, const int32_t *last, gs_splat_grad *sgrad,
-                      gs_gauss3d_grad *out, gs_status *st, cudaStream_t s);
+int launch_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *sp, const gs_bins *bins,
+                      const ViewTable &vt, const float bg[3], int L, void *ws, const float *d_image,
+                      const float *T_final, const int32_t *last, gs_splat_grad *sgrad, gs_gauss3d_grad *out,
+                      gs_status *st, cudaStream_t s);
 
 size_t decode_bwd_workspace_bytes(int N, int V, int M, long long cap_rows);
 int launch_decode_bwd(const gs_anchors *A, const gs_camera *cams, const ViewTable &vt, int precision,

@@ -1,147 +1,17 @@
-// render.cu -- tile compositing (Eq. 1) forward and backward, the L1 term of
-// Eq. 3, and the chain rule of the projection.
+// render_bwd.cu -- reverse of the tile compositing (Eq. 1) over chunked work
+// items, and the chain rule of the projection.
 //
-// One CTA of 256 threads per 16x16 tile (one thread per pixel), all views in
-// one launch (tiles numbered view-major).  The tile's sorted splat list is
-// staged through shared memory 256 records at a time; every thread reads the
-// same record at the same time (broadcast, no bank conflicts).
-//
-// The power / alpha arithmetic is written with explicit fmaf / __fmul_rn so
-// the forward pass, the recomputation inside the backward pass and any stored
-// forward state take bit-identical skip / stop decisions.
-#include "gs_internal.cuh"
+// Per item and pixel the reverse traversal starts from the transmittance after
+// the item's last composited splat and the colour composited behind it, and
+// walks the chunk's list back to front.  Single-chunk tiles take those from the
+// forward's optional per-pixel output or recompute them (one extra front-to-back
+// pass over the tile); multi-chunk tiles read them from the per-chunk state the
+// forward left in the render workspace.  Per-splat sums are reduced across the
+// warp (shuffles) before one global atomicAdd per warp and quantity.
+#include "render_common.cuh"
 
 namespace gs {
 
-constexpr int kRT = kTilePix;   // 256 threads per tile
-
-__device__ __forceinline__ float splat_power(float4 a, float cc, float px, float py, float *dx, float *dy)
-{
-    const float x = __fsub_rn(a.x, px), y = __fsub_rn(a.y, py);
-    *dx = x; *dy = y;
-    // -0.5 (ca x^2 + cc y^2) - cb x y
-    const float q = fmaf(a.z, __fmul_rn(x, x), __fmul_rn(cc, __fmul_rn(y, y)));
-    return fmaf(-0.5f, q, -__fmul_rn(a.w, __fmul_rn(x, y)));
-}
-
-__device__ __forceinline__ float splat_gauss(float power) { return __expf(power); }
-
-struct TileCoord {
-    int v, px, py;
-    bool inside;
-};
-__device__ __forceinline__ TileCoord tile_coord(const ViewTable &vt, int t)
-{
-    TileCoord c;
-    c.v = view_of_tile(vt, t);
-    const int local = t - vt.tile_base[c.v];
-    const int tx = local % vt.TX[c.v], ty = local / vt.TX[c.v];
-    c.px = tx * kTile + (threadIdx.x & (kTile - 1));
-    c.py = ty * kTile + (threadIdx.x >> 4);
-    c.inside = c.px < vt.W[c.v] && c.py < vt.H[c.v];
-    return c;
-}
-
-template <bool COUNT>
-__global__ void __launch_bounds__(kRT) render_fwd_kernel(const float4 *__restrict__ rec,
-                                                         const uint32_t *__restrict__ vals,
-                                                         const uint32_t *__restrict__ ranges, ViewTable vt,
-                                                         float bg0, float bg1, float bg2, float *__restrict__ image,
-                                                         float *__restrict__ T_final, int32_t *__restrict__ last,
-                                                         unsigned long long *__restrict__ n_eval,
-                                                         const uint32_t *__restrict__ n_pairs, long long cap_cand,
-                                                         const gs_status *st)
-{
-    if (has_error(st)) return;
-    __shared__ float4 s_a[kRT];
-    __shared__ float4 s_b[kRT];
-    __shared__ float s_c[kRT];
-    const int t = blockIdx.x;
-    const TileCoord tc = tile_coord(vt, t);
-    const float fpx = (float)tc.px, fpy = (float)tc.py;
-    uint32_t start = ranges[2 * t], end = ranges[2 * t + 1];
-    if (end < start || (end > start && !idx_ok(st, (long long)end - 1, (long long)*n_pairs, 41))) end = start;
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    int lastc = 0;
-    bool done = !tc.inside;
-    unsigned long long nev = 0, ncomp = 0;
-    for (uint32_t b0 = start; b0 < end; b0 += kRT) {
-        if (__syncthreads_count(done) == kRT) break;
-        const uint32_t i = b0 + threadIdx.x;
-        if (i < end) {
-            size_t id = vals[i];
-            if (!idx_ok(st, (long long)id, cap_cand, 42)) id = 0;
-            const float4 r0 = __ldg(&rec[3 * id]);
-            const float4 r1 = __ldg(&rec[3 * id + 1]);
-            const float4 r2 = __ldg(&rec[3 * id + 2]);
-            s_a[threadIdx.x] = r0;
-            s_b[threadIdx.x] = r1;
-            s_c[threadIdx.x] = r2.x;
-        }
-        __syncthreads();
-        const int n = (int)min((uint32_t)kRT, end - b0);
-        if (!done) {
-            for (int j = 0; j < n; ++j) {
-                if (COUNT) ++nev;
-                const float4 a = s_a[j];
-                const float4 bb = s_b[j];
-                float dx, dy;
-                const float power = splat_power(a, bb.x, fpx, fpy, &dx, &dy);
-                if (power > 0.f) continue;
-                const float alpha = fminf(kAlphaMax, __fmul_rn(bb.y, splat_gauss(power)));
-                if (alpha < kAlphaMin) continue;
-                const float Tn = __fmul_rn(T, 1.f - alpha);
-                if (Tn < kTMin) { done = true; break; }
-                const float w = __fmul_rn(alpha, T);
-                C0 = fmaf(bb.z, w, C0);
-                C1 = fmaf(bb.w, w, C1);
-                C2 = fmaf(s_c[j], w, C2);
-                T = Tn;
-                lastc = (int)(b0 - start) + j + 1;
-                if (COUNT) ++ncomp;
-            }
-        }
-    }
-    if (COUNT) {
-        // warp-reduce the evaluation counts, one atomic per warp and counter
-        for (int o = 16; o > 0; o >>= 1) {
-            nev += __shfl_down_sync(0xffffffffu, nev, o);
-            ncomp += __shfl_down_sync(0xffffffffu, ncomp, o);
-        }
-        if ((threadIdx.x & 31) == 0 && nev) atomicAdd(n_eval, nev);
-        if ((threadIdx.x & 31) == 0 && ncomp) atomicAdd(n_eval + 1, ncomp);
-    }
-    if (!tc.inside) return;
-    const int v = tc.v;
-    const long long W = vt.W[v], H = vt.H[v];
-    const long long pix = (long long)tc.py * W + tc.px;
-    float *img = image + 3 * vt.pix_base[v];
-    img[pix] = fmaf(T, bg0, C0);
-    img[W * H + pix] = fmaf(T, bg1, C1);
-    img[2 * W * H + pix] = fmaf(T, bg2, C2);
-    if (T_final) T_final[vt.pix_base[v] + pix] = T;
-    if (last) last[vt.pix_base[v] + pix] = lastc;
-}
-
-// ------------------------------------------------------------------- L1
-__global__ void __launch_bounds__(256) l1_kernel(const float *__restrict__ image, const float *__restrict__ target,
-                                                 ViewTable vt, float *__restrict__ loss, float *__restrict__ d_image)
-{
-    const long long n = 3 * vt.total_pixels;
-    float acc = 0.f;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        int v = 0;
-        while (v + 1 < vt.V && 3 * vt.pix_base[v + 1] <= i) ++v;
-        const float inv = 1.f / (float)(3 * vt.pix_base[v + 1] - 3 * vt.pix_base[v]);
-        const float d = image[i] - target[i];
-        acc += fabsf(d) * inv;
-        d_image[i] = d > 0.f ? inv : (d < 0.f ? -inv : 0.f);
-    }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc);
-}
-
-// ------------------------------------------------------------ backward
 __device__ __forceinline__ float warp_sum(float x)
 {
 #pragma unroll
@@ -151,50 +21,62 @@ __device__ __forceinline__ float warp_sum(float x)
 
 __global__ void __launch_bounds__(kRT) render_bwd_kernel(
     const float4 *__restrict__ rec, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
-    ViewTable vt, float bg0, float bg1, float bg2, const float *__restrict__ d_image,
+    ViewTable vt, RenderPlan plan, float bg0, float bg1, float bg2, const float *__restrict__ d_image,
     const float *__restrict__ T_final_in, const int32_t *__restrict__ last_in, float *__restrict__ sgrad,
-    const uint32_t *__restrict__ n_pairs, long long cap_cand, const gs_status *st)
+    long long cap_cand, const gs_status *st)
 {
     if (has_error(st)) return;
-    __shared__ float4 s_a[kRT];
-    __shared__ float4 s_b[kRT];
-    __shared__ float s_c[kRT];
-    __shared__ uint32_t s_id[kRT];
+    Item it;
+    if (!item_of(blockIdx.x, plan.item_base, vt.total_tiles, ranges, plan.L, &it)) return;
+    __shared__ Staged S;
     __shared__ int s_maxlast;
-    const int t = blockIdx.x;
-    const TileCoord tc = tile_coord(vt, t);
+    const TileCoord tc = tile_coord(vt, it.t);
     const float fpx = (float)tc.px, fpy = (float)tc.py;
-    uint32_t start = ranges[2 * t], end = ranges[2 * t + 1];
-    if (end < start || (end > start && !idx_ok(st, (long long)end - 1, (long long)*n_pairs, 51))) end = start;
     const int v = tc.v;
     const long long W = vt.W[v], H = vt.H[v];
     const long long pix = (long long)tc.py * W + tc.px;
-    float T = 1.f;
+    const int n_items = (int)(it.s1 - it.s0);
+    float T = 1.f, B0 = 0.f, B1 = 0.f, B2 = 0.f;
     int lastc = 0;
     if (threadIdx.x == 0) s_maxlast = 0;
-    if (T_final_in) {
+    if (it.nk > 1) {
+        // state of the forward: start transmittance, end state, colour behind
+        float T0 = 1.f, Tf = 1.f;
+        for (int j = 0; j < it.nk; ++j) {
+            if (!(T0 >= kTMin)) break;
+            const int item = it.base + j;
+            if (j > it.k) {
+                B0 += state_plane(plan.state, item, 2)[threadIdx.x];
+                B1 += state_plane(plan.state, item, 3)[threadIdx.x];
+                B2 += state_plane(plan.state, item, 4)[threadIdx.x];
+            }
+            Tf = state_plane(plan.state, item, 1)[threadIdx.x];
+            if (j == it.k) {
+                T = Tf;
+                lastc = reinterpret_cast<const int *>(state_plane(plan.state, item, 5))[threadIdx.x];
+            }
+            T0 = __fmul_rn(T0, state_plane(plan.state, item, 0)[threadIdx.x]);
+        }
+        if (!tc.inside) lastc = 0;
+        B0 = fmaf(Tf, bg0, B0); B1 = fmaf(Tf, bg1, B1); B2 = fmaf(Tf, bg2, B2);
+    } else if (T_final_in) {
         if (tc.inside) {
             T = T_final_in[vt.pix_base[v] + pix];
-            lastc = min(last_in[vt.pix_base[v] + pix], (int)(end - start));
+            lastc = min(last_in[vt.pix_base[v] + pix], n_items);
         }
+        B0 = T * bg0; B1 = T * bg1; B2 = T * bg2;
     } else {
         // recompute the forward transmittance and the last composited position
         bool done = !tc.inside;
-        for (uint32_t b0 = start; b0 < end; b0 += kRT) {
+        for (uint32_t b0 = it.s0; b0 < it.s1; b0 += kRT) {
             if (__syncthreads_count(done) == kRT) break;
-            const uint32_t i = b0 + threadIdx.x;
-            if (i < end) {
-                size_t id = vals[i];
-                if (!idx_ok(st, (long long)id, cap_cand, 52)) id = 0;
-                s_a[threadIdx.x] = __ldg(&rec[3 * id]);
-                s_b[threadIdx.x] = __ldg(&rec[3 * id + 1]);
-            }
+            stage(S, rec, vals, b0 + threadIdx.x, b0 + threadIdx.x < it.s1, cap_cand, st, 52, false);
             __syncthreads();
-            const int n = (int)min((uint32_t)kRT, end - b0);
+            const int n = (int)min((uint32_t)kRT, it.s1 - b0);
             if (!done) {
                 for (int j = 0; j < n; ++j) {
-                    const float4 a = s_a[j];
-                    const float4 bb = s_b[j];
+                    const float4 a = S.a[j];
+                    const float4 bb = S.b[j];
                     float dx, dy;
                     const float power = splat_power(a, bb.x, fpx, fpy, &dx, &dy);
                     if (power > 0.f) continue;
@@ -203,10 +85,11 @@ __global__ void __launch_bounds__(kRT) render_bwd_kernel(
                     const float Tn = __fmul_rn(T, 1.f - alpha);
                     if (Tn < kTMin) { done = true; break; }
                     T = Tn;
-                    lastc = (int)(b0 - start) + j + 1;
+                    lastc = (int)(b0 - it.s0) + j + 1;
                 }
             }
         }
+        B0 = T * bg0; B1 = T * bg1; B2 = T * bg2;
     }
     __syncthreads();
     atomicMax(&s_maxlast, lastc);
@@ -215,24 +98,16 @@ __global__ void __launch_bounds__(kRT) render_bwd_kernel(
         const float *dimg = d_image + 3 * vt.pix_base[v];
         g0 = dimg[pix]; g1 = dimg[W * H + pix]; g2 = dimg[2 * W * H + pix];
     }
-    float B0 = T * bg0, B1 = T * bg1, B2 = T * bg2;
     __syncthreads();
-    const int maxlast = min(s_maxlast, (int)(end - start));
+    const int maxlast = min(s_maxlast, n_items);
     const int lane = threadIdx.x & 31;
-    // back to front over list positions [0, maxlast)
+    // back to front over chunk positions [0, maxlast)
     for (int hi = maxlast; hi > 0; hi -= kRT) {
         const int lo = max(0, hi - kRT);
         __syncthreads();
         {
             const int p = hi - 1 - (int)threadIdx.x;   // smem slot j <-> position hi-1-j
-            if (p >= lo) {
-                uint32_t id = vals[start + p];
-                if (!idx_ok(st, (long long)id, cap_cand, 53)) id = 0;
-                s_id[threadIdx.x] = id;
-                s_a[threadIdx.x] = __ldg(&rec[3 * (size_t)id]);
-                s_b[threadIdx.x] = __ldg(&rec[3 * (size_t)id + 1]);
-                s_c[threadIdx.x] = __ldg(&rec[3 * (size_t)id + 2]).x;
-            }
+            stage(S, rec, vals, it.s0 + (uint32_t)max(p, 0), p >= lo, cap_cand, st, 53, true);
         }
         __syncthreads();
         const int n = hi - lo;
@@ -241,8 +116,8 @@ __global__ void __launch_bounds__(kRT) render_bwd_kernel(
             float gmx = 0.f, gmy = 0.f, gca = 0.f, gcb = 0.f, gcc = 0.f, gop = 0.f, gr = 0.f, gg = 0.f, gb = 0.f;
             bool contrib = false;
             if (p < lastc) {
-                const float4 a = s_a[j];
-                const float4 bb = s_b[j];
+                const float4 a = S.a[j];
+                const float4 bb = S.b[j];
                 float dx, dy;
                 const float power = splat_power(a, bb.x, fpx, fpy, &dx, &dy);
                 if (power <= 0.f) {
@@ -255,7 +130,7 @@ __global__ void __launch_bounds__(kRT) render_bwd_kernel(
                         T = T / om;                      // transmittance in front of this splat
                         const float w = alpha * T;
                         gr = w * g0; gg = w * g1; gb = w * g2;
-                        const float cr = bb.z, cg = bb.w, cbl = s_c[j];
+                        const float cr = bb.z, cg = bb.w, cbl = S.c[j];
                         const float dal = g0 * (cr * T - B0 / om) + g1 * (cg * T - B1 / om) +
                                           g2 * (cbl * T - B2 / om);
                         B0 = fmaf(cr, w, B0); B1 = fmaf(cg, w, B1); B2 = fmaf(cbl, w, B2);
@@ -275,7 +150,7 @@ __global__ void __launch_bounds__(kRT) render_bwd_kernel(
                 gmx = warp_sum(gmx); gmy = warp_sum(gmy); gca = warp_sum(gca); gcb = warp_sum(gcb);
                 gcc = warp_sum(gcc); gop = warp_sum(gop); gr = warp_sum(gr); gg = warp_sum(gg); gb = warp_sum(gb);
                 if (lane == 0) {
-                    float *o = sgrad + 9 * (size_t)s_id[j];
+                    float *o = sgrad + 9 * (size_t)S.id[j];
                     atomicAdd(o + 0, gmx); atomicAdd(o + 1, gmy); atomicAdd(o + 2, gca);
                     atomicAdd(o + 3, gcb); atomicAdd(o + 4, gcc); atomicAdd(o + 5, gop);
                     atomicAdd(o + 6, gr); atomicAdd(o + 7, gg); atomicAdd(o + 8, gb);
@@ -437,50 +312,19 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(ProjBwdArgs a, ViewTab
     }
 }
 
-// ------------------------------------------------------------ launchers
-int launch_render_fwd(const gs_splats *sp, const gs_bins *bins, const ViewTable &vt, const float bg[3],
-                      float *image, float *T_final, int32_t *last, long long *n_eval, gs_status *st,
-                      cudaStream_t s)
-{
-    if (vt.total_tiles == 0) return GS_OK;
-    const float4 *rec = reinterpret_cast<const float4 *>(sp->rec);
-    if (n_eval) {
-        cudaMemsetAsync(n_eval, 0, 2 * sizeof(long long), s);
-        render_fwd_kernel<true><<<vt.total_tiles, kRT, 0, s>>>(rec, bins->vals, bins->ranges, vt, bg[0], bg[1],
-                                                               bg[2], image, T_final, last,
-                                                               reinterpret_cast<unsigned long long *>(n_eval),
-                                                               bins->n_pairs, sp->cap, st);
-    } else {
-        render_fwd_kernel<false><<<vt.total_tiles, kRT, 0, s>>>(rec, bins->vals, bins->ranges, vt, bg[0], bg[1],
-                                                                bg[2], image, T_final, last, nullptr,
-                                                                bins->n_pairs, sp->cap, st);
-    }
-    count_launches(1);
-    return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
-}
-
-int launch_l1(const float *image, const float *target, const ViewTable &vt, float *loss, float *d_image,
-              cudaStream_t s)
-{
-    cudaMemsetAsync(loss, 0, sizeof(float), s);
-    const long long n = 3 * vt.total_pixels;
-    const int grid = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, (long long)sm_count() * 8));
-    l1_kernel<<<grid, 256, 0, s>>>(image, target, vt, loss, d_image);
-    count_launches(1);
-    return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
-}
-
+// ------------------------------------------------------------ launcher
 int launch_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *sp, const gs_bins *bins,
-                      const ViewTable &vt, const float bg[3], const float *d_image, const float *T_final,
-                      const int32_t *last, gs_splat_grad *sgrad, gs_gauss3d_grad *out, gs_status *st,
-                      cudaStream_t s)
+                      const ViewTable &vt, const float bg[3], int L, void *ws, const float *d_image,
+                      const float *T_final, const int32_t *last, gs_splat_grad *sgrad, gs_gauss3d_grad *out,
+                      gs_status *st, cudaStream_t s)
 {
     const long long cap_cand = g->cap_rows * (long long)g->k;
     cudaMemsetAsync(sgrad->g, 0, sizeof(float) * 9 * (size_t)cap_cand, s);
     const float4 *rec = reinterpret_cast<const float4 *>(sp->rec);
     if (vt.total_tiles > 0) {
-        render_bwd_kernel<<<vt.total_tiles, kRT, 0, s>>>(rec, bins->vals, bins->ranges, vt, bg[0], bg[1], bg[2],
-                                                          d_image, T_final, last, sgrad->g, bins->n_pairs,
+        const RenderPlan plan = render_plan(vt, bins->cap_pairs, L, ws);
+        render_bwd_kernel<<<plan.max_items, kRT, 0, s>>>(rec, bins->vals, bins->ranges, vt, plan, bg[0], bg[1],
+                                                          bg[2], d_image, T_final, last, sgrad->g,
                                                           std::min<long long>(sp->cap, cap_cand), st);
         count_launches(1);
     }

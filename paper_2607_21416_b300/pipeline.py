@@ -38,7 +38,7 @@ class RenderPass:
     def __init__(self, views: api.Views, anchors: api.Anchors | None = None, k: int = 1,
                  cap_rows: int | None = None, cap_pairs: int | None = None,
                  precision: int = L.GS_PREC_FP32, store_state: bool = True,
-                 bg=(0.0, 0.0, 0.0), device="cuda", keys=False):
+                 bg=(0.0, 0.0, 0.0), device="cuda", keys=False, chunk=0):
         self.views = views
         self.anchors = anchors
         self.k = anchors.k if anchors is not None else k
@@ -47,6 +47,7 @@ class RenderPass:
         self.bg = tuple(float(x) for x in bg)
         self.device = device
         self.want_keys = keys
+        self.chunk = int(chunk)
         V = views.V
         if cap_rows is None:
             cap_rows = (anchors.N * V) if anchors is not None else 1
@@ -73,6 +74,7 @@ class RenderPass:
         self.splats = api.Splats.alloc(C_, dev)
         self.bins = api.Bins.alloc(self.cap_pairs, self.views.total_tiles, dev, keys=self.want_keys)
         self.sort_ws = api.workspace(api.bin_sort_workspace(self.views, C_, self.cap_pairs), dev)
+        self.render_ws = api.workspace(api.render_workspace(self.views, self.cap_pairs, self.chunk), dev)
         self.sgrad = torch.zeros(max(C_, 1), 9, device=dev)
         self.ggrad = None
 
@@ -92,6 +94,7 @@ class RenderPass:
         api.project(self.g, self.views, self.splats, self.status, stream)
         api.bin_sort(self.splats, self.g, self.views, self.bins, self.sort_ws, self.status, stream)
         api.render_fwd(self.splats, self.bins, self.views, self.bg, self.image, self.status,
+                       self.render_ws, self.chunk,
                        self.T_final if self.store_state else None,
                        self.last if self.store_state else None,
                        self.n_eval if count_evals else None, stream)
@@ -106,7 +109,8 @@ class RenderPass:
             self.ggrad = api.Gauss3DGrad.like(self.g)
         dimg = self.d_image if d_image is None else d_image
         api.render_bwd(self.g, self.splats, self.bins, self.views, self.bg, dimg, self.sgrad, self.ggrad,
-                       self.status, self.T_final if self.store_state else None,
+                       self.status, self.render_ws, self.chunk,
+                       self.T_final if self.store_state else None,
                        self.last if self.store_state else None, stream)
         if self.anchors is not None:
             api.decode_bwd(self.anchors, self.views, self.g, self.ggrad, self.agrad, self.dbwd_ws,

@@ -79,6 +79,12 @@ def test_bad_arguments_rejected_without_a_gpu(lib):
     assert lib.gs_bin_sort(C.byref(sp), 1, C.c_void_p(16), 10, bad_views, 1, C.byref(bins), C.c_void_p(256),
                            1 << 20, C.c_void_p(16), None) == L.GS_ERR_INVALID_ARG
     bg = (C.c_float * 3)(0, 0, 0)
-    assert lib.gs_render_fwd(C.byref(sp), C.byref(bins), views, 65, bg, C.c_void_p(16), None, None, None,
-                             C.c_void_p(16), None) == L.GS_ERR_INVALID_ARG
+    assert lib.gs_render_fwd(C.byref(sp), C.byref(bins), views, 65, bg, 0, C.c_void_p(256), 1 << 20,
+                             C.c_void_p(16), None, None, None, C.c_void_p(16), None) == L.GS_ERR_INVALID_ARG
+    # chunk below 256 and an unaligned workspace are rejected
+    assert lib.gs_render_fwd(C.byref(sp), C.byref(bins), views, 1, bg, 100, C.c_void_p(256), 1 << 20,
+                             C.c_void_p(16), None, None, None, C.c_void_p(16), None) == L.GS_ERR_INVALID_ARG
+    assert lib.gs_render_fwd(C.byref(sp), C.byref(bins), views, 1, bg, 0, C.c_void_p(16), 1 << 20,
+                             C.c_void_p(16), None, None, None, C.c_void_p(16), None) == L.GS_ERR_INVALID_ARG
+    assert lib.gs_render_workspace(views, 1, 100000, 0) > lib.gs_render_workspace(views, 1, 100000, 4096) > 0
     assert lib.gs_l1_loss(None, None, views, 1, None, None, None) == L.GS_ERR_INVALID_ARG

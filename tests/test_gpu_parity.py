@@ -19,7 +19,7 @@ def explicit_1():
 
 
 def explicit_ragged():
-    return scenes.explicit_frustum(seed=7, n=700, width=83, height=61, fx=70.0, fy=75.0, cx=41.0, cy=30.5)
+    return scenes.explicit_frustum(seed=7, n=3000, width=83, height=61, fx=70.0, fy=75.0, cx=41.0, cy=30.5)
 
 
 def tiny():
@@ -133,7 +133,7 @@ def test_bin_sort_bit_exact_depth_ties():
 
 
 # ------------------------------------------------------------ render forward
-def _render_fwd_case(s, view_start, k, prj, opacity, colour, keys, vals, ranges, bg=(0.0, 0.0, 0.0)):
+def _render_fwd_case(s, view_start, k, prj, opacity, colour, keys, vals, ranges, bg=(0.0, 0.0, 0.0), chunk=0):
     rec, tiles = pack_records(prj, opacity, colour)
     vw = api.Views(s.cams, s.wh)
     sp = gpu_splats_from(rec, tiles)
@@ -143,7 +143,8 @@ def _render_fwd_case(s, view_start, k, prj, opacity, colour, keys, vals, ranges,
     last = torch.zeros(vw.total_pixels, device="cuda", dtype=torch.int32)
     nev = torch.zeros(2, device="cuda", dtype=torch.int64)
     st = api.new_status()
-    api.render_fwd(sp, bins, vw, bg, img, st, Tf, last, nev)
+    ws = api.workspace(api.render_workspace(vw, bins.cap_pairs, chunk))
+    api.render_fwd(sp, bins, vw, bg, img, st, ws, chunk, Tf, last, nev)
     torch.cuda.synchronize()
     assert api.read_status(st)[0] == 0
     r = rounded_projection(prj, opacity, colour)
@@ -158,30 +159,38 @@ def _render_fwd_case(s, view_start, k, prj, opacity, colour, keys, vals, ranges,
     assert np.allclose(to_np(Tf)[ok], ren.T_final[ok], rtol=1e-3, atol=1e-6)
     assert int(nev[0].item()) == pytest.approx(ren.nev, rel=1e-3)
     assert 0 < int(nev[1].item()) <= int(nev[0].item())
-    return sp, bins, to_np(Tf), to_np(last), ren
+    if chunk:
+        lens = ranges[:, 1].astype(np.int64) - ranges[:, 0]
+        assert (lens > chunk).any(), "case should contain tiles cut into several chunks"
+    return sp, bins, to_np(Tf), to_np(last), ren, ws
 
 
+@pytest.mark.parametrize("chunk", [0, 256])
 @pytest.mark.parametrize("make", EXPLICIT)
-def test_render_fwd_matches_oracle(make):
+def test_render_fwd_matches_oracle(make, chunk):
     s = make()
     vs, prj, keys, vals, ranges = oracle_explicit(s)
-    _render_fwd_case(s, vs, 1, prj, s.opacity, s.colour, keys, vals, ranges, bg=(0.1, 0.3, 0.7))
+    _render_fwd_case(s, vs, 1, prj, s.opacity, s.colour, keys, vals, ranges, bg=(0.1, 0.3, 0.7), chunk=chunk)
 
 
-def test_render_fwd_anchor_views_matches_oracle():
-    s = tiny()
+@pytest.mark.parametrize("chunk", [0, 256])
+def test_render_fwd_anchor_views_matches_oracle(chunk):
+    s = tiny() if chunk == 0 else scenes.tiny_corridor(seed=0, n_anchors=4000)
     fw = O.forward_anchor(s)
     _render_fwd_case(s, fw.dec.view_start, s.k, fw.prj, fw.dec.opacity, fw.dec.colour, fw.keys,
-                     fw.vals, fw.ranges)
+                     fw.vals, fw.ranges, chunk=chunk)
 
 
 # ----------------------------------------------------------- render backward
-@pytest.mark.parametrize("make,store", [(explicit_1, True), (explicit_1, False), (explicit_ragged, False)])
-def test_render_bwd_matches_oracle(make, store):
+@pytest.mark.parametrize("make,store,chunk", [(explicit_1, True, 0), (explicit_1, False, 0),
+                                              (explicit_ragged, False, 0), (explicit_1, True, 256),
+                                              (explicit_1, False, 256), (explicit_ragged, False, 256)])
+def test_render_bwd_matches_oracle(make, store, chunk):
     s = make()
     bg = (0.2, 0.1, 0.4)
     vs, prj, keys, vals, ranges = oracle_explicit(s)
-    sp, bins, Tf, last, ren = _render_fwd_case(s, vs, 1, prj, s.opacity, s.colour, keys, vals, ranges, bg)
+    sp, bins, Tf, last, ren, ws = _render_fwd_case(s, vs, 1, prj, s.opacity, s.colour, keys, vals, ranges, bg,
+                                                   chunk)
     rng = np.random.default_rng(5)
     ok = ren.pix_flag == 0
     dimg = rng.normal(size=ren.image.shape) * image_mask(s.wh, ok)
@@ -192,10 +201,10 @@ def test_render_bwd_matches_oracle(make, store):
     st = api.new_status()
     dimg_t = torch.as_tensor(f32(dimg)).cuda()
     if store:
-        api.render_bwd(g, sp, bins, vw, bg, dimg_t, sgrad, out, st, torch.as_tensor(Tf).cuda(),
+        api.render_bwd(g, sp, bins, vw, bg, dimg_t, sgrad, out, st, ws, chunk, torch.as_tensor(Tf).cuda(),
                        torch.as_tensor(last).cuda())
     else:
-        api.render_bwd(g, sp, bins, vw, bg, dimg_t, sgrad, out, st)
+        api.render_bwd(g, sp, bins, vw, bg, dimg_t, sgrad, out, st, ws, chunk)
     torch.cuda.synchronize()
     assert api.read_status(st)[0] == 0
     r = rounded_projection(prj, s.opacity, s.colour)
@@ -286,18 +295,19 @@ def _e2e_masks(s, fw):
     return ok
 
 
-@pytest.mark.parametrize("make", [explicit_1, tiny])
-def test_end_to_end_plain_path(make):
+@pytest.mark.parametrize("make,chunk,store", [(explicit_1, 0, True), (tiny, 0, True), (explicit_1, 256, False),
+                                              (tiny, 256, False)])
+def test_end_to_end(make, chunk, store):
     s = make()
     vw = api.Views(s.cams, s.wh)
     if s.xyz is None:
         fw = O.forward_explicit(s)
-        rp = pipeline.RenderPass(vw, None, cap_rows=s.mu.shape[0])
+        rp = pipeline.RenderPass(vw, None, cap_rows=s.mu.shape[0], chunk=chunk, store_state=store)
         g = api.Gauss3D.explicit(s.mu, s.scale, s.quat, s.opacity, s.colour)
         rp.set_explicit(g)
     else:
         fw = O.forward_anchor(s)
-        rp = pipeline.RenderPass(vw, api.Anchors.from_scene(s))
+        rp = pipeline.RenderPass(vw, api.Anchors.from_scene(s), chunk=chunk, store_state=store)
     tgt = O.targets_flat(s)
     assert rp.ensure_capacity() == 0
     img = rp.forward()
