@@ -195,6 +195,20 @@ int gs_decode(const gs_anchors *A, const gs_camera *cams, const gs_view *views, 
               int32_t precision, gs_gauss3d *out, void *ws, size_t ws_bytes, gs_status *status,
               void *stream);
 
+/* Same as gs_decode, for callers that cannot allocate device memory (for
+ * example a real-time thread that must not enter the driver's allocator, or a
+ * plug-in whose host framework owns all device memory): there is no workspace
+ * argument.  The scratch lives in a static device array of 512 KiB that every
+ * GPU loading this library keeps until the process exits; calls needing more
+ * than ceil(N / 2048) * V <= 131072 counts return GS_ERR_CAPACITY at once and
+ * enqueue nothing.  The first call on each device looks the array's device
+ * address up (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls on a device share the array, so
+ * calls that overlap on the GPU race on it.  Nothing is allocated.  The paper
+ * has no counterpart of this entry point. */
+int gs_decode_noalloc(const gs_anchors *A, const gs_camera *cams, const gs_view *views, int32_t V,
+                      int32_t precision, gs_gauss3d *out, gs_status *status, void *stream);
+
 /* EWA projection of every candidate (3DGS preliminaries, Sec. III-A): p = R mu
  * + t, culled if opacity <= 0 or p_z <= 0.2; Sigma3 = R_q S^2 R_q^T; Sigma2 =
  * J R Sigma3 R^T J^T + 0.3 I with x/z, y/z clamped to 1.3x the half field of

@@ -75,6 +75,7 @@ EXPORTS = {
     "gs_status_string": (C.c_char_p, [i32]),
     "gs_kernel_launches": (C.c_uint64, []),
     "gs_decode": (C.c_int, [P(gs_anchors), vp, P(gs_view), i32, i32, P(gs_gauss3d), vp, sz, vp, vp]),
+    "gs_decode_noalloc": (C.c_int, [P(gs_anchors), vp, P(gs_view), i32, i32, P(gs_gauss3d), vp, vp]),
     "gs_project": (C.c_int, [P(gs_gauss3d), vp, P(gs_view), i32, P(gs_splats), vp, vp]),
     "gs_bin_sort": (C.c_int, [P(gs_splats), i32, vp, i64, P(gs_view), i32, P(gs_bins), vp, sz, vp, vp]),
     "gs_render_workspace": (sz, [P(gs_view), i32, i64, i32]),

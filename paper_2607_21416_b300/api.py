@@ -215,6 +215,16 @@ def decode(anchors: Anchors, views: Views, out: Gauss3D, ws, status, precision=L
                                        _stream(stream)))
 
 
+def decode_noalloc(anchors: Anchors, views: Views, out: Gauss3D, status, precision=L.GS_PREC_FP32,
+                   stream=None):
+    """gs_decode without a workspace (scratch in a static device array)."""
+    lib = L.load()
+    a, g = anchors.struct(), out.struct()
+    L.check("gs_decode_noalloc", lib.gs_decode_noalloc(C.byref(a), _ptr(views.cams), views.ptr, views.V,
+                                                       precision, C.byref(g), _ptr(status),
+                                                       _stream(stream)))
+
+
 def decode_workspace(anchors: Anchors, views: Views, cap_rows):
     return int(L.load().gs_decode_workspace(anchors.N, views.V, anchors.M, cap_rows))
 
