@@ -18,11 +18,6 @@ namespace gs {
 constexpr int kDbRows = 128;
 constexpr int kDbStride = kDbRows + 1;
 
-struct DecodeBwdArgs {
-    DecodeArgs f;   // forward inputs (mu.. colour unused)
-    const float *dmu, *dscale, *dquat, *dopacity, *dcolour;
-    float *dxyz, *dfeat, *dls, *doff, *dmlp;
-};
 
 __device__ __forceinline__ void head_layout(int F, int k, int H, int h, int *off, int *din, int *dout)
 {
@@ -33,7 +28,7 @@ __device__ __forceinline__ void head_layout(int F, int k, int H, int h, int *off
     *off = o; *din = d; *dout = douts[h];
 }
 
-__global__ void __launch_bounds__(kDbRows) decode_bwd_fp32_kernel(DecodeBwdArgs a)
+__global__ void __launch_bounds__(kDbRows) decode_bwd_fp32_kernel(DecodeBwdArgsB a)
 {
     if (has_error(a.f.st)) return;
     extern __shared__ float sm[];
@@ -270,14 +265,14 @@ int launch_decode_bwd(const gs_anchors *A, const gs_camera *cams, const ViewTabl
                       const gs_gauss3d *g, const gs_gauss3d_grad *dg, gs_anchor_grad *out, void *ws,
                       gs_status *st, cudaStream_t s)
 {
-    (void)ws; (void)precision;
+    (void)ws;
     const long long P = gs_mlp_floats(A->F, A->k, A->hidden);
     cudaMemsetAsync(out->dxyz, 0, sizeof(float) * 3 * (size_t)A->N, s);
     cudaMemsetAsync(out->dfeat, 0, sizeof(float) * (size_t)A->F * A->N, s);
     cudaMemsetAsync(out->dlog_scaling, 0, sizeof(float) * 6 * (size_t)A->N, s);
     cudaMemsetAsync(out->doffsets, 0, sizeof(float) * 3 * (size_t)A->k * A->N, s);
     cudaMemsetAsync(out->dmlp, 0, sizeof(float) * (size_t)P * A->M, s);
-    DecodeBwdArgs a;
+    DecodeBwdArgsB a;
     DecodeArgs &f = a.f;
     f.xyz = A->xyz; f.feat = A->feat; f.log_scaling = A->log_scaling; f.offsets = A->offsets;
     f.part = A->part; f.mlp = A->mlp; f.mlp_floats = P; f.N = A->N; f.F = A->F; f.k = A->k; f.H = A->hidden;
@@ -286,6 +281,7 @@ int launch_decode_bwd(const gs_anchors *A, const gs_camera *cams, const ViewTabl
     f.st = st; f.cap_rows = g->cap_rows;
     a.dmu = dg->dmu; a.dscale = dg->dscale; a.dquat = dg->dquat; a.dopacity = dg->dopacity; a.dcolour = dg->dcolour;
     a.dxyz = out->dxyz; a.dfeat = out->dfeat; a.dls = out->dlog_scaling; a.doff = out->doffsets; a.dmlp = out->dmlp;
+    if (precision == GS_PREC_BF16) return launch_decode_bwd_bf16(a, s);
     const size_t smem = fp32_smem(A->F, A->k, A->hidden, P);
     static int configured_smem = 0;
     if ((int)smem > configured_smem) {

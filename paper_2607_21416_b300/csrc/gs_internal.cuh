@@ -21,6 +21,13 @@ struct DecodeArgs {
     long long cap_rows;
 };
 
+struct DecodeBwdArgsB {
+    DecodeArgs f;   // forward inputs (the candidate outputs are not read)
+    const float *dmu, *dscale, *dquat, *dopacity, *dcolour;
+    float *dxyz, *dfeat, *dls, *doff, *dmlp;
+};
+int launch_decode_bwd_bf16(const DecodeBwdArgsB &a, cudaStream_t s);
+
 size_t decode_workspace_bytes(int N, int V);
 int launch_decode(const gs_anchors *A, const gs_camera *cams, const ViewTable &vt, int precision,
                   gs_gauss3d *out, void *ws, gs_status *st, cudaStream_t s);
