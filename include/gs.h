@@ -129,11 +129,14 @@ typedef struct gs_gauss3d_grad {
 } gs_gauss3d_grad;
 
 /* Projected splats, candidate-indexed.  `rec` holds one 48-byte record per
- * candidate: float[12] = mean_x, mean_y, conic_a, conic_b, conic_c, opacity,
- * r, g, b, depth, then two uint32 words x0 | x1 << 16 and y0 | y1 << 16 (the
- * tile rectangle [x0,x1) x [y0,y1) inside the candidate's view).  `tiles` is
- * the number of tiles the rectangle covers, 0 for a culled candidate.  The
- * power of pixel p is -(a dx^2 + c dy^2)/2 - b dx dy with (dx, dy) = mean - p. */
+ * candidate: float[12] = mean_x, mean_y, A, B, C, L, r, g, b, depth, then two
+ * uint32 words x0 | x1 << 16 and y0 | y1 << 16 (the tile rectangle [x0,x1) x
+ * [y0,y1) inside the candidate's view).  With the conic (a, b, c) = Sigma2^-1
+ * and the opacity o: A = -a log2(e)/2, B = -b log2(e), C = -c log2(e)/2,
+ * L = log2(o), so that the power of pixel p is power = (A dx^2 + B dx dy +
+ * C dy^2) ln 2 with (dx, dy) = mean - p, and o exp(power) = 2^(A dx^2 + B dx dy
+ * + C dy^2 + L).  `tiles` is the number of tiles the rectangle covers, 0 for
+ * a culled candidate. */
 typedef struct gs_splats {
     int64_t cap;      /* capacity C in records */
     float *rec;       /* [C][12], 16-byte aligned */

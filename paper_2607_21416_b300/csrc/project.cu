@@ -110,8 +110,10 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a, ViewTable v
                 const int x0 = (int)fx0, x1 = (int)fx1, y0 = (int)fy0, y1 = (int)fy1;
                 ntiles = (x1 - x0) * (y1 - y0);
                 if (ntiles > 0) {
-                    r0 = make_float4(mx, my, ka, kb);
-                    r1 = make_float4(kc, op, __ldg(a.colour + 3 * c), __ldg(a.colour + 3 * c + 1));
+                    // exponent coefficients in base 2: power * log2(e) = A dx^2 + B dx dy + C dy^2
+                    const float l2e = 1.4426950408889634f;
+                    r0 = make_float4(mx, my, -0.5f * l2e * ka, -l2e * kb);
+                    r1 = make_float4(-0.5f * l2e * kc, log2f(op), __ldg(a.colour + 3 * c), __ldg(a.colour + 3 * c + 1));
                     r2 = make_float4(__ldg(a.colour + 3 * c + 2), pz,
                                      __uint_as_float((uint32_t)x0 | ((uint32_t)x1 << 16)),
                                      __uint_as_float((uint32_t)y0 | ((uint32_t)y1 << 16)));

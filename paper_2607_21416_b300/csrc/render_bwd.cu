@@ -19,7 +19,76 @@ __device__ __forceinline__ float warp_sum(float x)
     return x;
 }
 
-__global__ void __launch_bounds__(kRT) render_bwd_kernel(
+// Warp sum of eight values at once (transpose-style halving: 9 shuffles instead
+// of 40).  Lane L returns the total of value ((L >> 4) & 1) * 4 + ((L >> 3) & 1)
+// * 2 + ((L >> 2) & 1); lanes with (L & 3) == 0 hold the eight totals.
+__device__ __forceinline__ float warp_sum8(const float v[8])
+{
+    const int lane = threadIdx.x & 31;
+    float r4[4], r2[2];
+    const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float send = u16 ? v[i] : v[i + 4];
+        const float keep = u16 ? v[i + 4] : v[i];
+        r4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = u8 ? r4[i] : r4[i + 2];
+        const float keep = u8 ? r4[i + 2] : r4[i];
+        r2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    const float send = u4 ? r2[0] : r2[1];
+    float r = (u4 ? r2[1] : r2[0]) + __shfl_xor_sync(0xffffffffu, send, 4);
+    r += __shfl_xor_sync(0xffffffffu, r, 2);
+    r += __shfl_xor_sync(0xffffffffu, r, 1);
+    return r;
+}
+
+// Reverse state of one pixel.
+struct PixBwd {
+    float T, B0, B1, B2, g0, g1, g2;
+    int last;
+};
+
+// Gradient terms of one pixel for staged splat j, added to acc[9] =
+// (d mean x, d mean y, d conic a, b, c, d opacity, d r, d g, d b).
+__device__ __forceinline__ bool bwd_step(PixBwd &ps, const float4 a, const float4 bb, float cb, float io, float px,
+                                         float py, float acc[9])
+{
+    float dx, dy;
+    const float q = splat_q(a, bb.x, px, py, &dx, &dy);
+    if (q > 0.f) return false;
+    const float ag = splat_alpha(q, bb.y);
+    const float alpha = fminf(kAlphaMax, ag);
+    if (alpha < kAlphaMin) return false;
+    const float inv = __frcp_rn(1.f - alpha);
+    ps.T = ps.T * inv;                     // transmittance in front of this splat
+    const float w = alpha * ps.T;
+    acc[6] = fmaf(w, ps.g0, acc[6]);
+    acc[7] = fmaf(w, ps.g1, acc[7]);
+    acc[8] = fmaf(w, ps.g2, acc[8]);
+    const float gc = ps.g0 * bb.z + ps.g1 * bb.w + ps.g2 * cb;
+    const float gB = ps.g0 * ps.B0 + ps.g1 * ps.B1 + ps.g2 * ps.B2;
+    const float dal = gc * ps.T - gB * inv;
+    ps.B0 = fmaf(bb.z, w, ps.B0);
+    ps.B1 = fmaf(bb.w, w, ps.B1);
+    ps.B2 = fmaf(cb, w, ps.B2);
+    if (ag < kAlphaMax) {
+        acc[5] = fmaf(dal, ag * io, acc[5]);          // d opacity = dal * exp(power)
+        const float dp = dal * alpha;                 // d power
+        const float dpl = dp * 0.6931471805599453f;   // power = ln 2 * (A dx^2 + B dx dy + C dy^2)
+        acc[0] = fmaf(dpl, fmaf(2.f * a.z, dx, a.w * dy), acc[0]);
+        acc[1] = fmaf(dpl, fmaf(2.f * bb.x, dy, a.w * dx), acc[1]);
+        acc[2] = fmaf(-0.5f * dp, dx * dx, acc[2]);
+        acc[3] = fmaf(-dp, dx * dy, acc[3]);
+        acc[4] = fmaf(-0.5f * dp, dy * dy, acc[4]);
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(kRThreads) render_bwd_kernel(
     const float4 *__restrict__ rec, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
     ViewTable vt, RenderPlan plan, float bg0, float bg1, float bg2, const float *__restrict__ d_image,
     const float *__restrict__ T_final_in, const int32_t *__restrict__ last_in, float *__restrict__ sgrad,
@@ -30,131 +99,131 @@ __global__ void __launch_bounds__(kRT) render_bwd_kernel(
     if (!item_of(blockIdx.x, plan.item_base, vt.total_tiles, ranges, plan.L, &it)) return;
     __shared__ Staged S;
     __shared__ int s_maxlast;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const TileCoord tc = tile_coord(vt, it.t);
-    const float fpx = (float)tc.px, fpy = (float)tc.py;
+    const float fpx = (float)tc.px, fy0 = (float)tc.py, fy1 = (float)(tc.py + 1);
     const int v = tc.v;
     const long long W = vt.W[v], H = vt.H[v];
-    const long long pix = (long long)tc.py * W + tc.px;
+    const long long pix0 = (long long)tc.py * W + tc.px, pix1 = pix0 + W;
     const int n_items = (int)(it.s1 - it.s0);
-    float T = 1.f, B0 = 0.f, B1 = 0.f, B2 = 0.f;
-    int lastc = 0;
-    if (threadIdx.x == 0) s_maxlast = 0;
+    PixBwd p0, p1;
+    p0.T = p1.T = 1.f;
+    p0.B0 = p0.B1 = p0.B2 = p1.B0 = p1.B1 = p1.B2 = 0.f;
+    p0.last = p1.last = 0;
+    if (tid == 0) s_maxlast = 0;
     if (it.nk > 1) {
-        // state of the forward: start transmittance, end state, colour behind
-        float T0 = 1.f, Tf = 1.f;
-        for (int j = 0; j < it.nk; ++j) {
-            if (!(T0 >= kTMin)) break;
-            const int item = it.base + j;
-            if (j > it.k) {
-                B0 += state_plane(plan.state, item, 2)[threadIdx.x];
-                B1 += state_plane(plan.state, item, 3)[threadIdx.x];
-                B2 += state_plane(plan.state, item, 4)[threadIdx.x];
+        // forward state: end transmittance, last position, colour behind the chunk
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            PixBwd &ps = half ? p1 : p0;
+            const int pix = tc.pid0 + half * kTile;
+            float T0 = 1.f, Tf = 1.f;
+            for (int j = 0; j < it.nk; ++j) {
+                if (!(T0 >= kTMin)) break;
+                const int item = it.base + j;
+                if (j > it.k) {
+                    ps.B0 += state_plane(plan.state, item, 2)[pix];
+                    ps.B1 += state_plane(plan.state, item, 3)[pix];
+                    ps.B2 += state_plane(plan.state, item, 4)[pix];
+                }
+                Tf = state_plane(plan.state, item, 1)[pix];
+                if (j == it.k) {
+                    ps.T = Tf;
+                    ps.last = reinterpret_cast<const int *>(state_plane(plan.state, item, 5))[pix];
+                }
+                if (j < it.nk - 1) T0 = __fmul_rn(T0, state_plane(plan.state, item, 0)[pix]);
             }
-            Tf = state_plane(plan.state, item, 1)[threadIdx.x];
-            if (j == it.k) {
-                T = Tf;
-                lastc = reinterpret_cast<const int *>(state_plane(plan.state, item, 5))[threadIdx.x];
-            }
-            T0 = __fmul_rn(T0, state_plane(plan.state, item, 0)[threadIdx.x]);
+            if (!(half ? tc.in1 : tc.in0)) ps.last = 0;
+            ps.B0 = fmaf(Tf, bg0, ps.B0); ps.B1 = fmaf(Tf, bg1, ps.B1); ps.B2 = fmaf(Tf, bg2, ps.B2);
         }
-        if (!tc.inside) lastc = 0;
-        B0 = fmaf(Tf, bg0, B0); B1 = fmaf(Tf, bg1, B1); B2 = fmaf(Tf, bg2, B2);
     } else if (T_final_in) {
-        if (tc.inside) {
-            T = T_final_in[vt.pix_base[v] + pix];
-            lastc = min(last_in[vt.pix_base[v] + pix], n_items);
-        }
-        B0 = T * bg0; B1 = T * bg1; B2 = T * bg2;
+        if (tc.in0) { p0.T = T_final_in[vt.pix_base[v] + pix0]; p0.last = min(last_in[vt.pix_base[v] + pix0], n_items); }
+        if (tc.in1) { p1.T = T_final_in[vt.pix_base[v] + pix1]; p1.last = min(last_in[vt.pix_base[v] + pix1], n_items); }
+        p0.B0 = p0.T * bg0; p0.B1 = p0.T * bg1; p0.B2 = p0.T * bg2;
+        p1.B0 = p1.T * bg0; p1.B1 = p1.T * bg1; p1.B2 = p1.T * bg2;
     } else {
         // recompute the forward transmittance and the last composited position
-        bool done = !tc.inside;
+        bool d0 = !tc.in0, d1 = !tc.in1;
         for (uint32_t b0 = it.s0; b0 < it.s1; b0 += kRT) {
-            if (__syncthreads_count(done) == kRT) break;
-            stage(S, rec, vals, b0 + threadIdx.x, b0 + threadIdx.x < it.s1, cap_cand, st, 52, false);
+            if (__syncthreads_count(d0 && d1) == kRThreads) break;
+            stage(S, tid, rec, vals, b0 + tid, b0 + tid < it.s1, cap_cand, st, 52, false);
+            stage(S, tid + kRThreads, rec, vals, b0 + tid + kRThreads, b0 + tid + kRThreads < it.s1, cap_cand, st, 52,
+                  false);
             __syncthreads();
             const int n = (int)min((uint32_t)kRT, it.s1 - b0);
-            if (!done) {
-                for (int j = 0; j < n; ++j) {
-                    const float4 a = S.a[j];
-                    const float4 bb = S.b[j];
-                    float dx, dy;
-                    const float power = splat_power(a, bb.x, fpx, fpy, &dx, &dy);
-                    if (power > 0.f) continue;
-                    const float alpha = fminf(kAlphaMax, __fmul_rn(bb.y, splat_gauss(power)));
-                    if (alpha < kAlphaMin) continue;
-                    const float Tn = __fmul_rn(T, 1.f - alpha);
-                    if (Tn < kTMin) { done = true; break; }
-                    T = Tn;
-                    lastc = (int)(b0 - it.s0) + j + 1;
-                }
-            }
-        }
-        B0 = T * bg0; B1 = T * bg1; B2 = T * bg2;
-    }
-    __syncthreads();
-    atomicMax(&s_maxlast, lastc);
-    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-    if (tc.inside) {
-        const float *dimg = d_image + 3 * vt.pix_base[v];
-        g0 = dimg[pix]; g1 = dimg[W * H + pix]; g2 = dimg[2 * W * H + pix];
-    }
-    __syncthreads();
-    const int maxlast = min(s_maxlast, n_items);
-    const int lane = threadIdx.x & 31;
-    // back to front over chunk positions [0, maxlast)
-    for (int hi = maxlast; hi > 0; hi -= kRT) {
-        const int lo = max(0, hi - kRT);
-        __syncthreads();
-        {
-            const int p = hi - 1 - (int)threadIdx.x;   // smem slot j <-> position hi-1-j
-            stage(S, rec, vals, it.s0 + (uint32_t)max(p, 0), p >= lo, cap_cand, st, 53, true);
-        }
-        __syncthreads();
-        const int n = hi - lo;
-        for (int j = 0; j < n; ++j) {
-            const int p = hi - 1 - j;
-            float gmx = 0.f, gmy = 0.f, gca = 0.f, gcb = 0.f, gcc = 0.f, gop = 0.f, gr = 0.f, gg = 0.f, gb = 0.f;
-            bool contrib = false;
-            if (p < lastc) {
+            const int base = (int)(b0 - it.s0);
+            const int cnt = warp_list(S, n, tc.x0, tc.y0);
+            for (int li = 0; li < cnt; ++li) {
+                const int j = S.wl[warp][li];
                 const float4 a = S.a[j];
                 const float4 bb = S.b[j];
                 float dx, dy;
-                const float power = splat_power(a, bb.x, fpx, fpy, &dx, &dy);
-                if (power <= 0.f) {
-                    const float G = splat_gauss(power);
-                    const float ag = __fmul_rn(bb.y, G);
-                    const float alpha = fminf(kAlphaMax, ag);
-                    if (alpha >= kAlphaMin) {
-                        contrib = true;
-                        const float om = 1.f - alpha;
-                        T = T / om;                      // transmittance in front of this splat
-                        const float w = alpha * T;
-                        gr = w * g0; gg = w * g1; gb = w * g2;
-                        const float cr = bb.z, cg = bb.w, cbl = S.c[j];
-                        const float dal = g0 * (cr * T - B0 / om) + g1 * (cg * T - B1 / om) +
-                                          g2 * (cbl * T - B2 / om);
-                        B0 = fmaf(cr, w, B0); B1 = fmaf(cg, w, B1); B2 = fmaf(cbl, w, B2);
-                        if (ag < kAlphaMax) {
-                            gop = dal * G;
-                            const float dp = dal * alpha;
-                            gmx = -dp * (a.z * dx + a.w * dy);
-                            gmy = -dp * (bb.x * dy + a.w * dx);
-                            gca = -0.5f * dp * dx * dx;
-                            gcb = -dp * dx * dy;
-                            gcc = -0.5f * dp * dy * dy;
+                if (!d0) {
+                    const float q = splat_q(a, bb.x, fpx, fy0, &dx, &dy);
+                    if (q <= 0.f) {
+                        const float alpha = fminf(kAlphaMax, splat_alpha(q, bb.y));
+                        if (alpha >= kAlphaMin) {
+                            const float Tn = __fmul_rn(p0.T, 1.f - alpha);
+                            if (Tn < kTMin) d0 = true;
+                            else { p0.T = Tn; p0.last = base + j + 1; }
+                        }
+                    }
+                }
+                if (!d1) {
+                    const float q = splat_q(a, bb.x, fpx, fy1, &dx, &dy);
+                    if (q <= 0.f) {
+                        const float alpha = fminf(kAlphaMax, splat_alpha(q, bb.y));
+                        if (alpha >= kAlphaMin) {
+                            const float Tn = __fmul_rn(p1.T, 1.f - alpha);
+                            if (Tn < kTMin) d1 = true;
+                            else { p1.T = Tn; p1.last = base + j + 1; }
                         }
                     }
                 }
             }
+        }
+        p0.B0 = p0.T * bg0; p0.B1 = p0.T * bg1; p0.B2 = p0.T * bg2;
+        p1.B0 = p1.T * bg0; p1.B1 = p1.T * bg1; p1.B2 = p1.T * bg2;
+    }
+    __syncthreads();
+    atomicMax(&s_maxlast, max(p0.last, p1.last));
+    p0.g0 = p0.g1 = p0.g2 = p1.g0 = p1.g1 = p1.g2 = 0.f;
+    {
+        const float *dimg = d_image + 3 * vt.pix_base[v];
+        if (tc.in0) { p0.g0 = dimg[pix0]; p0.g1 = dimg[W * H + pix0]; p0.g2 = dimg[2 * W * H + pix0]; }
+        if (tc.in1) { p1.g0 = dimg[pix1]; p1.g1 = dimg[W * H + pix1]; p1.g2 = dimg[2 * W * H + pix1]; }
+    }
+    __syncthreads();
+    const int maxlast = min(s_maxlast, n_items);
+    // back to front over chunk positions [0, maxlast)
+    for (int hi = maxlast; hi > 0; hi -= kRT) {
+        const int lo = max(0, hi - kRT);
+        __syncthreads();
+        {   // slot j <-> position hi - 1 - j
+            const int pa = hi - 1 - tid, pb = hi - 1 - (tid + kRThreads);
+            stage(S, tid, rec, vals, it.s0 + (uint32_t)max(pa, 0), pa >= lo, cap_cand, st, 53, true);
+            stage(S, tid + kRThreads, rec, vals, it.s0 + (uint32_t)max(pb, 0), pb >= lo, cap_cand, st, 53, true);
+        }
+        __syncthreads();
+        const int cnt = warp_list(S, hi - lo, tc.x0, tc.y0);
+        for (int li = 0; li < cnt; ++li) {
+            const int j = S.wl[warp][li];
+            const int p = hi - 1 - j;
+            float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            bool contrib = false;
+            if (p < p0.last || p < p1.last) {
+                const float4 a = S.a[j];
+                const float4 bb = S.b[j];
+                const float cb = S.c[j], io = S.io[j];
+                if (p < p0.last) contrib |= bwd_step(p0, a, bb, cb, io, fpx, fy0, acc);
+                if (p < p1.last) contrib |= bwd_step(p1, a, bb, cb, io, fpx, fy1, acc);
+            }
             if (__any_sync(0xffffffffu, contrib)) {
-                gmx = warp_sum(gmx); gmy = warp_sum(gmy); gca = warp_sum(gca); gcb = warp_sum(gcb);
-                gcc = warp_sum(gcc); gop = warp_sum(gop); gr = warp_sum(gr); gg = warp_sum(gg); gb = warp_sum(gb);
-                if (lane == 0) {
-                    float *o = sgrad + 9 * (size_t)S.id[j];
-                    atomicAdd(o + 0, gmx); atomicAdd(o + 1, gmy); atomicAdd(o + 2, gca);
-                    atomicAdd(o + 3, gcb); atomicAdd(o + 4, gcc); atomicAdd(o + 5, gop);
-                    atomicAdd(o + 6, gr); atomicAdd(o + 7, gg); atomicAdd(o + 8, gb);
-                }
+                const float t8 = warp_sum8(acc);
+                const float t9 = warp_sum(acc[8]);
+                float *o = sgrad + 9 * (size_t)S.id[j];
+                if ((lane & 3) == 0) atomicAdd(o + (((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1)), t8);
+                if (lane == 1) atomicAdd(o + 8, t9);
             }
         }
     }
@@ -323,7 +392,7 @@ int launch_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splat
     const float4 *rec = reinterpret_cast<const float4 *>(sp->rec);
     if (vt.total_tiles > 0) {
         const RenderPlan plan = render_plan(vt, bins->cap_pairs, L, ws);
-        render_bwd_kernel<<<plan.max_items, kRT, 0, s>>>(rec, bins->vals, bins->ranges, vt, plan, bg[0], bg[1],
+        render_bwd_kernel<<<plan.max_items, kRThreads, 0, s>>>(rec, bins->vals, bins->ranges, vt, plan, bg[0], bg[1],
                                                           bg[2], d_image, T_final, last, sgrad->g,
                                                           std::min<long long>(sp->cap, cap_cand), st);
         count_launches(1);

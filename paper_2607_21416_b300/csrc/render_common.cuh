@@ -23,23 +23,38 @@
 
 namespace gs {
 
-constexpr int kRT = kTilePix;      // 256 threads per tile / work item
+constexpr int kRT = kTilePix;      // pixels per tile / work item
+constexpr int kRThreads = 128;     // threads per work item: two pixels each (rows y and y + 8)
 constexpr int kStateWords = 6;     // Tprod, Tend, C0, C1, C2, last  (x 256 pixels)
 
-__device__ __forceinline__ float splat_power(float4 a, float cc, float px, float py, float *dx, float *dy)
+// 2^x on the special-function unit (ex2.approx, max relative error ~2^-22).
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// power * log2(e) of a splat record (a = mean x, mean y, A, B; C) at pixel
+// (px, py): (A dx + B dy) dx + C dy^2 with (dx, dy) = mean - pixel.  Explicit
+// rounding so that every pass that re-evaluates a pair decides identically.
+__device__ __forceinline__ float splat_q(float4 a, float C, float px, float py, float *dx, float *dy)
 {
     const float x = __fsub_rn(a.x, px), y = __fsub_rn(a.y, py);
     *dx = x; *dy = y;
-    // -0.5 (ca x^2 + cc y^2) - cb x y
-    const float q = fmaf(a.z, __fmul_rn(x, x), __fmul_rn(cc, __fmul_rn(y, y)));
-    return fmaf(-0.5f, q, -__fmul_rn(a.w, __fmul_rn(x, y)));
+    const float t = fmaf(a.z, x, __fmul_rn(a.w, y));
+    return fmaf(t, x, __fmul_rn(__fmul_rn(C, y), y));
 }
 
-__device__ __forceinline__ float splat_gauss(float power) { return __expf(power); }
+// Unclamped alpha o exp(power) = 2^(q + L).
+__device__ __forceinline__ float splat_alpha(float q, float L) { return ex2_approx(__fadd_rn(q, L)); }
 
+// A thread owns pixels (px, py) and (px, py + 1) of its tile, with px = x0 +
+// (tid & 15), py = y0 + 2 (tid >> 4): tile-local pixel ids pid0 = (py - y0) *
+// 16 + (px - x0) and pid0 + 16.  Warp w covers the 16x4 block of rows 4w..4w+3.
 struct TileCoord {
-    int v, px, py;
-    bool inside;
+    int v, x0, y0, px, py, pid0;
+    bool in0, in1;
 };
 __device__ __forceinline__ TileCoord tile_coord(const ViewTable &vt, int t)
 {
@@ -47,9 +62,13 @@ __device__ __forceinline__ TileCoord tile_coord(const ViewTable &vt, int t)
     c.v = view_of_tile(vt, t);
     const int local = t - vt.tile_base[c.v];
     const int tx = local % vt.TX[c.v], ty = local / vt.TX[c.v];
-    c.px = tx * kTile + (threadIdx.x & (kTile - 1));
-    c.py = ty * kTile + (threadIdx.x >> 4);
-    c.inside = c.px < vt.W[c.v] && c.py < vt.H[c.v];
+    c.x0 = tx * kTile;
+    c.y0 = ty * kTile;
+    c.px = c.x0 + (threadIdx.x & (kTile - 1));
+    c.py = c.y0 + 2 * (threadIdx.x >> 4);
+    c.pid0 = 2 * (threadIdx.x >> 4) * kTile + (threadIdx.x & (kTile - 1));
+    c.in0 = c.px < vt.W[c.v] && c.py < vt.H[c.v];
+    c.in1 = c.px < vt.W[c.v] && c.py + 1 < vt.H[c.v];
     return c;
 }
 
@@ -89,33 +108,87 @@ __device__ __forceinline__ float *state_plane(float *state, int item, int plane)
     return state + ((size_t)item * kStateWords + plane) * kRT;
 }
 
-// Transmittance in front of chunk k: the product of the earlier chunks' Tprod.
-__device__ __forceinline__ float chunk_T0(const float *state, const Item &it)
+// Transmittance in front of chunk k at tile pixel `pix`: the product of the
+// earlier chunks' Tprod.
+__device__ __forceinline__ float chunk_T0(const float *state, const Item &it, int pix)
 {
     float T = 1.f;
-    for (int j = 0; j < it.k; ++j) T = __fmul_rn(T, state_plane(const_cast<float *>(state), it.base + j, 0)[threadIdx.x]);
+    for (int j = 0; j < it.k; ++j) T = __fmul_rn(T, state_plane(const_cast<float *>(state), it.base + j, 0)[pix]);
     return T;
 }
 
-// Stage list positions [b0, b0 + n) of vals into shared memory records.
+// Shared-memory records of one batch of kRT list positions.
 struct Staged {
-    float4 a[kRT];    // mean x, mean y, conic a, conic b
-    float4 b[kRT];    // conic c, opacity, r, g
+    float4 a[kRT];    // mean x, mean y, A, B
+    float4 b[kRT];    // C, L, r, g
+    float4 box[kRT];  // x0, x1, y0, y1: bounding box of the splat's alpha >= 1/255 region
     float c[kRT];     // b
+    float io[kRT];    // 1 / opacity (backward only)
     uint32_t id[kRT];
+    uint8_t wl[kRThreads / 32][kRT];   // per warp: staged slots whose box meets its 16x4 block
+    int wn[kRThreads / 32];
 };
 
-__device__ __forceinline__ void stage(Staged &S, const float4 *__restrict__ rec,
+// Bounding box of {pixel : 2^(q + L) >= 1/255}, an ellipse since q is a
+// negative-definite quadratic form in (dx, dy): with Q = -[[A, B/2], [B/2, C]]
+// and s = log2(255) + L > 0, the region is d^T Q d <= s and its half-extents
+// are sqrt(s (Q^-1)_xx), sqrt(s (Q^-1)_yy).  The box is widened by 0.1 % + 0.01
+// px, far beyond the FP32 error of q, so every pixel outside it also fails the
+// alpha test as the kernels evaluate it: skipping those pairs is exact.
+__device__ __forceinline__ float4 alpha_box(float4 a, float4 b)
+{
+    const float s = b.y + 7.994353436858858f;   // L + log2(255)
+    if (!(s > 0.f)) return make_float4(1e30f, -1e30f, 1e30f, -1e30f);   // opacity < 1/255: empty
+    const float det = a.z * b.x - 0.25f * a.w * a.w;                     // det Q = AC - B^2/4
+    if (!(det > 0.f)) return make_float4(-1e30f, 1e30f, -1e30f, 1e30f);  // degenerate: no culling
+    const float hx = sqrtf(s * (-b.x) / det) * 1.001f + 0.01f;
+    const float hy = sqrtf(s * (-a.z) / det) * 1.001f + 0.01f;
+    return make_float4(a.x - hx, a.x + hx, a.y - hy, a.y + hy);
+}
+
+// Stages list position `pos` into slot `slot` (when valid).
+__device__ __forceinline__ void stage(Staged &S, int slot, const float4 *__restrict__ rec,
                                       const uint32_t *__restrict__ vals, uint32_t pos, bool valid,
                                       long long cap_cand, const gs_status *st, int site, bool with_colour)
 {
     if (!valid) return;
     uint32_t id = vals[pos];
     if (!idx_ok(st, (long long)id, cap_cand, site)) id = 0;
-    S.id[threadIdx.x] = id;
-    S.a[threadIdx.x] = __ldg(&rec[3 * (size_t)id]);
-    S.b[threadIdx.x] = __ldg(&rec[3 * (size_t)id + 1]);
-    if (with_colour) S.c[threadIdx.x] = __ldg(&rec[3 * (size_t)id + 2]).x;
+    S.id[slot] = id;
+    const float4 a = __ldg(&rec[3 * (size_t)id]);
+    const float4 b = __ldg(&rec[3 * (size_t)id + 1]);
+    S.a[slot] = a;
+    S.b[slot] = b;
+    S.box[slot] = alpha_box(a, b);
+    if (with_colour) {
+        S.c[slot] = __ldg(&rec[3 * (size_t)id + 2]).x;
+        S.io[slot] = exp2f(-b.y);
+    }
+}
+
+// Each warp lists, in slot order, the staged slots [0, n) whose alpha box meets
+// its 16x4 pixel block (call after the batch is staged and synchronised).
+__device__ __forceinline__ int warp_list(Staged &S, int n, int x0, int y0)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float bx0 = (float)x0, bx1 = (float)(x0 + kTile - 1);
+    const float by0 = (float)(y0 + 4 * warp), by1 = by0 + 3.f;
+    unsigned lt;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+    int cnt = 0;
+    for (int base = 0; base < n; base += 32) {
+        const int j = base + lane;
+        bool hit = false;
+        if (j < n) {
+            const float4 b = S.box[j];
+            hit = b.x <= bx1 && b.y >= bx0 && b.z <= by1 && b.w >= by0;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (hit) S.wl[warp][cnt + __popc(m & lt)] = (uint8_t)j;
+        cnt += __popc(m);
+    }
+    __syncwarp();
+    return cnt;
 }
 
 struct RenderPlan {

@@ -1,7 +1,10 @@
 // render_fwd.cu -- front-to-back tile compositing (Eq. 1) over chunked work
 // items, and the L1 term of Eq. 3.
 //
-// Kernels (all views in every launch, tiles numbered view-major):
+// Kernels (all views in every launch, tiles numbered view-major; 128 threads
+// per work item, each owning pixels (x, y) and (x, y + 1) of the 16x16 tile, so
+// every splat read from shared memory serves two evaluations; each warp walks
+// only the splats whose alpha >= 1/255 box meets its 16x4 block):
 //   plan_kernel     per-tile chunk counts -> item_base (one CTA scan)
 //   prod_kernel     Tprod of every chunk of a multi-chunk tile
 //   chunk_kernel    compositing of every item; single-chunk tiles write the
@@ -65,152 +68,240 @@ __global__ void __launch_bounds__(1024) plan_kernel(const uint32_t *__restrict__
     }
 }
 
+// Front-to-back state of one pixel.
+struct PixFwd {
+    float T, C0, C1, C2;
+    int last;      // position of the last composited splat (1-based, in the chunk)
+    int stop;      // position of the splat that stopped the pixel (0: not stopped)
+    bool done;
+};
+
+// Eq. 1 step of one pixel over a staged splat at chunk position pos (1-based).
+__device__ __forceinline__ void fwd_step(PixFwd &ps, const float4 a, const float4 bb, float cb, float px, float py,
+                                         int pos)
+{
+    float dx, dy;
+    const float q = splat_q(a, bb.x, px, py, &dx, &dy);
+    if (q > 0.f) return;
+    const float alpha = fminf(kAlphaMax, splat_alpha(q, bb.y));
+    if (alpha < kAlphaMin) return;
+    const float Tn = __fmul_rn(ps.T, 1.f - alpha);
+    if (Tn < kTMin) { ps.done = true; ps.stop = pos; return; }
+    const float w = __fmul_rn(alpha, ps.T);
+    ps.C0 = fmaf(bb.z, w, ps.C0);
+    ps.C1 = fmaf(bb.w, w, ps.C1);
+    ps.C2 = fmaf(cb, w, ps.C2);
+    ps.T = Tn;
+    ps.last = pos;
+}
+
 // Transmittance product of one chunk (no stop rule; early exit below 1e-4).
-__global__ void __launch_bounds__(kRT) prod_kernel(const float4 *__restrict__ rec, const uint32_t *__restrict__ vals,
-                                                   const uint32_t *__restrict__ ranges, ViewTable vt,
-                                                   RenderPlan plan, long long cap_cand, const gs_status *st)
+// The last chunk of a tile needs none.
+__global__ void __launch_bounds__(kRThreads) prod_kernel(const float4 *__restrict__ rec,
+                                                         const uint32_t *__restrict__ vals,
+                                                         const uint32_t *__restrict__ ranges, ViewTable vt,
+                                                         RenderPlan plan, long long cap_cand, const gs_status *st)
 {
     if (has_error(st)) return;
     Item it;
-    if (!item_of(blockIdx.x, plan.item_base, vt.total_tiles, ranges, plan.L, &it) || it.nk == 1) return;
+    if (!item_of(blockIdx.x, plan.item_base, vt.total_tiles, ranges, plan.L, &it) || it.nk == 1 ||
+        it.k == it.nk - 1)
+        return;
     __shared__ Staged S;
     const TileCoord tc = tile_coord(vt, it.t);
-    const float fpx = (float)tc.px, fpy = (float)tc.py;
-    float T = 1.f;
-    bool done = !tc.inside;
+    const float fpx = (float)tc.px, fy0 = (float)tc.py, fy1 = (float)(tc.py + 1);
+    float T0 = 1.f, T1 = 1.f;
+    bool d0 = !tc.in0, d1 = !tc.in1;
+    const int tid = threadIdx.x, warp = tid >> 5;
     for (uint32_t b0 = it.s0; b0 < it.s1; b0 += kRT) {
-        if (__syncthreads_count(done) == kRT) break;
-        stage(S, rec, vals, b0 + threadIdx.x, b0 + threadIdx.x < it.s1, cap_cand, st, 43, false);
+        if (__syncthreads_count(d0 && d1) == kRThreads) break;
+        stage(S, tid, rec, vals, b0 + tid, b0 + tid < it.s1, cap_cand, st, 43, false);
+        stage(S, tid + kRThreads, rec, vals, b0 + tid + kRThreads, b0 + tid + kRThreads < it.s1, cap_cand, st, 43,
+              false);
         __syncthreads();
         const int n = (int)min((uint32_t)kRT, it.s1 - b0);
-        if (!done) {
-            for (int j = 0; j < n; ++j) {
-                const float4 a = S.a[j];
-                const float4 bb = S.b[j];
-                float dx, dy;
-                const float power = splat_power(a, bb.x, fpx, fpy, &dx, &dy);
-                if (power > 0.f) continue;
-                const float alpha = fminf(kAlphaMax, __fmul_rn(bb.y, splat_gauss(power)));
-                if (alpha < kAlphaMin) continue;
-                T = __fmul_rn(T, 1.f - alpha);
-                if (T < kTMin) { done = true; break; }
+        const int cnt = warp_list(S, n, tc.x0, tc.y0);
+        for (int li = 0; li < cnt; ++li) {
+            const int j = S.wl[warp][li];
+            const float4 a = S.a[j];
+            const float4 bb = S.b[j];
+            float dx, dy;
+            if (!d0) {
+                const float q = splat_q(a, bb.x, fpx, fy0, &dx, &dy);
+                if (q <= 0.f) {
+                    const float alpha = fminf(kAlphaMax, splat_alpha(q, bb.y));
+                    if (alpha >= kAlphaMin) {
+                        T0 = __fmul_rn(T0, 1.f - alpha);
+                        d0 = T0 < kTMin;
+                    }
+                }
+            }
+            if (!d1) {
+                const float q = splat_q(a, bb.x, fpx, fy1, &dx, &dy);
+                if (q <= 0.f) {
+                    const float alpha = fminf(kAlphaMax, splat_alpha(q, bb.y));
+                    if (alpha >= kAlphaMin) {
+                        T1 = __fmul_rn(T1, 1.f - alpha);
+                        d1 = T1 < kTMin;
+                    }
+                }
             }
         }
     }
-    state_plane(plan.state, it.base + it.k, 0)[threadIdx.x] = T;
+    float *pl = state_plane(plan.state, it.base + it.k, 0);
+    pl[tc.pid0] = T0;
+    pl[tc.pid0 + kTile] = T1;
 }
 
+__device__ __forceinline__ void write_pixel_or_state(const PixFwd &ps, bool inside, bool multi, int item, int pix,
+                                                     const RenderPlan &plan, const ViewTable &vt, int v, int px,
+                                                     int py, float bg0, float bg1, float bg2, float *image,
+                                                     float *T_final, int32_t *last)
+{
+    if (multi) {
+        state_plane(plan.state, item, 1)[pix] = ps.T;
+        state_plane(plan.state, item, 2)[pix] = ps.C0;
+        state_plane(plan.state, item, 3)[pix] = ps.C1;
+        state_plane(plan.state, item, 4)[pix] = ps.C2;
+        reinterpret_cast<int *>(state_plane(plan.state, item, 5))[pix] = ps.last;
+        return;
+    }
+    if (!inside) return;
+    const long long W = vt.W[v], H = vt.H[v];
+    const long long p = (long long)py * W + px;
+    float *img = image + 3 * vt.pix_base[v];
+    img[p] = fmaf(ps.T, bg0, ps.C0);
+    img[W * H + p] = fmaf(ps.T, bg1, ps.C1);
+    img[2 * W * H + p] = fmaf(ps.T, bg2, ps.C2);
+    if (T_final) T_final[vt.pix_base[v] + p] = ps.T;
+    if (last) last[vt.pix_base[v] + p] = ps.last;
+}
+
+// Compositing of one work item.  Each warp walks only the staged splats whose
+// alpha box meets its pixel block.  With COUNT, the pairs the method examines
+// (every list position up to the stop) and the pairs composited are counted.
 template <bool COUNT>
-__global__ void __launch_bounds__(kRT) chunk_kernel(const float4 *__restrict__ rec, const uint32_t *__restrict__ vals,
-                                                    const uint32_t *__restrict__ ranges, ViewTable vt, RenderPlan plan,
-                                                    float bg0, float bg1, float bg2, float *__restrict__ image,
-                                                    float *__restrict__ T_final, int32_t *__restrict__ last,
-                                                    unsigned long long *__restrict__ n_eval, long long cap_cand,
-                                                    const gs_status *st)
+__global__ void __launch_bounds__(kRThreads) chunk_kernel(const float4 *__restrict__ rec,
+                                                          const uint32_t *__restrict__ vals,
+                                                          const uint32_t *__restrict__ ranges, ViewTable vt,
+                                                          RenderPlan plan, float bg0, float bg1, float bg2,
+                                                          float *__restrict__ image, float *__restrict__ T_final,
+                                                          int32_t *__restrict__ last,
+                                                          unsigned long long *__restrict__ n_eval,
+                                                          long long cap_cand, const gs_status *st)
 {
     if (has_error(st)) return;
     Item it;
     if (!item_of(blockIdx.x, plan.item_base, vt.total_tiles, ranges, plan.L, &it)) return;
     __shared__ Staged S;
+    const int tid = threadIdx.x, warp = tid >> 5;
     const TileCoord tc = tile_coord(vt, it.t);
-    const float fpx = (float)tc.px, fpy = (float)tc.py;
+    const float fpx = (float)tc.px, fy0 = (float)tc.py, fy1 = (float)(tc.py + 1);
     const bool multi = it.nk > 1;
-    const float T0 = multi ? chunk_T0(plan.state, it) : 1.f;
-    float T = T0, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    int lastc = 0;
-    bool done = !tc.inside || T0 < kTMin;
-    unsigned long long nev = 0, ncomp = 0;
+    PixFwd p0, p1;
+    p0.T = multi ? chunk_T0(plan.state, it, tc.pid0) : 1.f;
+    p1.T = multi ? chunk_T0(plan.state, it, tc.pid0 + kTile) : 1.f;
+    p0.C0 = p0.C1 = p0.C2 = p1.C0 = p1.C1 = p1.C2 = 0.f;
+    p0.last = p1.last = p0.stop = p1.stop = 0;
+    p0.done = !tc.in0 || p0.T < kTMin;
+    p1.done = !tc.in1 || p1.T < kTMin;
+    const bool act0 = !p0.done, act1 = !p1.done;
     for (uint32_t b0 = it.s0; b0 < it.s1; b0 += kRT) {
-        if (__syncthreads_count(done) == kRT) break;
-        stage(S, rec, vals, b0 + threadIdx.x, b0 + threadIdx.x < it.s1, cap_cand, st, 42, true);
+        if (__syncthreads_count(p0.done && p1.done) == kRThreads) break;
+        stage(S, tid, rec, vals, b0 + tid, b0 + tid < it.s1, cap_cand, st, 42, true);
+        stage(S, tid + kRThreads, rec, vals, b0 + tid + kRThreads, b0 + tid + kRThreads < it.s1, cap_cand, st, 42,
+              true);
         __syncthreads();
         const int n = (int)min((uint32_t)kRT, it.s1 - b0);
-        if (!done) {
-            for (int j = 0; j < n; ++j) {
-                if (COUNT) ++nev;
-                const float4 a = S.a[j];
-                const float4 bb = S.b[j];
-                float dx, dy;
-                const float power = splat_power(a, bb.x, fpx, fpy, &dx, &dy);
-                if (power > 0.f) continue;
-                const float alpha = fminf(kAlphaMax, __fmul_rn(bb.y, splat_gauss(power)));
-                if (alpha < kAlphaMin) continue;
-                const float Tn = __fmul_rn(T, 1.f - alpha);
-                if (Tn < kTMin) { done = true; break; }
-                const float w = __fmul_rn(alpha, T);
-                C0 = fmaf(bb.z, w, C0);
-                C1 = fmaf(bb.w, w, C1);
-                C2 = fmaf(S.c[j], w, C2);
-                T = Tn;
-                lastc = (int)(b0 - it.s0) + j + 1;
-                if (COUNT) ++ncomp;
-            }
+        const int base = (int)(b0 - it.s0);
+        const int cnt = warp_list(S, n, tc.x0, tc.y0);
+        for (int li = 0; li < cnt; ++li) {
+            const int j = S.wl[warp][li];
+            const float4 a = S.a[j];
+            const float4 bb = S.b[j];
+            const float cb = S.c[j];
+            if (!p0.done) fwd_step(p0, a, bb, cb, fpx, fy0, base + j + 1);
+            if (!p1.done) fwd_step(p1, a, bb, cb, fpx, fy1, base + j + 1);
         }
     }
     if (COUNT) {
+        const int n_items = (int)(it.s1 - it.s0);
+        unsigned long long nev = 0, ncomp = 0;
+        if (act0) nev += p0.stop ? p0.stop : n_items;
+        if (act1) nev += p1.stop ? p1.stop : n_items;
+        // composited pairs: recount over the list (cheap next to the composite itself)
+        for (int pass = 0; pass < 2; ++pass) {
+            const PixFwd &ps = pass ? p1 : p0;
+            if (!(pass ? act1 : act0)) continue;
+            float T = multi ? chunk_T0(plan.state, it, tc.pid0 + pass * kTile) : 1.f;
+            const float fy = pass ? fy1 : fy0;
+            for (int pos = 0; pos < ps.last; ++pos) {
+                uint32_t id = vals[it.s0 + pos];
+                if (!idx_ok(st, (long long)id, cap_cand, 44)) break;
+                const float4 a = __ldg(&rec[3 * (size_t)id]);
+                const float4 bb = __ldg(&rec[3 * (size_t)id + 1]);
+                float dx, dy;
+                const float q = splat_q(a, bb.x, fpx, fy, &dx, &dy);
+                if (q > 0.f) continue;
+                const float alpha = fminf(kAlphaMax, splat_alpha(q, bb.y));
+                if (alpha < kAlphaMin) continue;
+                T = __fmul_rn(T, 1.f - alpha);
+                ++ncomp;
+            }
+        }
         for (int o = 16; o > 0; o >>= 1) {
             nev += __shfl_down_sync(0xffffffffu, nev, o);
             ncomp += __shfl_down_sync(0xffffffffu, ncomp, o);
         }
-        if ((threadIdx.x & 31) == 0 && nev) atomicAdd(n_eval, nev);
-        if ((threadIdx.x & 31) == 0 && ncomp) atomicAdd(n_eval + 1, ncomp);
+        if ((tid & 31) == 0 && nev) atomicAdd(n_eval, nev);
+        if ((tid & 31) == 0 && ncomp) atomicAdd(n_eval + 1, ncomp);
     }
-    if (multi) {
-        const int item = it.base + it.k;
-        state_plane(plan.state, item, 1)[threadIdx.x] = T;
-        state_plane(plan.state, item, 2)[threadIdx.x] = C0;
-        state_plane(plan.state, item, 3)[threadIdx.x] = C1;
-        state_plane(plan.state, item, 4)[threadIdx.x] = C2;
-        reinterpret_cast<int *>(state_plane(plan.state, item, 5))[threadIdx.x] = lastc;
-        return;
-    }
-    if (!tc.inside) return;
-    const int v = tc.v;
-    const long long W = vt.W[v], H = vt.H[v];
-    const long long pix = (long long)tc.py * W + tc.px;
-    float *img = image + 3 * vt.pix_base[v];
-    img[pix] = fmaf(T, bg0, C0);
-    img[W * H + pix] = fmaf(T, bg1, C1);
-    img[2 * W * H + pix] = fmaf(T, bg2, C2);
-    if (T_final) T_final[vt.pix_base[v] + pix] = T;
-    if (last) last[vt.pix_base[v] + pix] = lastc;
+    const int item = it.base + it.k;
+    write_pixel_or_state(p0, tc.in0, multi, item, tc.pid0, plan, vt, tc.v, tc.px, tc.py, bg0, bg1, bg2, image,
+                         T_final, last);
+    write_pixel_or_state(p1, tc.in1, multi, item, tc.pid0 + kTile, plan, vt, tc.v, tc.px, tc.py + 1, bg0, bg1, bg2,
+                         image, T_final, last);
 }
 
 // Image of a multi-chunk tile: sum of the active chunks' colour plus the final
 // transmittance (that of the last active chunk) times the background.
-__global__ void __launch_bounds__(kRT) combine_kernel(const uint32_t *__restrict__ ranges, ViewTable vt,
-                                                      RenderPlan plan, float bg0, float bg1, float bg2,
-                                                      float *__restrict__ image, float *__restrict__ T_final,
-                                                      int32_t *__restrict__ last, const gs_status *st)
+__global__ void __launch_bounds__(kRThreads) combine_kernel(const uint32_t *__restrict__ ranges, ViewTable vt,
+                                                            RenderPlan plan, float bg0, float bg1, float bg2,
+                                                            float *__restrict__ image, float *__restrict__ T_final,
+                                                            int32_t *__restrict__ last, const gs_status *st)
 {
     if (has_error(st)) return;
     const int t = blockIdx.x;
     const int base = plan.item_base[t], nk = plan.item_base[t + 1] - base;
     if (nk <= 1) return;
     const TileCoord tc = tile_coord(vt, t);
-    if (!tc.inside) return;
-    float T0 = 1.f, Tf = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    int lastc = 0;
-    for (int j = 0; j < nk; ++j) {
-        if (!(T0 >= kTMin)) break;
-        const int item = base + j;
-        C0 += state_plane(plan.state, item, 2)[threadIdx.x];
-        C1 += state_plane(plan.state, item, 3)[threadIdx.x];
-        C2 += state_plane(plan.state, item, 4)[threadIdx.x];
-        Tf = state_plane(plan.state, item, 1)[threadIdx.x];
-        const int lj = reinterpret_cast<const int *>(state_plane(plan.state, item, 5))[threadIdx.x];
-        if (lj > 0) lastc = j * plan.L + lj;
-        T0 = __fmul_rn(T0, state_plane(plan.state, item, 0)[threadIdx.x]);
+    for (int half = 0; half < 2; ++half) {
+        const bool inside = half ? tc.in1 : tc.in0;
+        if (!inside) continue;
+        const int pix = tc.pid0 + half * kTile;
+        float T0 = 1.f, Tf = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+        int lastc = 0;
+        for (int j = 0; j < nk; ++j) {
+            if (!(T0 >= kTMin)) break;
+            const int item = base + j;
+            C0 += state_plane(plan.state, item, 2)[pix];
+            C1 += state_plane(plan.state, item, 3)[pix];
+            C2 += state_plane(plan.state, item, 4)[pix];
+            Tf = state_plane(plan.state, item, 1)[pix];
+            const int lj = reinterpret_cast<const int *>(state_plane(plan.state, item, 5))[pix];
+            if (lj > 0) lastc = j * plan.L + lj;
+            if (j < nk - 1) T0 = __fmul_rn(T0, state_plane(plan.state, item, 0)[pix]);
+        }
+        const int v = tc.v;
+        const long long W = vt.W[v], H = vt.H[v];
+        const long long p = (long long)(tc.py + half) * W + tc.px;
+        float *img = image + 3 * vt.pix_base[v];
+        img[p] = fmaf(Tf, bg0, C0);
+        img[W * H + p] = fmaf(Tf, bg1, C1);
+        img[2 * W * H + p] = fmaf(Tf, bg2, C2);
+        if (T_final) T_final[vt.pix_base[v] + p] = Tf;
+        if (last) last[vt.pix_base[v] + p] = lastc;
     }
-    const int v = tc.v;
-    const long long W = vt.W[v], H = vt.H[v];
-    const long long pix = (long long)tc.py * W + tc.px;
-    float *img = image + 3 * vt.pix_base[v];
-    img[pix] = fmaf(Tf, bg0, C0);
-    img[W * H + pix] = fmaf(Tf, bg1, C1);
-    img[2 * W * H + pix] = fmaf(Tf, bg2, C2);
-    if (T_final) T_final[vt.pix_base[v] + pix] = Tf;
-    if (last) last[vt.pix_base[v] + pix] = lastc;
 }
 
 // ------------------------------------------------------------------- L1
@@ -264,17 +355,17 @@ int launch_render_fwd(const gs_splats *sp, const gs_bins *bins, const ViewTable 
     const RenderPlan plan = render_plan(vt, bins->cap_pairs, L, ws);
     plan_kernel<<<1, 1024, 0, s>>>(bins->ranges, vt.total_tiles, L, plan.max_items,
                                    const_cast<int32_t *>(plan.item_base), st);
-    prod_kernel<<<plan.max_items, kRT, 0, s>>>(rec, bins->vals, bins->ranges, vt, plan, sp->cap, st);
+    prod_kernel<<<plan.max_items, kRThreads, 0, s>>>(rec, bins->vals, bins->ranges, vt, plan, sp->cap, st);
     if (n_eval) {
         cudaMemsetAsync(n_eval, 0, 2 * sizeof(long long), s);
-        chunk_kernel<true><<<plan.max_items, kRT, 0, s>>>(rec, bins->vals, bins->ranges, vt, plan, bg[0], bg[1],
+        chunk_kernel<true><<<plan.max_items, kRThreads, 0, s>>>(rec, bins->vals, bins->ranges, vt, plan, bg[0], bg[1],
                                                           bg[2], image, T_final, last,
                                                           reinterpret_cast<unsigned long long *>(n_eval), sp->cap, st);
     } else {
-        chunk_kernel<false><<<plan.max_items, kRT, 0, s>>>(rec, bins->vals, bins->ranges, vt, plan, bg[0], bg[1],
+        chunk_kernel<false><<<plan.max_items, kRThreads, 0, s>>>(rec, bins->vals, bins->ranges, vt, plan, bg[0], bg[1],
                                                            bg[2], image, T_final, last, nullptr, sp->cap, st);
     }
-    combine_kernel<<<vt.total_tiles, kRT, 0, s>>>(bins->ranges, vt, plan, bg[0], bg[1], bg[2], image, T_final,
+    combine_kernel<<<vt.total_tiles, kRThreads, 0, s>>>(bins->ranges, vt, plan, bg[0], bg[1], bg[2], image, T_final,
                                                    last, st);
     count_launches(4);
     return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;

@@ -24,8 +24,14 @@ def pack_records(prj: O.Projected, opacity, colour):
     rec = np.zeros((C_, 12), np.float32)
     ok = prj.tiles > 0
     rec[:, 0:2] = f32(prj.mean2d)
-    rec[:, 2:5] = f32(prj.conic)
-    rec[:, 5] = f32(opacity)
+    # exponent coefficients in base 2 and log2 opacity (the library's record layout)
+    l2e = 1.0 / np.log(2.0)
+    conic = np.asarray(prj.conic, np.float64)
+    rec[:, 2] = f32(-0.5 * l2e * conic[:, 0])
+    rec[:, 3] = f32(-l2e * conic[:, 1])
+    rec[:, 4] = f32(-0.5 * l2e * conic[:, 2])
+    with np.errstate(divide="ignore"):
+        rec[:, 5] = f32(np.log2(np.maximum(np.asarray(opacity, np.float64), 1e-30)))
     rec[:, 6:9] = f32(colour)
     rec[:, 9] = f32(prj.depth)
     rx = (prj.rect[:, 0].astype(np.uint32) | (prj.rect[:, 2].astype(np.uint32) << 16))
@@ -37,9 +43,15 @@ def pack_records(prj: O.Projected, opacity, colour):
 
 
 def rounded_projection(prj: O.Projected, opacity, colour):
-    """The oracle projection with every float rounded to FP32 (as doubles)."""
+    """The oracle projection as the library's FP32 records carry it (as doubles):
+    conic and opacity recovered from the rounded base-2 coefficients."""
     r = lambda a: np.asarray(a, np.float64).astype(np.float32).astype(np.float64)
-    return dict(mean2d=r(prj.mean2d), conic=r(prj.conic), opacity=r(opacity), colour=r(colour),
+    rec, _ = pack_records(prj, opacity, colour)
+    rec = rec.astype(np.float64)
+    l2e = 1.0 / np.log(2.0)
+    conic = np.stack([-2.0 * rec[:, 2] / l2e, -rec[:, 3] / l2e, -2.0 * rec[:, 4] / l2e], 1)
+    op = np.where(np.asarray(opacity) > 0, np.exp2(rec[:, 5]), 0.0)
+    return dict(mean2d=r(prj.mean2d), conic=conic, opacity=op, colour=r(colour),
                 depth_bits=prj.depth_bits, rect=prj.rect, status=prj.status)
 
 

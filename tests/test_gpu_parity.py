@@ -67,9 +67,12 @@ def test_project_matches_oracle(make):
     v = ok & (prj.tiles > 0)
     assert v.sum() > 100
     assert np.allclose(rec[v, 0:2], prj.mean2d[v], rtol=2e-6, atol=2e-5)
+    l2e = 1.0 / np.log(2.0)
+    r64 = rec.astype(np.float64)
+    conic = np.stack([-2.0 * r64[:, 2] / l2e, -r64[:, 3] / l2e, -2.0 * r64[:, 4] / l2e], 1)
     scale = np.max(np.abs(prj.conic[v]), axis=1, keepdims=True)
-    assert np.all(np.abs(rec[v, 2:5] - prj.conic[v]) <= 2e-5 * scale)
-    assert np.allclose(rec[v, 5], s.opacity[v]) and np.allclose(rec[v, 6:9], s.colour[v])
+    assert np.all(np.abs(conic[v] - prj.conic[v]) <= 2e-5 * scale)
+    assert np.allclose(np.exp2(r64[v, 5]), s.opacity[v], rtol=2e-6) and np.allclose(rec[v, 6:9], s.colour[v])
     assert np.allclose(rec[v, 9], prj.depth[v], rtol=1e-6)
     rx = rec[v, 10].view(np.uint32)
     ry = rec[v, 11].view(np.uint32)
