@@ -40,16 +40,6 @@ struct TcShape {
 
 static int up16(int x) { return (x + 15) / 16 * 16; }
 
-// Activations of the BF16 path on the SFU: tanh.approx (max relative error
-// about 2^-11, below the BF16 rounding of the MMA inputs), sigmoid(x) =
-// (1 + tanh(x / 2)) / 2.
-__device__ __forceinline__ float tanh_fast(float x)
-{
-    float y;
-    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float sigmoid_fast(float x) { return fmaf(0.5f, tanh_fast(0.5f * x), 0.5f); }
 
 static TcShape tc_shape(int F, int k, int H)
 {

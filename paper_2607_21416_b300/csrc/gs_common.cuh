@@ -102,6 +102,17 @@ __device__ __forceinline__ Cam load_cam(const gs_camera *__restrict__ cams, int 
 
 __device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }
 
+// SFU activations of the BF16 decoding path: tanh.approx (max relative error
+// about 2^-11, below the BF16 rounding of the MMA inputs) and
+// sigmoid(x) = (1 + tanh(x / 2)) / 2.
+__device__ __forceinline__ float tanh_fast(float x)
+{
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sigmoid_fast(float x) { return fmaf(0.5f, tanh_fast(0.5f * x), 0.5f); }
+
 inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 // Number of SMs of the current device (cached per device).

@@ -10,6 +10,12 @@
 // 128 B and the 8-row-group stride (stride byte offset) is K * 16 B.  One MMA
 // consumes K = 16, i.e. two core matrices along K; k-step s starts s * 256 B in.
 //
+// The same bytes also serve as the transposed (MN-major) operand of another
+// product -- rows of the stored matrix become the reduction index K, its
+// columns the M or N index.  For that use the descriptor takes the stride
+// between 8-row groups (the K direction) as leading byte offset and 128 B
+// (the MN direction) as stride byte offset.
+//
 // Accumulator layout (M = 128, cta_group::1): row i of D is TMEM lane i,
 // column j of D is TMEM column (base + j), one FP32 value per lane and column.
 // Warp w of the CTA may read lanes 32 (w % 4) .. 32 (w % 4) + 31 only.
@@ -42,11 +48,12 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
     return d;
 }
 
-// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
-// K-major, dense, M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, dense,
+// M x N; a_mn / b_mn select an MN-major (transposed) A / B operand.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int a_mn = 0, int b_mn = 0)
 {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(a_mn & 1) << 15) | ((uint32_t)(b_mn & 1) << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 // ---- TMEM allocation (one full warp executes these)
