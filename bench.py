@@ -52,6 +52,9 @@ def parse():
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     p.add_argument("--anchors", type=int, default=200000)
     p.add_argument("--views", type=int, default=8)
+    p.add_argument("--state", default="recompute", choices=["recompute", "store"],
+                   help="per-pixel forward state of single-chunk tiles: recomputed in the backward "
+                        "or written by the forward (8 B per pixel)")
     return p.parse_args()
 
 
@@ -125,8 +128,9 @@ def run_ours(args, rank, world, dist):
     npix = views.total_pixels
 
     # ---- batched path: capacity first (outside capture), then one CUDA graph
+    store = args.state == "store"
     rp = pipeline.RenderPass(views, anchors, cap_rows=int(1.2 * scene.N * 0.6 * views.V),
-                             precision=prec, store_state=False)
+                             precision=prec, store_state=store)
     code = rp.ensure_capacity(target)
     assert code == 0, f"capacity handling failed ({code})"
     torch.cuda.synchronize()
@@ -146,14 +150,15 @@ def run_ours(args, rank, world, dist):
         ev[2].record()
         api.bin_sort(rp.splats, rp.g, views, rp.bins, rp.sort_ws, rp.status)
         ev[3].record()
-        api.render_fwd(rp.splats, rp.bins, views, rp.bg, rp.image, rp.status, rp.render_ws, rp.chunk)
+        api.render_fwd(rp.splats, rp.bins, views, rp.bg, rp.image, rp.status, rp.render_ws, rp.chunk,
+                       rp.T_final, rp.last)
         ev[4].record()
         api.l1_loss(rp.image, target, views, rp.loss, rp.d_image)
         ev[5].record()
         if rp.ggrad is None:
             rp.ggrad = api.Gauss3DGrad.like(rp.g)
         api.render_bwd(rp.g, rp.splats, rp.bins, views, rp.bg, rp.d_image, rp.sgrad, rp.ggrad, rp.status,
-                       rp.render_ws, rp.chunk)
+                       rp.render_ws, rp.chunk, rp.T_final, rp.last)
         ev[6].record()
         api.decode_bwd(anchors, views, rp.g, rp.ggrad, rp.agrad, rp.dbwd_ws, rp.status, prec)
         ev[7].record()
@@ -400,7 +405,7 @@ def main():
                 "data": "synthetic (seeded driving-corridor scene; no dataset)",
                 "config": {"workload": WORKLOAD, "anchors": args.anchors, "keyframes": args.views,
                            "resolution": "1241x376", "k": 10, "feature_dim": 32, "hidden": 32,
-                           "path": "batched, one CUDA graph per iteration, state recomputed",
+                           "path": "batched, one CUDA graph per iteration, per-pixel state " + ("stored" if args.state == "store" else "recomputed"),
                            "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) before each step"},
                 "e2e": {"value": r["e2e_mpix"], "unit": "Mpix/s", "h2d_bytes_per_step": r["h2d"],
                         "d2h_bytes_per_step": r["d2h"]},
