@@ -156,3 +156,78 @@ class RenderPass:
 
     def n_pairs(self):
         return int(self.bins.n_pairs.item())
+
+
+class MappingStep:
+    """One mapping iteration of a keyframe batch (decode -> ... -> decode
+    backward, no optimizer step) captured once into a CUDA graph and replayed.
+
+    `prepare(target)` sizes the buffers with one host-synchronised eager pass
+    and captures the graph; `run()` replays it on device-resident inputs;
+    `step(target_host, cams_host)` is the end-to-end call: it copies the
+    iteration's target images (and optionally cameras) from pinned host memory,
+    replays the graph and reads back the loss and the status word (one stream
+    synchronisation).  A capacity overflow found there re-prepares the buffers
+    and repeats the iteration.
+    """
+
+    def __init__(self, views: api.Views, anchors: api.Anchors, precision: int = L.GS_PREC_BF16,
+                 cap_rows: int | None = None, store_state: bool = False, chunk: int = 0, device="cuda"):
+        self.views = views
+        self.anchors = anchors
+        self.rp = RenderPass(views, anchors, cap_rows=cap_rows, precision=precision, store_state=store_state,
+                             chunk=chunk, device=device)
+        self.target = torch.zeros(3 * views.total_pixels, device=device)
+        self.stream = torch.cuda.Stream(device=device)
+        self.graph = None
+        self._loss_host = torch.zeros(1, dtype=torch.float32).pin_memory()
+        self._status_host = torch.zeros(2, dtype=torch.int64).pin_memory()
+
+    @property
+    def h2d_bytes(self):
+        return self.target.numel() * 4
+
+    def prepare(self, target=None):
+        if target is not None:
+            self.target.copy_(target)
+        code = self.rp.ensure_capacity(self.target)
+        if code != 0:
+            raise L.GsError("capacity handling", code)
+        with torch.cuda.stream(self.stream):
+            self.rp.step(self.target)   # kernel attributes and workspaces settle outside the capture
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=self.stream):
+            self.rp.step(self.target)
+        torch.cuda.synchronize()
+
+    def run(self):
+        """Replays the captured iteration on the current inputs; returns the device loss."""
+        with torch.cuda.stream(self.stream):
+            self.graph.replay()
+        return self.rp.loss
+
+    def step(self, target_host, cams_host=None, retries=2):
+        """End-to-end iteration from host inputs; returns the loss as a Python float."""
+        if self.graph is None:
+            self.prepare(target_host.to(self.target.device))
+        for _ in range(retries + 1):
+            with torch.cuda.stream(self.stream):
+                self.target.copy_(target_host, non_blocking=True)
+                if cams_host is not None:
+                    self.views.cams.copy_(cams_host, non_blocking=True)
+                self.graph.replay()
+                self._loss_host.copy_(self.rp.loss, non_blocking=True)
+                self._status_host.copy_(self.rp.status, non_blocking=True)
+            self.stream.synchronize()
+            code = int(np.int32(int(self._status_host[0]) & 0xFFFFFFFF))
+            if code == 0:
+                return float(self._loss_host[0])
+            if code != L.GS_ERR_CAPACITY:
+                raise L.GsError("mapping step", code)
+            self.prepare()
+        raise L.GsError("mapping step: capacity", L.GS_ERR_CAPACITY)
+
+    @property
+    def d2h_bytes(self):
+        return 4 + 16
