@@ -285,6 +285,17 @@ int gs_decode_bwd(const gs_anchors *A, const gs_camera *cams, const gs_view *vie
                   gs_anchor_grad *out, void *ws, size_t ws_bytes, gs_status *status,
                   void *stream);
 
+/* Measurement helper (no counterpart in the paper): launches `blocks` CTAs of
+ * 256 threads, each running 8 independent chains of `iters` dependent
+ * operations -- kind 0: FP32 fused multiply-add, kind 1: SFU ex2.approx --
+ * and stores the number of operations issued in *ops (host).  The caller
+ * times the launch on `stream` to get the device's FP32-pipe or SFU issue
+ * rate, the denominators of the compositing kernels' rooflines.  sink: a
+ * device buffer of `blocks` floats (written only in a case that does not
+ * occur).  Returns GS_ERR_INVALID_ARG for another kind, blocks < 1 or
+ * iters < 1. */
+int gs_probe_peak(int32_t kind, int32_t blocks, int32_t iters, float *sink, int64_t *ops, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

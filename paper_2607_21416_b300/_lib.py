@@ -74,6 +74,7 @@ EXPORTS = {
     "gs_decode_bwd_workspace": (sz, [i32, i32, i32, i64]),
     "gs_status_string": (C.c_char_p, [i32]),
     "gs_kernel_launches": (C.c_uint64, []),
+    "gs_probe_peak": (i32, [i32, i32, i32, vp, C.POINTER(C.c_int64), vp]),
     "gs_decode": (C.c_int, [P(gs_anchors), vp, P(gs_view), i32, i32, P(gs_gauss3d), vp, sz, vp, vp]),
     "gs_decode_noalloc": (C.c_int, [P(gs_anchors), vp, P(gs_view), i32, i32, P(gs_gauss3d), vp, vp]),
     "gs_project": (C.c_int, [P(gs_gauss3d), vp, P(gs_view), i32, P(gs_splats), vp, vp]),

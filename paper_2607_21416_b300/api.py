@@ -294,3 +294,20 @@ def decode_bwd(anchors: Anchors, views: Views, g: Gauss3D, dg: Gauss3DGrad, out:
     L.check("gs_decode_bwd", lib.gs_decode_bwd(C.byref(a), _ptr(views.cams), views.ptr, views.V,
                                                precision, C.byref(gs_), C.byref(d), C.byref(o),
                                                _ptr(ws), ws.numel(), _ptr(status), _stream(stream)))
+
+
+def probe_peak(kind: int, blocks: int | None = None, iters: int = 4096, device="cuda"):
+    """Issue rate of FP32 fused multiply-adds (kind 0) or SFU ex2 (kind 1) on
+    the current device, in operations per second (measurement helper)."""
+    if blocks is None:
+        blocks = torch.cuda.get_device_properties(device).multi_processor_count * 8
+    sink = torch.zeros(blocks, device=device)
+    ops = C.c_int64(0)
+    lib = L.load()
+    for _ in range(2):   # warm-up launch, then the timed one
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        L.check("gs_probe_peak", lib.gs_probe_peak(kind, blocks, iters, _ptr(sink), C.byref(ops), _stream()))
+        e1.record()
+        torch.cuda.synchronize()
+    return ops.value / (e0.elapsed_time(e1) * 1e-3)
