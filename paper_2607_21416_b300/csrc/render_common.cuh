@@ -2,21 +2,25 @@
 //
 // Work decomposition.  Each 16x16 tile's sorted splat list [start, end) is
 // cut into chunks of at most L splats; chunk k of tile t is one work item and
-// one CTA of 256 threads (one thread per pixel).  item_base[t] (exclusive scan
-// of the per-tile chunk counts, built on the device) numbers the items; the
-// item of block b is found by binary search.  A tile with one chunk is
-// composited directly.  A tile with several chunks keeps per-chunk, per-pixel
-// state in the render workspace:
-//   Tprod  product of (1 - alpha) over the chunk's splats (no stop rule; it
-//          may stop early once below 1e-4, which decides every later chunk)
+// one CTA of 128 threads (two pixels each).  item_base[t] (exclusive scan of
+// the per-tile chunk counts, built on the device) numbers the items; the item
+// of block b is found by binary search.  A tile with one chunk is composited
+// directly.  Chunk 0 of a multi-chunk tile is composited exactly (it starts
+// at T = 1); every later chunk is composited with its own transmittance
+// starting at 1 and no stop rule, and the combine step scales it by the
+// transmittance in front of it.  That is Eq. 1 exactly unless a pixel's stop
+// (T' < 1e-4) falls inside the chunk; those (chunk, pixel) pairs are
+// composited again from the now known entering transmittance (fix-up).
+// After the forward, each item of a multi-chunk tile holds per pixel:
+//   Tprod  product of (1 - alpha) over the chunk's splats (0 when chunk 0
+//          stopped the pixel; it may stop early once below 1e-4, which decides
+//          every later chunk)
 //   Tend   transmittance after the chunk's compositing (stop rule applied)
 //   C[3]   the chunk's colour contribution
 //   last   1-based position (in the chunk) of its last composited splat
-// so that compositing Eq. 1 front to back over the whole list is reproduced
-// exactly: chunk k starts from T0_k = prod_{j<k} Tprod_j (it is active iff
-// T0_k >= 1e-4, i.e. iff no earlier splat stopped the pixel), and the
-// backward pass of chunk k needs only T0_k, its own Tend/last and the colour
-// of the chunks behind it.
+// so chunk k starts from T0_k = prod_{j<k} Tprod_j (it is active iff T0_k >=
+// 1e-4), and the backward pass of chunk k needs only T0_k, its own Tend/last
+// and the colour of the chunks behind it.
 #pragma once
 
 #include "gs_internal.cuh"
@@ -25,7 +29,7 @@ namespace gs {
 
 constexpr int kRT = kTilePix;      // pixels per tile / work item
 constexpr int kRThreads = 128;     // threads per work item: two pixels each (rows y and y + 8)
-constexpr int kStateWords = 6;     // Tprod, Tend, C0, C1, C2, last  (x 256 pixels)
+constexpr int kStateWords = 7;     // Tprod, Tend, C0, C1, C2, last, composited count  (x 256 pixels)
 
 // 2^x on the special-function unit (ex2.approx, max relative error ~2^-22).
 __device__ __forceinline__ float ex2_approx(float x)
@@ -108,15 +112,6 @@ __device__ __forceinline__ float *state_plane(float *state, int item, int plane)
     return state + ((size_t)item * kStateWords + plane) * kRT;
 }
 
-// Transmittance in front of chunk k at tile pixel `pix`: the product of the
-// earlier chunks' Tprod.
-__device__ __forceinline__ float chunk_T0(const float *state, const Item &it, int pix)
-{
-    float T = 1.f;
-    for (int j = 0; j < it.k; ++j) T = __fmul_rn(T, state_plane(const_cast<float *>(state), it.base + j, 0)[pix]);
-    return T;
-}
-
 // Shared-memory records of one batch of kRT list positions.
 struct Staged {
     float4 a[kRT];    // mean x, mean y, A, B
@@ -193,7 +188,8 @@ __device__ __forceinline__ int warp_list(Staged &S, int n, int x0, int y0)
 
 struct RenderPlan {
     const int32_t *item_base;   // [T+1]
-    float *state;               // [max_items][6][256]
+    int32_t *fix;               // [max_items] items with pixels to composite again
+    float *state;               // [max_items][kStateWords][256]
     int L;
     int max_items;
 };

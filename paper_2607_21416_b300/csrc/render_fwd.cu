@@ -6,10 +6,15 @@
 // every splat read from shared memory serves two evaluations; each warp walks
 // only the splats whose alpha >= 1/255 box meets its 16x4 block):
 //   plan_kernel     per-tile chunk counts -> item_base (one CTA scan)
-//   prod_kernel     Tprod of every chunk of a multi-chunk tile
-//   chunk_kernel    compositing of every item; single-chunk tiles write the
-//                   image directly, multi-chunk tiles write per-chunk state
-//   combine_kernel  image (and optional T_final / last) of multi-chunk tiles
+//   chunk_kernel    compositing of every item: single-chunk tiles write the
+//                   image directly; chunk 0 of a multi-chunk tile composites
+//                   exactly, later chunks on their own transmittance (see
+//                   render_common.cuh); multi-chunk tiles write per-chunk state
+//   combine_kernel  multi-chunk tiles: scales each chunk by the transmittance
+//                   in front of it and writes the image, or marks the chunk
+//                   that holds the pixel's stop for the fix-up
+//   chunk_kernel<fix-up>  composites the marked chunks again from their
+//                   entering transmittance, with the stop rule
 // The power / alpha arithmetic is pinned (explicit fmaf / __fmul_rn) so every
 // pass that re-evaluates a pair takes bit-identical skip / stop decisions.
 #include "render_common.cuh"
@@ -18,8 +23,9 @@ namespace gs {
 
 __global__ void __launch_bounds__(1024) plan_kernel(const uint32_t *__restrict__ ranges, int T, int L,
                                                     int max_items, int32_t *__restrict__ item_base,
-                                                    const gs_status *st)
+                                                    int32_t *__restrict__ fix, const gs_status *st)
 {
+    for (int i = threadIdx.x; i < max_items; i += blockDim.x) fix[i] = 0;
     __shared__ int s_warp[32];
     __shared__ long long s_carry;
     if (threadIdx.x == 0) s_carry = 0;
@@ -73,10 +79,16 @@ struct PixFwd {
     float T, C0, C1, C2;
     int last;      // position of the last composited splat (1-based, in the chunk)
     int stop;      // position of the splat that stopped the pixel (0: not stopped)
+    int ncomp;     // splats composited
     bool done;
 };
 
 // Eq. 1 step of one pixel over a staged splat at chunk position pos (1-based).
+// STOP: the stop rule of the method (the pixel's entering transmittance is
+// known).  Otherwise (a later chunk on its own transmittance) every splat is
+// composited; once the chunk's own product is below 1e-4 the pixel is stopped
+// in any case and the pass ends for it.
+template <bool STOP>
 __device__ __forceinline__ void fwd_step(PixFwd &ps, const float4 a, const float4 bb, float cb, float px, float py,
                                          int pos)
 {
@@ -86,101 +98,49 @@ __device__ __forceinline__ void fwd_step(PixFwd &ps, const float4 a, const float
     const float alpha = fminf(kAlphaMax, splat_alpha(q, bb.y));
     if (alpha < kAlphaMin) return;
     const float Tn = __fmul_rn(ps.T, 1.f - alpha);
-    if (Tn < kTMin) { ps.done = true; ps.stop = pos; return; }
+    if (STOP && Tn < kTMin) { ps.done = true; ps.stop = pos; return; }
     const float w = __fmul_rn(alpha, ps.T);
     ps.C0 = fmaf(bb.z, w, ps.C0);
     ps.C1 = fmaf(bb.w, w, ps.C1);
     ps.C2 = fmaf(cb, w, ps.C2);
     ps.T = Tn;
     ps.last = pos;
+    ++ps.ncomp;
+    if (!STOP && Tn < kTMin) ps.done = true;
 }
 
-// Transmittance product of one chunk (no stop rule; early exit below 1e-4).
-// The last chunk of a tile needs none.
-__global__ void __launch_bounds__(kRThreads) prod_kernel(const float4 *__restrict__ rec,
-                                                         const uint32_t *__restrict__ vals,
-                                                         const uint32_t *__restrict__ ranges, ViewTable vt,
-                                                         RenderPlan plan, long long cap_cand, const gs_status *st)
+// Image (and optional T_final / last) of one pixel; lastg < 0 leaves `last`.
+__device__ __forceinline__ void write_image(const ViewTable &vt, int v, int px, int py, float C0, float C1, float C2,
+                                            float T, int lastg, float bg0, float bg1, float bg2, float *image,
+                                            float *T_final, int32_t *last)
 {
-    if (has_error(st)) return;
-    Item it;
-    if (!item_of(blockIdx.x, plan.item_base, vt.total_tiles, ranges, plan.L, &it) || it.nk == 1 ||
-        it.k == it.nk - 1)
-        return;
-    __shared__ Staged S;
-    const TileCoord tc = tile_coord(vt, it.t);
-    const float fpx = (float)tc.px, fy0 = (float)tc.py, fy1 = (float)(tc.py + 1);
-    float T0 = 1.f, T1 = 1.f;
-    bool d0 = !tc.in0, d1 = !tc.in1;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    for (uint32_t b0 = it.s0; b0 < it.s1; b0 += kRT) {
-        if (__syncthreads_count(d0 && d1) == kRThreads) break;
-        stage(S, tid, rec, vals, b0 + tid, b0 + tid < it.s1, cap_cand, st, 43, false);
-        stage(S, tid + kRThreads, rec, vals, b0 + tid + kRThreads, b0 + tid + kRThreads < it.s1, cap_cand, st, 43,
-              false);
-        __syncthreads();
-        const int n = (int)min((uint32_t)kRT, it.s1 - b0);
-        const int cnt = warp_list(S, n, tc.x0, tc.y0);
-        for (int li = 0; li < cnt; ++li) {
-            const int j = S.wl[warp][li];
-            const float4 a = S.a[j];
-            const float4 bb = S.b[j];
-            float dx, dy;
-            if (!d0) {
-                const float q = splat_q(a, bb.x, fpx, fy0, &dx, &dy);
-                if (q <= 0.f) {
-                    const float alpha = fminf(kAlphaMax, splat_alpha(q, bb.y));
-                    if (alpha >= kAlphaMin) {
-                        T0 = __fmul_rn(T0, 1.f - alpha);
-                        d0 = T0 < kTMin;
-                    }
-                }
-            }
-            if (!d1) {
-                const float q = splat_q(a, bb.x, fpx, fy1, &dx, &dy);
-                if (q <= 0.f) {
-                    const float alpha = fminf(kAlphaMax, splat_alpha(q, bb.y));
-                    if (alpha >= kAlphaMin) {
-                        T1 = __fmul_rn(T1, 1.f - alpha);
-                        d1 = T1 < kTMin;
-                    }
-                }
-            }
-        }
-    }
-    float *pl = state_plane(plan.state, it.base + it.k, 0);
-    pl[tc.pid0] = T0;
-    pl[tc.pid0 + kTile] = T1;
-}
-
-__device__ __forceinline__ void write_pixel_or_state(const PixFwd &ps, bool inside, bool multi, int item, int pix,
-                                                     const RenderPlan &plan, const ViewTable &vt, int v, int px,
-                                                     int py, float bg0, float bg1, float bg2, float *image,
-                                                     float *T_final, int32_t *last)
-{
-    if (multi) {
-        state_plane(plan.state, item, 1)[pix] = ps.T;
-        state_plane(plan.state, item, 2)[pix] = ps.C0;
-        state_plane(plan.state, item, 3)[pix] = ps.C1;
-        state_plane(plan.state, item, 4)[pix] = ps.C2;
-        reinterpret_cast<int *>(state_plane(plan.state, item, 5))[pix] = ps.last;
-        return;
-    }
-    if (!inside) return;
     const long long W = vt.W[v], H = vt.H[v];
     const long long p = (long long)py * W + px;
     float *img = image + 3 * vt.pix_base[v];
-    img[p] = fmaf(ps.T, bg0, ps.C0);
-    img[W * H + p] = fmaf(ps.T, bg1, ps.C1);
-    img[2 * W * H + p] = fmaf(ps.T, bg2, ps.C2);
-    if (T_final) T_final[vt.pix_base[v] + p] = ps.T;
-    if (last) last[vt.pix_base[v] + p] = ps.last;
+    img[p] = fmaf(T, bg0, C0);
+    img[W * H + p] = fmaf(T, bg1, C1);
+    img[2 * W * H + p] = fmaf(T, bg2, C2);
+    if (T_final) T_final[vt.pix_base[v] + p] = T;
+    if (last && lastg >= 0) last[vt.pix_base[v] + p] = lastg;
 }
 
-// Compositing of one work item.  Each warp walks only the staged splats whose
-// alpha box meets its pixel block.  With COUNT, the pairs the method examines
-// (every list position up to the stop) and the pairs composited are counted.
-template <bool COUNT>
+// Warp totals of the examined / composited pair counts into n_eval[0..1].
+__device__ __forceinline__ void count_add(unsigned long long *n_eval, unsigned long long nev, unsigned long long ncomp)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        nev += __shfl_down_sync(0xffffffffu, nev, o);
+        ncomp += __shfl_down_sync(0xffffffffu, ncomp, o);
+    }
+    if ((threadIdx.x & 31) == 0 && nev) atomicAdd(n_eval, nev);
+    if ((threadIdx.x & 31) == 0 && ncomp) atomicAdd(n_eval + 1, ncomp);
+}
+
+// Compositing of one work item (FIX: the fix-up pass over marked chunks).
+// Each warp walks only the staged splats whose alpha box meets its pixel
+// block.  With COUNT, the pairs the method examines (every list position up to
+// the stop) and the pairs composited are counted for the chunks whose activity
+// is decided here; the combine step counts the others.
+template <bool COUNT, bool FIX>
 __global__ void __launch_bounds__(kRThreads) chunk_kernel(const float4 *__restrict__ rec,
                                                           const uint32_t *__restrict__ vals,
                                                           const uint32_t *__restrict__ ranges, ViewTable vt,
@@ -191,6 +151,7 @@ __global__ void __launch_bounds__(kRThreads) chunk_kernel(const float4 *__restri
                                                           long long cap_cand, const gs_status *st)
 {
     if (has_error(st)) return;
+    if (FIX && plan.fix[blockIdx.x] == 0) return;
     Item it;
     if (!item_of(blockIdx.x, plan.item_base, vt.total_tiles, ranges, plan.L, &it)) return;
     __shared__ Staged S;
@@ -198,13 +159,22 @@ __global__ void __launch_bounds__(kRThreads) chunk_kernel(const float4 *__restri
     const TileCoord tc = tile_coord(vt, it.t);
     const float fpx = (float)tc.px, fy0 = (float)tc.py, fy1 = (float)(tc.py + 1);
     const bool multi = it.nk > 1;
+    const bool exact = !multi || it.k == 0 || FIX;
+    const int item = it.base + it.k;
     PixFwd p0, p1;
-    p0.T = multi ? chunk_T0(plan.state, it, tc.pid0) : 1.f;
-    p1.T = multi ? chunk_T0(plan.state, it, tc.pid0 + kTile) : 1.f;
+    p0.T = p1.T = 1.f;
     p0.C0 = p0.C1 = p0.C2 = p1.C0 = p1.C1 = p1.C2 = 0.f;
-    p0.last = p1.last = p0.stop = p1.stop = 0;
-    p0.done = !tc.in0 || p0.T < kTMin;
-    p1.done = !tc.in1 || p1.T < kTMin;
+    p0.last = p1.last = p0.stop = p1.stop = p0.ncomp = p1.ncomp = 0;
+    p0.done = !tc.in0;
+    p1.done = !tc.in1;
+    if (FIX) {   // the marked pixels start from their entering transmittance
+        const int *lp = reinterpret_cast<const int *>(state_plane(plan.state, item, 5));
+        const float *tp = state_plane(plan.state, item, 1);
+        p0.done = p0.done || lp[tc.pid0] != -1;
+        p1.done = p1.done || lp[tc.pid0 + kTile] != -1;
+        if (!p0.done) p0.T = tp[tc.pid0];
+        if (!p1.done) p1.T = tp[tc.pid0 + kTile];
+    }
     const bool act0 = !p0.done, act1 = !p1.done;
     for (uint32_t b0 = it.s0; b0 < it.s1; b0 += kRT) {
         if (__syncthreads_count(p0.done && p1.done) == kRThreads) break;
@@ -215,93 +185,146 @@ __global__ void __launch_bounds__(kRThreads) chunk_kernel(const float4 *__restri
         const int n = (int)min((uint32_t)kRT, it.s1 - b0);
         const int base = (int)(b0 - it.s0);
         const int cnt = warp_list(S, n, tc.x0, tc.y0);
-        for (int li = 0; li < cnt; ++li) {
-            const int j = S.wl[warp][li];
-            const float4 a = S.a[j];
-            const float4 bb = S.b[j];
-            const float cb = S.c[j];
-            if (!p0.done) fwd_step(p0, a, bb, cb, fpx, fy0, base + j + 1);
-            if (!p1.done) fwd_step(p1, a, bb, cb, fpx, fy1, base + j + 1);
+        if (exact) {
+            for (int li = 0; li < cnt; ++li) {
+                const int j = S.wl[warp][li];
+                const float4 a = S.a[j];
+                const float4 bb = S.b[j];
+                const float cb = S.c[j];
+                if (!p0.done) fwd_step<true>(p0, a, bb, cb, fpx, fy0, base + j + 1);
+                if (!p1.done) fwd_step<true>(p1, a, bb, cb, fpx, fy1, base + j + 1);
+            }
+        } else {
+            for (int li = 0; li < cnt; ++li) {
+                const int j = S.wl[warp][li];
+                const float4 a = S.a[j];
+                const float4 bb = S.b[j];
+                const float cb = S.c[j];
+                if (!p0.done) fwd_step<false>(p0, a, bb, cb, fpx, fy0, base + j + 1);
+                if (!p1.done) fwd_step<false>(p1, a, bb, cb, fpx, fy1, base + j + 1);
+            }
         }
     }
     if (COUNT) {
         const int n_items = (int)(it.s1 - it.s0);
         unsigned long long nev = 0, ncomp = 0;
-        if (act0) nev += p0.stop ? p0.stop : n_items;
-        if (act1) nev += p1.stop ? p1.stop : n_items;
-        // composited pairs: recount over the list (cheap next to the composite itself)
-        for (int pass = 0; pass < 2; ++pass) {
-            const PixFwd &ps = pass ? p1 : p0;
-            if (!(pass ? act1 : act0)) continue;
-            float T = multi ? chunk_T0(plan.state, it, tc.pid0 + pass * kTile) : 1.f;
-            const float fy = pass ? fy1 : fy0;
-            for (int pos = 0; pos < ps.last; ++pos) {
-                uint32_t id = vals[it.s0 + pos];
-                if (!idx_ok(st, (long long)id, cap_cand, 44)) break;
-                const float4 a = __ldg(&rec[3 * (size_t)id]);
-                const float4 bb = __ldg(&rec[3 * (size_t)id + 1]);
-                float dx, dy;
-                const float q = splat_q(a, bb.x, fpx, fy, &dx, &dy);
-                if (q > 0.f) continue;
-                const float alpha = fminf(kAlphaMax, splat_alpha(q, bb.y));
-                if (alpha < kAlphaMin) continue;
-                T = __fmul_rn(T, 1.f - alpha);
-                ++ncomp;
-            }
+        if (exact) {
+            if (act0) { nev += p0.stop ? p0.stop : n_items; ncomp += p0.ncomp; }
+            if (act1) { nev += p1.stop ? p1.stop : n_items; ncomp += p1.ncomp; }
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            nev += __shfl_down_sync(0xffffffffu, nev, o);
-            ncomp += __shfl_down_sync(0xffffffffu, ncomp, o);
-        }
-        if ((tid & 31) == 0 && nev) atomicAdd(n_eval, nev);
-        if ((tid & 31) == 0 && ncomp) atomicAdd(n_eval + 1, ncomp);
+        count_add(n_eval, nev, ncomp);
     }
-    const int item = it.base + it.k;
-    write_pixel_or_state(p0, tc.in0, multi, item, tc.pid0, plan, vt, tc.v, tc.px, tc.py, bg0, bg1, bg2, image,
-                         T_final, last);
-    write_pixel_or_state(p1, tc.in1, multi, item, tc.pid0 + kTile, plan, vt, tc.v, tc.px, tc.py + 1, bg0, bg1, bg2,
-                         image, T_final, last);
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        const PixFwd &ps = half ? p1 : p0;
+        const int pix = tc.pid0 + half * kTile;
+        const int py = tc.py + half;
+        if (!multi) {
+            if (half ? tc.in1 : tc.in0)
+                write_image(vt, tc.v, tc.px, py, ps.C0, ps.C1, ps.C2, ps.T, ps.last, bg0, bg1, bg2, image, T_final,
+                            last);
+            continue;
+        }
+        if (FIX) {
+            if (!(half ? act1 : act0)) continue;
+            float *c0 = state_plane(plan.state, item, 2), *c1 = state_plane(plan.state, item, 3);
+            float *c2 = state_plane(plan.state, item, 4);
+            const float f0 = c0[pix], f1 = c1[pix], f2 = c2[pix];   // colour in front of the chunk
+            state_plane(plan.state, item, 1)[pix] = ps.T;
+            c0[pix] = ps.C0;
+            c1[pix] = ps.C1;
+            c2[pix] = ps.C2;
+            reinterpret_cast<int *>(state_plane(plan.state, item, 5))[pix] = ps.last;
+            write_image(vt, tc.v, tc.px, py, f0 + ps.C0, f1 + ps.C1, f2 + ps.C2, ps.T,
+                        ps.last > 0 ? it.k * plan.L + ps.last : -1, bg0, bg1, bg2, image, T_final, last);
+            continue;
+        }
+        // per-chunk state; a stop in chunk 0 is marked by Tprod = 0
+        state_plane(plan.state, item, 0)[pix] = (it.k == 0 && ps.stop) ? 0.f : ps.T;
+        state_plane(plan.state, item, 1)[pix] = ps.T;
+        state_plane(plan.state, item, 2)[pix] = ps.C0;
+        state_plane(plan.state, item, 3)[pix] = ps.C1;
+        state_plane(plan.state, item, 4)[pix] = ps.C2;
+        reinterpret_cast<int *>(state_plane(plan.state, item, 5))[pix] = ps.last;
+        if (COUNT) reinterpret_cast<int *>(state_plane(plan.state, item, 6))[pix] = ps.ncomp;
+    }
 }
 
-// Image of a multi-chunk tile: sum of the active chunks' colour plus the final
-// transmittance (that of the last active chunk) times the background.
+// Multi-chunk tiles, per pixel: chunk 0 is exact; every later chunk k is
+// scaled by the transmittance T0 in front of it (its state becomes the
+// chunk's true contribution) while T0 * Tprod_k >= 1e-4 -- no splat of the
+// chunk can then meet the stop rule; the first chunk where that fails holds
+// the pixel's stop and is marked for the fix-up, with T0 and the colour in
+// front of it in its Tend / colour planes and last = -1.
+template <bool COUNT>
 __global__ void __launch_bounds__(kRThreads) combine_kernel(const uint32_t *__restrict__ ranges, ViewTable vt,
                                                             RenderPlan plan, float bg0, float bg1, float bg2,
                                                             float *__restrict__ image, float *__restrict__ T_final,
-                                                            int32_t *__restrict__ last, const gs_status *st)
+                                                            int32_t *__restrict__ last,
+                                                            unsigned long long *__restrict__ n_eval,
+                                                            const gs_status *st)
 {
     if (has_error(st)) return;
     const int t = blockIdx.x;
     const int base = plan.item_base[t], nk = plan.item_base[t + 1] - base;
     if (nk <= 1) return;
     const TileCoord tc = tile_coord(vt, t);
+    const uint32_t s_start = ranges[2 * t], s_end = ranges[2 * t + 1];
+    unsigned long long nev = 0, ncomp = 0;
     for (int half = 0; half < 2; ++half) {
-        const bool inside = half ? tc.in1 : tc.in0;
-        if (!inside) continue;
+        if (!(half ? tc.in1 : tc.in0)) continue;
         const int pix = tc.pid0 + half * kTile;
-        float T0 = 1.f, Tf = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-        int lastc = 0;
-        for (int j = 0; j < nk; ++j) {
-            if (!(T0 >= kTMin)) break;
-            const int item = base + j;
-            C0 += state_plane(plan.state, item, 2)[pix];
-            C1 += state_plane(plan.state, item, 3)[pix];
-            C2 += state_plane(plan.state, item, 4)[pix];
-            Tf = state_plane(plan.state, item, 1)[pix];
-            const int lj = reinterpret_cast<const int *>(state_plane(plan.state, item, 5))[pix];
-            if (lj > 0) lastc = j * plan.L + lj;
-            if (j < nk - 1) T0 = __fmul_rn(T0, state_plane(plan.state, item, 0)[pix]);
+        const int py = tc.py + half;
+        float C0 = state_plane(plan.state, base, 2)[pix];
+        float C1 = state_plane(plan.state, base, 3)[pix];
+        float C2 = state_plane(plan.state, base, 4)[pix];
+        const int l0 = reinterpret_cast<const int *>(state_plane(plan.state, base, 5))[pix];
+        int lastg = l0 > 0 ? l0 : 0;
+        float T0 = state_plane(plan.state, base, 0)[pix];
+        if (T0 == 0.f) {   // chunk 0 stopped the pixel
+            write_image(vt, tc.v, tc.px, py, C0, C1, C2, state_plane(plan.state, base, 1)[pix], lastg, bg0, bg1, bg2,
+                        image, T_final, last);
+            continue;
         }
-        const int v = tc.v;
-        const long long W = vt.W[v], H = vt.H[v];
-        const long long p = (long long)(tc.py + half) * W + tc.px;
-        float *img = image + 3 * vt.pix_base[v];
-        img[p] = fmaf(Tf, bg0, C0);
-        img[W * H + p] = fmaf(Tf, bg1, C1);
-        img[2 * W * H + p] = fmaf(Tf, bg2, C2);
-        if (T_final) T_final[vt.pix_base[v] + p] = Tf;
-        if (last) last[vt.pix_base[v] + p] = lastc;
+        bool marked = false;
+        for (int k = 1; k < nk; ++k) {
+            if (!(T0 >= kTMin)) break;
+            const int item = base + k;
+            float *te = state_plane(plan.state, item, 1);
+            float *c0 = state_plane(plan.state, item, 2), *c1 = state_plane(plan.state, item, 3);
+            float *c2 = state_plane(plan.state, item, 4);
+            int *lp = reinterpret_cast<int *>(state_plane(plan.state, item, 5));
+            const float T1 = __fmul_rn(T0, state_plane(plan.state, item, 0)[pix]);
+            if (T1 >= kTMin) {   // no stop inside: the chunk's true contribution
+                const float g0 = T0 * c0[pix], g1 = T0 * c1[pix], g2 = T0 * c2[pix];
+                c0[pix] = g0;
+                c1[pix] = g1;
+                c2[pix] = g2;
+                te[pix] = T1;
+                C0 += g0;
+                C1 += g1;
+                C2 += g2;
+                if (lp[pix] > 0) lastg = k * plan.L + lp[pix];
+                if (COUNT) {
+                    nev += min((uint32_t)plan.L, s_end - (s_start + (uint32_t)k * (uint32_t)plan.L));
+                    ncomp += reinterpret_cast<const int *>(state_plane(plan.state, item, 6))[pix];
+                }
+                T0 = T1;
+            } else {             // the pixel's stop lies in chunk k
+                te[pix] = T0;
+                c0[pix] = C0;
+                c1[pix] = C1;
+                c2[pix] = C2;
+                lp[pix] = -1;
+                plan.fix[item] = 1;
+                if (last) last[vt.pix_base[tc.v] + (long long)py * vt.W[tc.v] + tc.px] = lastg;
+                marked = true;
+                break;
+            }
+        }
+        if (!marked) write_image(vt, tc.v, tc.px, py, C0, C1, C2, T0, lastg, bg0, bg1, bg2, image, T_final, last);
     }
+    if (COUNT) count_add(n_eval, nev, ncomp);
 }
 
 // ------------------------------------------------------------------- L1
@@ -331,19 +354,38 @@ int render_max_items(const ViewTable &vt, long long cap_pairs, int L)
 size_t render_workspace_bytes(const ViewTable &vt, long long cap_pairs, int L)
 {
     const long long items = render_max_items(vt, cap_pairs, L);
-    return align_up(sizeof(int32_t) * ((size_t)vt.total_tiles + 1), 256) +
+    return align_up(sizeof(int32_t) * ((size_t)vt.total_tiles + 1), 256) + align_up(sizeof(int32_t) * (size_t)items, 256) +
            align_up(sizeof(float) * (size_t)items * kStateWords * kRT, 256);
 }
 
+// Workspace: item_base [T + 1] | fix flags [max_items] | state [max_items][kStateWords][256]
 RenderPlan render_plan(const ViewTable &vt, long long cap_pairs, int L, void *ws)
 {
     RenderPlan p;
     p.L = L;
     p.max_items = render_max_items(vt, cap_pairs, L);
     char *w = reinterpret_cast<char *>(ws);
+    const size_t o1 = align_up(sizeof(int32_t) * ((size_t)vt.total_tiles + 1), 256);
+    const size_t o2 = o1 + align_up(sizeof(int32_t) * (size_t)p.max_items, 256);
     p.item_base = reinterpret_cast<int32_t *>(w);
-    p.state = reinterpret_cast<float *>(w + align_up(sizeof(int32_t) * ((size_t)vt.total_tiles + 1), 256));
+    p.fix = reinterpret_cast<int32_t *>(w + o1);
+    p.state = reinterpret_cast<float *>(w + o2);
     return p;
+}
+
+template <bool COUNT>
+static void launch_items(const float4 *rec, const gs_bins *bins, const ViewTable &vt, const RenderPlan &plan,
+                         const float bg[3], float *image, float *T_final, int32_t *last, unsigned long long *n_eval,
+                         long long cap, gs_status *st, cudaStream_t s)
+{
+    chunk_kernel<COUNT, false><<<plan.max_items, kRThreads, 0, s>>>(rec, bins->vals, bins->ranges, vt, plan, bg[0],
+                                                                   bg[1], bg[2], image, T_final, last, n_eval, cap,
+                                                                   st);
+    combine_kernel<COUNT><<<vt.total_tiles, kRThreads, 0, s>>>(bins->ranges, vt, plan, bg[0], bg[1], bg[2], image,
+                                                              T_final, last, n_eval, st);
+    chunk_kernel<COUNT, true><<<plan.max_items, kRThreads, 0, s>>>(rec, bins->vals, bins->ranges, vt, plan, bg[0],
+                                                                  bg[1], bg[2], image, T_final, last, n_eval, cap,
+                                                                  st);
 }
 
 int launch_render_fwd(const gs_splats *sp, const gs_bins *bins, const ViewTable &vt, const float bg[3], int L,
@@ -354,19 +396,14 @@ int launch_render_fwd(const gs_splats *sp, const gs_bins *bins, const ViewTable 
     const float4 *rec = reinterpret_cast<const float4 *>(sp->rec);
     const RenderPlan plan = render_plan(vt, bins->cap_pairs, L, ws);
     plan_kernel<<<1, 1024, 0, s>>>(bins->ranges, vt.total_tiles, L, plan.max_items,
-                                   const_cast<int32_t *>(plan.item_base), st);
-    prod_kernel<<<plan.max_items, kRThreads, 0, s>>>(rec, bins->vals, bins->ranges, vt, plan, sp->cap, st);
+                                   const_cast<int32_t *>(plan.item_base), plan.fix, st);
     if (n_eval) {
         cudaMemsetAsync(n_eval, 0, 2 * sizeof(long long), s);
-        chunk_kernel<true><<<plan.max_items, kRThreads, 0, s>>>(rec, bins->vals, bins->ranges, vt, plan, bg[0], bg[1],
-                                                          bg[2], image, T_final, last,
-                                                          reinterpret_cast<unsigned long long *>(n_eval), sp->cap, st);
+        launch_items<true>(rec, bins, vt, plan, bg, image, T_final, last,
+                           reinterpret_cast<unsigned long long *>(n_eval), sp->cap, st, s);
     } else {
-        chunk_kernel<false><<<plan.max_items, kRThreads, 0, s>>>(rec, bins->vals, bins->ranges, vt, plan, bg[0], bg[1],
-                                                           bg[2], image, T_final, last, nullptr, sp->cap, st);
+        launch_items<false>(rec, bins, vt, plan, bg, image, T_final, last, nullptr, sp->cap, st, s);
     }
-    combine_kernel<<<vt.total_tiles, kRThreads, 0, s>>>(bins->ranges, vt, plan, bg[0], bg[1], bg[2], image, T_final,
-                                                   last, st);
     count_launches(4);
     return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
