@@ -97,11 +97,13 @@ __global__ void __launch_bounds__(kRThreads) render_bwd_kernel(
     if (has_error(st)) return;
     Item it;
     if (!item_of(blockIdx.x, plan.item_base, vt.total_tiles, ranges, plan.L, &it)) return;
-    __shared__ Staged S;
-    __shared__ int s_maxlast;
+    __shared__ WarpStage WS[kRThreads / 32];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    WarpStage &WSw = WS[warp];
     const TileCoord tc = tile_coord(vt, it.t);
     const float fpx = (float)tc.px, fy0 = (float)tc.py, fy1 = (float)(tc.py + 1);
+    const float bx0 = (float)tc.x0, bx1 = bx0 + (float)(kTile - 1);
+    const float by0 = (float)(tc.y0 + 4 * warp), by1 = by0 + 3.f;
     const int v = tc.v;
     const long long W = vt.W[v], H = vt.H[v];
     const long long pix0 = (long long)tc.py * W + tc.px, pix1 = pix0 + W;
@@ -110,7 +112,6 @@ __global__ void __launch_bounds__(kRThreads) render_bwd_kernel(
     p0.T = p1.T = 1.f;
     p0.B0 = p0.B1 = p0.B2 = p1.B0 = p1.B1 = p1.B2 = 0.f;
     p0.last = p1.last = 0;
-    if (tid == 0) s_maxlast = 0;
     if (it.nk > 1) {
         // forward state: end transmittance, last position, colour behind the chunk
 #pragma unroll
@@ -142,21 +143,17 @@ __global__ void __launch_bounds__(kRThreads) render_bwd_kernel(
         p0.B0 = p0.T * bg0; p0.B1 = p0.T * bg1; p0.B2 = p0.T * bg2;
         p1.B0 = p1.T * bg0; p1.B1 = p1.T * bg1; p1.B2 = p1.T * bg2;
     } else {
-        // recompute the forward transmittance and the last composited position
+        // recompute the forward transmittance and the last composited position (per warp)
         bool d0 = !tc.in0, d1 = !tc.in1;
-        for (uint32_t b0 = it.s0; b0 < it.s1; b0 += kRT) {
-            if (__syncthreads_count(d0 && d1) == kRThreads) break;
-            stage(S, tid, rec, vals, b0 + tid, b0 + tid < it.s1, cap_cand, st, 52, false);
-            stage(S, tid + kRThreads, rec, vals, b0 + tid + kRThreads, b0 + tid + kRThreads < it.s1, cap_cand, st, 52,
-                  false);
-            __syncthreads();
-            const int n = (int)min((uint32_t)kRT, it.s1 - b0);
-            const int base = (int)(b0 - it.s0);
-            const int cnt = warp_list(S, n, tc.x0, tc.y0);
-            for (int li = 0; li < cnt; ++li) {
-                const int j = S.wl[warp][li];
-                const float4 a = S.a[j];
-                const float4 bb = S.b[j];
+        for (uint32_t b0 = it.s0; b0 < it.s1; b0 += 32) {
+            if (__all_sync(0xffffffffu, d0 && d1)) break;
+            const uint32_t pos = b0 + lane;
+            const int cnt = warp_stage(WSw, rec, vals, pos, it.s0, pos < it.s1, cap_cand, st, 52, false, bx0, bx1,
+                                       by0, by1);
+            for (int e = 0; e < cnt; ++e) {
+                const float4 a = WSw.a[e];
+                const float4 bb = WSw.b[e];
+                const int q1 = WSw.pos[e] + 1;
                 float dx, dy;
                 if (!d0) {
                     const float q = splat_q(a, bb.x, fpx, fy0, &dx, &dy);
@@ -165,7 +162,7 @@ __global__ void __launch_bounds__(kRThreads) render_bwd_kernel(
                         if (alpha >= kAlphaMin) {
                             const float Tn = __fmul_rn(p0.T, 1.f - alpha);
                             if (Tn < kTMin) d0 = true;
-                            else { p0.T = Tn; p0.last = base + j + 1; }
+                            else { p0.T = Tn; p0.last = q1; }
                         }
                     }
                 }
@@ -176,56 +173,48 @@ __global__ void __launch_bounds__(kRThreads) render_bwd_kernel(
                         if (alpha >= kAlphaMin) {
                             const float Tn = __fmul_rn(p1.T, 1.f - alpha);
                             if (Tn < kTMin) d1 = true;
-                            else { p1.T = Tn; p1.last = base + j + 1; }
+                            else { p1.T = Tn; p1.last = q1; }
                         }
                     }
                 }
             }
+            __syncwarp();
         }
         p0.B0 = p0.T * bg0; p0.B1 = p0.T * bg1; p0.B2 = p0.T * bg2;
         p1.B0 = p1.T * bg0; p1.B1 = p1.T * bg1; p1.B2 = p1.T * bg2;
     }
-    __syncthreads();
-    atomicMax(&s_maxlast, max(p0.last, p1.last));
     p0.g0 = p0.g1 = p0.g2 = p1.g0 = p1.g1 = p1.g2 = 0.f;
     {
         const float *dimg = d_image + 3 * vt.pix_base[v];
         if (tc.in0) { p0.g0 = dimg[pix0]; p0.g1 = dimg[W * H + pix0]; p0.g2 = dimg[2 * W * H + pix0]; }
         if (tc.in1) { p1.g0 = dimg[pix1]; p1.g1 = dimg[W * H + pix1]; p1.g2 = dimg[2 * W * H + pix1]; }
     }
-    __syncthreads();
-    const int maxlast = min(s_maxlast, n_items);
-    // back to front over chunk positions [0, maxlast)
-    for (int hi = maxlast; hi > 0; hi -= kRT) {
-        const int lo = max(0, hi - kRT);
-        __syncthreads();
-        {   // slot j <-> position hi - 1 - j
-            const int pa = hi - 1 - tid, pb = hi - 1 - (tid + kRThreads);
-            stage(S, tid, rec, vals, it.s0 + (uint32_t)max(pa, 0), pa >= lo, cap_cand, st, 53, true);
-            stage(S, tid + kRThreads, rec, vals, it.s0 + (uint32_t)max(pb, 0), pb >= lo, cap_cand, st, 53, true);
-        }
-        __syncthreads();
-        const int cnt = warp_list(S, hi - lo, tc.x0, tc.y0);
-        for (int li = 0; li < cnt; ++li) {
-            const int j = S.wl[warp][li];
-            const int p = hi - 1 - j;
+    // back to front over the warp's chunk positions [0, maxlast), 32 at a time
+    const int maxlast = min(__reduce_max_sync(0xffffffffu, max(p0.last, p1.last)), n_items);
+    for (int hi = maxlast; hi > 0; hi -= 32) {
+        const int pl = hi - 1 - lane;   // lane l <-> position hi - 1 - l: hits come back to front
+        const int cnt = warp_stage(WSw, rec, vals, it.s0 + (uint32_t)max(pl, 0), it.s0, pl >= 0, cap_cand, st, 53,
+                                   true, bx0, bx1, by0, by1);
+        for (int e = 0; e < cnt; ++e) {
+            const int p = WSw.pos[e];
             float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             bool contrib = false;
             if (p < p0.last || p < p1.last) {
-                const float4 a = S.a[j];
-                const float4 bb = S.b[j];
-                const float cb = S.c[j], io = S.io[j];
+                const float4 a = WSw.a[e];
+                const float4 bb = WSw.b[e];
+                const float cb = WSw.c[e], io = WSw.io[e];
                 if (p < p0.last) contrib |= bwd_step(p0, a, bb, cb, io, fpx, fy0, acc);
                 if (p < p1.last) contrib |= bwd_step(p1, a, bb, cb, io, fpx, fy1, acc);
             }
             if (__any_sync(0xffffffffu, contrib)) {
                 const float t8 = warp_sum8(acc);
                 const float t9 = warp_sum(acc[8]);
-                float *o = sgrad + 9 * (size_t)S.id[j];
+                float *o = sgrad + 9 * (size_t)WSw.id[e];
                 if ((lane & 3) == 0) atomicAdd(o + (((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1)), t8);
                 if (lane == 1) atomicAdd(o + 8, t9);
             }
         }
+        __syncwarp();
     }
 }
 

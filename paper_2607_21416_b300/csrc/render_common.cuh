@@ -112,78 +112,73 @@ __device__ __forceinline__ float *state_plane(float *state, int item, int plane)
     return state + ((size_t)item * kStateWords + plane) * kRT;
 }
 
-// Shared-memory records of one batch of kRT list positions.
-struct Staged {
-    float4 a[kRT];    // mean x, mean y, A, B
-    float4 b[kRT];    // C, L, r, g
-    float4 box[kRT];  // x0, x1, y0, y1: bounding box of the splat's alpha >= 1/255 region
-    float c[kRT];     // b
-    float io[kRT];    // 1 / opacity (backward only)
-    uint32_t id[kRT];
-    uint8_t wl[kRThreads / 32][kRT];   // per warp: staged slots whose box meets its 16x4 block
-    int wn[kRThreads / 32];
+// Per-warp record stage: a warp walks its item's list 32 positions at a
+// time; lane l reads position base + l and the warp keeps, in list order,
+// the splats whose alpha >= 1/255 region meets its 16x4 block.
+struct WarpStage {
+    float4 a[32];      // mean x, mean y, A, B
+    float4 b[32];      // C, L, r, g
+    float c[32];       // b
+    float io[32];      // 1 / opacity (backward)
+    uint32_t id[32];   // candidate id
+    int pos[32];       // list position within the item (0-based)
 };
 
-// Bounding box of {pixel : 2^(q + L) >= 1/255}, an ellipse since q is a
-// negative-definite quadratic form in (dx, dy): with Q = -[[A, B/2], [B/2, C]]
-// and s = log2(255) + L > 0, the region is d^T Q d <= s and its half-extents
-// are sqrt(s (Q^-1)_xx), sqrt(s (Q^-1)_yy).  The box is widened by 0.1 % + 0.01
-// px, far beyond the FP32 error of q, so every pixel outside it also fails the
-// alpha test as the kernels evaluate it: skipping those pairs is exact.
-__device__ __forceinline__ float4 alpha_box(float4 a, float4 b)
+// Whether the alpha >= 1/255 region of a splat record meets the pixel block
+// [bx0, bx1] x [by0, by1].  The region {2^(q + L) >= 1/255} is an ellipse
+// since q is a negative-definite quadratic form in (dx, dy): with Q = -[[A,
+// B/2], [B/2, C]] and s = log2(255) + L > 0 it is d^T Q d <= s, with
+// half-extents sqrt(s (Q^-1)_xx), sqrt(s (Q^-1)_yy).  Its bounding box, grown
+// by 0.1 % + 0.01 px (far beyond the FP32 error of q, so every pixel outside
+// also fails the alpha test as the kernels evaluate it: skipping is exact), is
+// tested against the block without a square root: with d the distance from
+// the mean to the block along an axis, less 0.01 px, d <= 1.001 sqrt(s
+// (Q^-1)_axis) reads d^2 det Q <= 1.002001 s (-C) for x and (-A) for y.
+__device__ __forceinline__ bool meets_block(float4 a, float4 b, float bx0, float bx1, float by0, float by1)
 {
     const float s = b.y + 7.994353436858858f;   // L + log2(255)
-    if (!(s > 0.f)) return make_float4(1e30f, -1e30f, 1e30f, -1e30f);   // opacity < 1/255: empty
-    const float det = a.z * b.x - 0.25f * a.w * a.w;                     // det Q = AC - B^2/4
-    if (!(det > 0.f)) return make_float4(-1e30f, 1e30f, -1e30f, 1e30f);  // degenerate: no culling
-    const float hx = sqrtf(s * (-b.x) / det) * 1.001f + 0.01f;
-    const float hy = sqrtf(s * (-a.z) / det) * 1.001f + 0.01f;
-    return make_float4(a.x - hx, a.x + hx, a.y - hy, a.y + hy);
+    if (!(s > 0.f)) return false;
+    const float det = a.z * b.x - 0.25f * a.w * a.w;
+    if (!(det > 0.f)) return true;
+    const float dx = fmaxf(fmaxf(bx0 - a.x, a.x - bx1) - 0.01f, 0.f);
+    const float dy = fmaxf(fmaxf(by0 - a.y, a.y - by1) - 0.01f, 0.f);
+    return dx * dx * det <= 1.002001f * s * (-b.x) && dy * dy * det <= 1.002001f * s * (-a.z);
 }
 
-// Stages list position `pos` into slot `slot` (when valid).
-__device__ __forceinline__ void stage(Staged &S, int slot, const float4 *__restrict__ rec,
-                                      const uint32_t *__restrict__ vals, uint32_t pos, bool valid,
-                                      long long cap_cand, const gs_status *st, int site, bool with_colour)
+// Reads list position `pos` of the item (when valid) and tests it against the
+// warp's block; the hits are compacted into the warp's stage in list order
+// (lane order).  Returns the number of hits.
+__device__ __forceinline__ int warp_stage(WarpStage &W, const float4 *__restrict__ rec,
+                                          const uint32_t *__restrict__ vals, uint32_t pos, uint32_t s0, bool valid,
+                                          long long cap_cand, const gs_status *st, int site, bool backward,
+                                          float bx0, float bx1, float by0, float by1)
 {
-    if (!valid) return;
-    uint32_t id = vals[pos];
-    if (!idx_ok(st, (long long)id, cap_cand, site)) id = 0;
-    S.id[slot] = id;
-    const float4 a = __ldg(&rec[3 * (size_t)id]);
-    const float4 b = __ldg(&rec[3 * (size_t)id + 1]);
-    S.a[slot] = a;
-    S.b[slot] = b;
-    S.box[slot] = alpha_box(a, b);
-    if (with_colour) {
-        S.c[slot] = __ldg(&rec[3 * (size_t)id + 2]).x;
-        S.io[slot] = exp2f(-b.y);
+    const int lane = threadIdx.x & 31;
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+    uint32_t id = 0;
+    bool hit = false;
+    if (valid) {
+        id = vals[pos];
+        if (!idx_ok(st, (long long)id, cap_cand, site)) id = 0;
+        a = __ldg(&rec[3 * (size_t)id]);
+        b = __ldg(&rec[3 * (size_t)id + 1]);
+        hit = meets_block(a, b, bx0, bx1, by0, by1);
     }
-}
-
-// Each warp lists, in slot order, the staged slots [0, n) whose alpha box meets
-// its 16x4 pixel block (call after the batch is staged and synchronised).
-__device__ __forceinline__ int warp_list(Staged &S, int n, int x0, int y0)
-{
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const float bx0 = (float)x0, bx1 = (float)(x0 + kTile - 1);
-    const float by0 = (float)(y0 + 4 * warp), by1 = by0 + 3.f;
-    unsigned lt;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
-    int cnt = 0;
-    for (int base = 0; base < n; base += 32) {
-        const int j = base + lane;
-        bool hit = false;
-        if (j < n) {
-            const float4 b = S.box[j];
-            hit = b.x <= bx1 && b.y >= bx0 && b.z <= by1 && b.w >= by0;
-        }
-        const unsigned m = __ballot_sync(0xffffffffu, hit);
-        if (hit) S.wl[warp][cnt + __popc(m & lt)] = (uint8_t)j;
-        cnt += __popc(m);
+    const unsigned m = __ballot_sync(0xffffffffu, hit);
+    if (hit) {
+        unsigned lt;
+        asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+        const int slot = __popc(m & lt);
+        W.a[slot] = a;
+        W.b[slot] = b;
+        W.c[slot] = __ldg(reinterpret_cast<const float *>(&rec[3 * (size_t)id + 2]));
+        if (backward) W.io[slot] = exp2f(-b.y);
+        W.id[slot] = id;
+        W.pos[slot] = (int)(pos - s0);
     }
     __syncwarp();
-    return cnt;
+    (void)lane;
+    return __popc(m);
 }
 
 struct RenderPlan {

@@ -154,10 +154,13 @@ __global__ void __launch_bounds__(kRThreads) chunk_kernel(const float4 *__restri
     if (FIX && plan.fix[blockIdx.x] == 0) return;
     Item it;
     if (!item_of(blockIdx.x, plan.item_base, vt.total_tiles, ranges, plan.L, &it)) return;
-    __shared__ Staged S;
-    const int tid = threadIdx.x, warp = tid >> 5;
+    __shared__ WarpStage WS[kRThreads / 32];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    WarpStage &W = WS[warp];
     const TileCoord tc = tile_coord(vt, it.t);
     const float fpx = (float)tc.px, fy0 = (float)tc.py, fy1 = (float)(tc.py + 1);
+    const float bx0 = (float)tc.x0, bx1 = bx0 + (float)(kTile - 1);
+    const float by0 = (float)(tc.y0 + 4 * warp), by1 = by0 + 3.f;
     const bool multi = it.nk > 1;
     const bool exact = !multi || it.k == 0 || FIX;
     const int item = it.base + it.k;
@@ -176,34 +179,32 @@ __global__ void __launch_bounds__(kRThreads) chunk_kernel(const float4 *__restri
         if (!p1.done) p1.T = tp[tc.pid0 + kTile];
     }
     const bool act0 = !p0.done, act1 = !p1.done;
-    for (uint32_t b0 = it.s0; b0 < it.s1; b0 += kRT) {
-        if (__syncthreads_count(p0.done && p1.done) == kRThreads) break;
-        stage(S, tid, rec, vals, b0 + tid, b0 + tid < it.s1, cap_cand, st, 42, true);
-        stage(S, tid + kRThreads, rec, vals, b0 + tid + kRThreads, b0 + tid + kRThreads < it.s1, cap_cand, st, 42,
-              true);
-        __syncthreads();
-        const int n = (int)min((uint32_t)kRT, it.s1 - b0);
-        const int base = (int)(b0 - it.s0);
-        const int cnt = warp_list(S, n, tc.x0, tc.y0);
+    // the warp walks the item's list on its own, 32 positions at a time
+    for (uint32_t b0 = it.s0; b0 < it.s1; b0 += 32) {
+        if (__all_sync(0xffffffffu, p0.done && p1.done)) break;
+        const uint32_t pos = b0 + lane;
+        const int cnt = warp_stage(W, rec, vals, pos, it.s0, pos < it.s1, cap_cand, st, 42, false, bx0, bx1, by0,
+                                   by1);
         if (exact) {
-            for (int li = 0; li < cnt; ++li) {
-                const int j = S.wl[warp][li];
-                const float4 a = S.a[j];
-                const float4 bb = S.b[j];
-                const float cb = S.c[j];
-                if (!p0.done) fwd_step<true>(p0, a, bb, cb, fpx, fy0, base + j + 1);
-                if (!p1.done) fwd_step<true>(p1, a, bb, cb, fpx, fy1, base + j + 1);
+            for (int e = 0; e < cnt; ++e) {
+                const float4 a = W.a[e];
+                const float4 bb = W.b[e];
+                const float cb = W.c[e];
+                const int q = W.pos[e] + 1;
+                if (!p0.done) fwd_step<true>(p0, a, bb, cb, fpx, fy0, q);
+                if (!p1.done) fwd_step<true>(p1, a, bb, cb, fpx, fy1, q);
             }
         } else {
-            for (int li = 0; li < cnt; ++li) {
-                const int j = S.wl[warp][li];
-                const float4 a = S.a[j];
-                const float4 bb = S.b[j];
-                const float cb = S.c[j];
-                if (!p0.done) fwd_step<false>(p0, a, bb, cb, fpx, fy0, base + j + 1);
-                if (!p1.done) fwd_step<false>(p1, a, bb, cb, fpx, fy1, base + j + 1);
+            for (int e = 0; e < cnt; ++e) {
+                const float4 a = W.a[e];
+                const float4 bb = W.b[e];
+                const float cb = W.c[e];
+                const int q = W.pos[e] + 1;
+                if (!p0.done) fwd_step<false>(p0, a, bb, cb, fpx, fy0, q);
+                if (!p1.done) fwd_step<false>(p1, a, bb, cb, fpx, fy1, q);
             }
         }
+        __syncwarp();
     }
     if (COUNT) {
         const int n_items = (int)(it.s1 - it.s0);
