@@ -88,19 +88,17 @@ __device__ __forceinline__ bool bwd_step(PixBwd &ps, const float4 a, const float
     return true;
 }
 
-__global__ void __launch_bounds__(kRThreads) render_bwd_kernel(
-    const float4 *__restrict__ rec, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
-    ViewTable vt, RenderPlan plan, float bg0, float bg1, float bg2, const float *__restrict__ d_image,
-    const float *__restrict__ T_final_in, const int32_t *__restrict__ last_in, float *__restrict__ sgrad,
-    long long cap_cand, const gs_status *st)
+__device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const uint32_t *__restrict__ vals,
+                                         const uint32_t *__restrict__ ranges, const ViewTable &vt,
+                                         const RenderPlan &plan, float bg0, float bg1, float bg2,
+                                         const float *__restrict__ d_image, const float *__restrict__ T_final_in,
+                                         const int32_t *__restrict__ last_in, float *__restrict__ sgrad,
+                                         long long cap_cand, const gs_status *st, int b, int warp, WarpStage &WSw)
 {
-    if (has_error(st)) return;
     Item it;
-    if (!item_of(blockIdx.x, plan.item_base, vt.total_tiles, ranges, plan.L, &it)) return;
-    __shared__ WarpStage WS[kRThreads / 32];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    WarpStage &WSw = WS[warp];
-    const TileCoord tc = tile_coord(vt, it.t);
+    if (!item_of(b, plan.item_base, vt.total_tiles, ranges, plan.L, &it)) return;
+    const int lane = threadIdx.x & 31, tid = warp * 32 + lane;
+    const TileCoord tc = tile_coord(vt, it.t, tid);
     const float fpx = (float)tc.px, fy0 = (float)tc.py, fy1 = (float)(tc.py + 1);
     const float bx0 = (float)tc.x0, bx1 = bx0 + (float)(kTile - 1);
     const float by0 = (float)(tc.y0 + 4 * warp), by1 = by0 + 3.f;
@@ -216,6 +214,24 @@ __global__ void __launch_bounds__(kRThreads) render_bwd_kernel(
         }
         __syncwarp();
     }
+}
+
+// Persistent reverse pass: each warp takes work units u = 4 item + w from the
+// counter and runs block w of item u / 4.
+__global__ void __launch_bounds__(kRThreads) render_bwd_kernel(
+    const float4 *__restrict__ rec, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
+    ViewTable vt, RenderPlan plan, float bg0, float bg1, float bg2, const float *__restrict__ d_image,
+    const float *__restrict__ T_final_in, const int32_t *__restrict__ last_in, float *__restrict__ sgrad,
+    long long cap_cand, const gs_status *st)
+{
+    if (has_error(st)) return;
+    __shared__ WarpStage WS[kRThreads / 32];
+    WarpStage &W = WS[threadIdx.x >> 5];
+    const int n_units = 4 * __ldg(plan.item_base + vt.total_tiles);
+    int32_t *counter = plan.counters + 2;
+    for (int u = next_unit(counter); u < n_units; u = next_unit(counter))
+        bwd_unit(rec, vals, ranges, vt, plan, bg0, bg1, bg2, d_image, T_final_in, last_in, sgrad, cap_cand, st, u >> 2,
+                 u & 3, W);
 }
 
 // Projection chain rule, one thread per candidate.
@@ -381,7 +397,8 @@ int launch_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splat
     const float4 *rec = reinterpret_cast<const float4 *>(sp->rec);
     if (vt.total_tiles > 0) {
         const RenderPlan plan = render_plan(vt, bins->cap_pairs, L, ws);
-        render_bwd_kernel<<<plan.max_items, kRThreads, 0, s>>>(rec, bins->vals, bins->ranges, vt, plan, bg[0], bg[1],
+        cudaMemsetAsync(plan.counters + 2, 0, sizeof(int32_t), s);
+        render_bwd_kernel<<<persistent_grid((const void *)render_bwd_kernel), kRThreads, 0, s>>>(rec, bins->vals, bins->ranges, vt, plan, bg[0], bg[1],
                                                           bg[2], d_image, T_final, last, sgrad->g,
                                                           std::min<long long>(sp->cap, cap_cand), st);
         count_launches(1);

@@ -53,14 +53,17 @@ __device__ __forceinline__ float splat_q(float4 a, float C, float px, float py, 
 // Unclamped alpha o exp(power) = 2^(q + L).
 __device__ __forceinline__ float splat_alpha(float q, float L) { return ex2_approx(__fadd_rn(q, L)); }
 
-// A thread owns pixels (px, py) and (px, py + 1) of its tile, with px = x0 +
-// (tid & 15), py = y0 + 2 (tid >> 4): tile-local pixel ids pid0 = (py - y0) *
-// 16 + (px - x0) and pid0 + 16.  Warp w covers the 16x4 block of rows 4w..4w+3.
+// Tile thread `tid` (0..127) owns pixels (px, py) and (px, py + 1), with px =
+// x0 + (tid & 15), py = y0 + 2 (tid >> 4): tile-local pixel ids pid0 = (py -
+// y0) * 16 + (px - x0) and pid0 + 16.  Tile warp w = tid >> 5 covers the 16x4
+// block of rows 4w..4w+3.  The compositing kernels are persistent: each warp
+// takes work units (item, block w) from a device counter and plays tile warp
+// w of that item.
 struct TileCoord {
     int v, x0, y0, px, py, pid0;
     bool in0, in1;
 };
-__device__ __forceinline__ TileCoord tile_coord(const ViewTable &vt, int t)
+__device__ __forceinline__ TileCoord tile_coord(const ViewTable &vt, int t, int tid)
 {
     TileCoord c;
     c.v = view_of_tile(vt, t);
@@ -68,9 +71,9 @@ __device__ __forceinline__ TileCoord tile_coord(const ViewTable &vt, int t)
     const int tx = local % vt.TX[c.v], ty = local / vt.TX[c.v];
     c.x0 = tx * kTile;
     c.y0 = ty * kTile;
-    c.px = c.x0 + (threadIdx.x & (kTile - 1));
-    c.py = c.y0 + 2 * (threadIdx.x >> 4);
-    c.pid0 = 2 * (threadIdx.x >> 4) * kTile + (threadIdx.x & (kTile - 1));
+    c.px = c.x0 + (tid & (kTile - 1));
+    c.py = c.y0 + 2 * (tid >> 4);
+    c.pid0 = 2 * (tid >> 4) * kTile + (tid & (kTile - 1));
     c.in0 = c.px < vt.W[c.v] && c.py < vt.H[c.v];
     c.in1 = c.px < vt.W[c.v] && c.py + 1 < vt.H[c.v];
     return c;
@@ -181,8 +184,17 @@ __device__ __forceinline__ int warp_stage(WarpStage &W, const float4 *__restrict
     return __popc(m);
 }
 
+// Next work unit of the calling warp from a device counter (lane 0 takes it).
+__device__ __forceinline__ int next_unit(int32_t *counter)
+{
+    int u = 0;
+    if ((threadIdx.x & 31) == 0) u = atomicAdd(counter, 1);
+    return __shfl_sync(0xffffffffu, u, 0);
+}
+
 struct RenderPlan {
     const int32_t *item_base;   // [T+1]
+    int32_t *counters;          // [4] work-unit counters: forward, fix-up, backward
     int32_t *fix;               // [max_items] items with pixels to composite again
     float *state;               // [max_items][kStateWords][256]
     int L;
@@ -190,5 +202,9 @@ struct RenderPlan {
 };
 
 RenderPlan render_plan(const ViewTable &vt, long long cap_pairs, int L, void *ws);
+
+// CTAs of 128 threads of a persistent compositing kernel that fit on the
+// device at once (registers, shared memory, warps), times the SM count.
+int persistent_grid(const void *kernel);
 
 }  // namespace gs

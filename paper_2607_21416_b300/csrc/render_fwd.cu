@@ -23,9 +23,11 @@ namespace gs {
 
 __global__ void __launch_bounds__(1024) plan_kernel(const uint32_t *__restrict__ ranges, int T, int L,
                                                     int max_items, int32_t *__restrict__ item_base,
-                                                    int32_t *__restrict__ fix, const gs_status *st)
+                                                    int32_t *__restrict__ fix, int32_t *__restrict__ counters,
+                                                    const gs_status *st)
 {
     for (int i = threadIdx.x; i < max_items; i += blockDim.x) fix[i] = 0;
+    if (threadIdx.x < 4) counters[threadIdx.x] = 0;
     __shared__ int s_warp[32];
     __shared__ long long s_carry;
     if (threadIdx.x == 0) s_carry = 0;
@@ -141,23 +143,18 @@ __device__ __forceinline__ void count_add(unsigned long long *n_eval, unsigned l
 // the stop) and the pairs composited are counted for the chunks whose activity
 // is decided here; the combine step counts the others.
 template <bool COUNT, bool FIX>
-__global__ void __launch_bounds__(kRThreads) chunk_kernel(const float4 *__restrict__ rec,
-                                                          const uint32_t *__restrict__ vals,
-                                                          const uint32_t *__restrict__ ranges, ViewTable vt,
-                                                          RenderPlan plan, float bg0, float bg1, float bg2,
-                                                          float *__restrict__ image, float *__restrict__ T_final,
-                                                          int32_t *__restrict__ last,
-                                                          unsigned long long *__restrict__ n_eval,
-                                                          long long cap_cand, const gs_status *st)
+__device__ __forceinline__ void chunk_unit(const float4 *__restrict__ rec, const uint32_t *__restrict__ vals,
+                                           const uint32_t *__restrict__ ranges, const ViewTable &vt,
+                                           const RenderPlan &plan, float bg0, float bg1, float bg2,
+                                           float *__restrict__ image, float *__restrict__ T_final,
+                                           int32_t *__restrict__ last, unsigned long long *__restrict__ n_eval,
+                                           long long cap_cand, const gs_status *st, int b, int warp, WarpStage &W)
 {
-    if (has_error(st)) return;
-    if (FIX && plan.fix[blockIdx.x] == 0) return;
+    if (FIX && plan.fix[b] == 0) return;
     Item it;
-    if (!item_of(blockIdx.x, plan.item_base, vt.total_tiles, ranges, plan.L, &it)) return;
-    __shared__ WarpStage WS[kRThreads / 32];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    WarpStage &W = WS[warp];
-    const TileCoord tc = tile_coord(vt, it.t);
+    if (!item_of(b, plan.item_base, vt.total_tiles, ranges, plan.L, &it)) return;
+    const int lane = threadIdx.x & 31, tid = warp * 32 + lane;
+    const TileCoord tc = tile_coord(vt, it.t, tid);
     const float fpx = (float)tc.px, fy0 = (float)tc.py, fy1 = (float)(tc.py + 1);
     const float bx0 = (float)tc.x0, bx1 = bx0 + (float)(kTile - 1);
     const float by0 = (float)(tc.y0 + 4 * warp), by1 = by0 + 3.f;
@@ -251,6 +248,28 @@ __global__ void __launch_bounds__(kRThreads) chunk_kernel(const float4 *__restri
     }
 }
 
+// Persistent compositing: each warp takes work units u = 4 item + w from the
+// counter and composites block w of item u / 4.
+template <bool COUNT, bool FIX>
+__global__ void __launch_bounds__(kRThreads) chunk_kernel(const float4 *__restrict__ rec,
+                                                          const uint32_t *__restrict__ vals,
+                                                          const uint32_t *__restrict__ ranges, ViewTable vt,
+                                                          RenderPlan plan, float bg0, float bg1, float bg2,
+                                                          float *__restrict__ image, float *__restrict__ T_final,
+                                                          int32_t *__restrict__ last,
+                                                          unsigned long long *__restrict__ n_eval,
+                                                          long long cap_cand, const gs_status *st)
+{
+    if (has_error(st)) return;
+    __shared__ WarpStage WS[kRThreads / 32];
+    WarpStage &W = WS[threadIdx.x >> 5];
+    const int n_units = 4 * __ldg(plan.item_base + vt.total_tiles);
+    int32_t *counter = plan.counters + (FIX ? 1 : 0);
+    for (int u = next_unit(counter); u < n_units; u = next_unit(counter))
+        chunk_unit<COUNT, FIX>(rec, vals, ranges, vt, plan, bg0, bg1, bg2, image, T_final, last, n_eval, cap_cand, st,
+                               u >> 2, u & 3, W);
+}
+
 // Multi-chunk tiles, per pixel: chunk 0 is exact; every later chunk k is
 // scaled by the transmittance T0 in front of it (its state becomes the
 // chunk's true contribution) while T0 * Tprod_k >= 1e-4 -- no splat of the
@@ -269,7 +288,7 @@ __global__ void __launch_bounds__(kRThreads) combine_kernel(const uint32_t *__re
     const int t = blockIdx.x;
     const int base = plan.item_base[t], nk = plan.item_base[t + 1] - base;
     if (nk <= 1) return;
-    const TileCoord tc = tile_coord(vt, t);
+    const TileCoord tc = tile_coord(vt, t, threadIdx.x);
     const uint32_t s_start = ranges[2 * t], s_end = ranges[2 * t + 1];
     unsigned long long nev = 0, ncomp = 0;
     for (int half = 0; half < 2; ++half) {
@@ -328,6 +347,23 @@ __global__ void __launch_bounds__(kRThreads) combine_kernel(const uint32_t *__re
     if (COUNT) count_add(n_eval, nev, ncomp);
 }
 
+int persistent_grid(const void *kernel)
+{
+    static int dev_smem = 0, dev_reserve = 0;
+    if (dev_smem == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&dev_reserve, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    }
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return sm_count();
+    int occ = 64 / (kRThreads / 32);                                             // warps per SM
+    occ = std::min(occ, 65536 / std::max(1, fa.numRegs * kRThreads));           // registers
+    occ = std::min(occ, dev_smem / std::max(1, (int)fa.sharedSizeBytes + dev_reserve));
+    return sm_count() * std::max(1, occ);
+}
+
 // ------------------------------------------------------------------- L1
 __global__ void __launch_bounds__(256) l1_kernel(const float *__restrict__ image, const float *__restrict__ target,
                                                  ViewTable vt, float *__restrict__ loss, float *__restrict__ d_image)
@@ -355,20 +391,22 @@ int render_max_items(const ViewTable &vt, long long cap_pairs, int L)
 size_t render_workspace_bytes(const ViewTable &vt, long long cap_pairs, int L)
 {
     const long long items = render_max_items(vt, cap_pairs, L);
-    return align_up(sizeof(int32_t) * ((size_t)vt.total_tiles + 1), 256) + align_up(sizeof(int32_t) * (size_t)items, 256) +
-           align_up(sizeof(float) * (size_t)items * kStateWords * kRT, 256);
+    return align_up(sizeof(int32_t) * ((size_t)vt.total_tiles + 1), 256) + 256 +
+           align_up(sizeof(int32_t) * (size_t)items, 256) + align_up(sizeof(float) * (size_t)items * kStateWords * kRT, 256);
 }
 
-// Workspace: item_base [T + 1] | fix flags [max_items] | state [max_items][kStateWords][256]
+// Workspace: item_base [T + 1] | counters [4] | fix flags [max_items] | state [max_items][kStateWords][256]
 RenderPlan render_plan(const ViewTable &vt, long long cap_pairs, int L, void *ws)
 {
     RenderPlan p;
     p.L = L;
     p.max_items = render_max_items(vt, cap_pairs, L);
     char *w = reinterpret_cast<char *>(ws);
-    const size_t o1 = align_up(sizeof(int32_t) * ((size_t)vt.total_tiles + 1), 256);
+    const size_t o0 = align_up(sizeof(int32_t) * ((size_t)vt.total_tiles + 1), 256);
+    const size_t o1 = o0 + 256;
     const size_t o2 = o1 + align_up(sizeof(int32_t) * (size_t)p.max_items, 256);
     p.item_base = reinterpret_cast<int32_t *>(w);
+    p.counters = reinterpret_cast<int32_t *>(w + o0);
     p.fix = reinterpret_cast<int32_t *>(w + o1);
     p.state = reinterpret_cast<float *>(w + o2);
     return p;
@@ -379,12 +417,12 @@ static void launch_items(const float4 *rec, const gs_bins *bins, const ViewTable
                          const float bg[3], float *image, float *T_final, int32_t *last, unsigned long long *n_eval,
                          long long cap, gs_status *st, cudaStream_t s)
 {
-    chunk_kernel<COUNT, false><<<plan.max_items, kRThreads, 0, s>>>(rec, bins->vals, bins->ranges, vt, plan, bg[0],
+    chunk_kernel<COUNT, false><<<persistent_grid((const void *)chunk_kernel<COUNT, false>), kRThreads, 0, s>>>(rec, bins->vals, bins->ranges, vt, plan, bg[0],
                                                                    bg[1], bg[2], image, T_final, last, n_eval, cap,
                                                                    st);
     combine_kernel<COUNT><<<vt.total_tiles, kRThreads, 0, s>>>(bins->ranges, vt, plan, bg[0], bg[1], bg[2], image,
                                                               T_final, last, n_eval, st);
-    chunk_kernel<COUNT, true><<<plan.max_items, kRThreads, 0, s>>>(rec, bins->vals, bins->ranges, vt, plan, bg[0],
+    chunk_kernel<COUNT, true><<<persistent_grid((const void *)chunk_kernel<COUNT, true>), kRThreads, 0, s>>>(rec, bins->vals, bins->ranges, vt, plan, bg[0],
                                                                   bg[1], bg[2], image, T_final, last, n_eval, cap,
                                                                   st);
 }
@@ -397,7 +435,7 @@ int launch_render_fwd(const gs_splats *sp, const gs_bins *bins, const ViewTable 
     const float4 *rec = reinterpret_cast<const float4 *>(sp->rec);
     const RenderPlan plan = render_plan(vt, bins->cap_pairs, L, ws);
     plan_kernel<<<1, 1024, 0, s>>>(bins->ranges, vt.total_tiles, L, plan.max_items,
-                                   const_cast<int32_t *>(plan.item_base), plan.fix, st);
+                                   const_cast<int32_t *>(plan.item_base), plan.fix, plan.counters, st);
     if (n_eval) {
         cudaMemsetAsync(n_eval, 0, 2 * sizeof(long long), s);
         launch_items<true>(rec, bins, vt, plan, bg, image, T_final, last,
