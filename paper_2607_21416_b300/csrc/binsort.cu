@@ -7,8 +7,10 @@
 //      candidate-id order;
 //   2. stable radix sort of those splats on their 32-bit depth bits (ties
 //      keep id order);
-//   3. scan the tile counts in depth order and emit one (tile id, splat id)
-//      pair per covered tile;
+//   3. scan the tile counts in depth order (per-splat pair offsets) and emit
+//      one (tile id, splat id) pair per covered tile, load-balanced: each
+//      CTA writes 2048 consecutive pairs and finds each pair's splat by
+//      binary search over the offsets;
 //   4. stable radix sort of the pairs on the tile id (only the bits the tile
 //      count needs), which keeps depth-then-id order inside each tile;
 //   5. tile ranges [start, end) and, on request, the 64-bit keys.
@@ -318,12 +320,11 @@ __global__ void __launch_bounds__(kSortThreads) count_pairs_kernel(
     if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
 }
 
-// Emission: every covering splat (in depth order) writes its (tile, id) pairs.
-__global__ void __launch_bounds__(kSortThreads) emit_pairs_kernel(
+// Per-splat pair offsets in depth order: offs[i] = sum of the tile counts of
+// splats 0..i-1 (block prefixes from scan_block_sums).
+__global__ void __launch_bounds__(kSortThreads) pair_offsets_kernel(
     const uint32_t *__restrict__ ids, const uint32_t *__restrict__ n_ptr, const int32_t *__restrict__ tiles,
-    const float4 *__restrict__ rec, const int32_t *__restrict__ view_start, int k,
-    const uint32_t *__restrict__ block_off, uint32_t *__restrict__ tkeys, uint32_t *__restrict__ tvals,
-    ViewTable vt, long long cap_cand, long long cap_pairs, const gs_status *st)
+    const uint32_t *__restrict__ block_off, uint32_t *__restrict__ offs, long long cap_cand, const gs_status *st)
 {
     if (has_error(st)) return;
     const uint32_t S = *n_ptr;
@@ -333,34 +334,81 @@ __global__ void __launch_bounds__(kSortThreads) emit_pairs_kernel(
     uint32_t base = block_off[blockIdx.x];
     for (uint32_t tb = t0 * kSortTile; tb < min(S, t1 * kSortTile); tb += kSortThreads) {
         const uint32_t i = tb + threadIdx.x;
-        uint32_t id = 0, cnt = 0;
+        uint32_t cnt = 0;
         if (i < S) {
-            id = ids[i];
+            const uint32_t id = ids[i];
             if (idx_ok(st, id, cap_cand, 35)) cnt = (uint32_t)__ldg(tiles + id);
         }
         uint32_t tot;
-        uint32_t off = base + scan256(cnt, s_warp, &tot);
-        if (cnt) {
-            const float4 r2 = __ldg(&rec[3 * (size_t)id + 2]);
-            const uint32_t rx = __float_as_uint(r2.z), ry = __float_as_uint(r2.w);
-            const int x0 = rx & 0xffff, x1 = rx >> 16, y0 = ry & 0xffff, y1 = ry >> 16;
-            const int v = view_of_row(view_start, vt.V, (int)(id / (uint32_t)k));
-            const uint32_t tbase = (uint32_t)vt.tile_base[v];
-            const int TXv = vt.TX[v];
-            if ((long long)(x1 - x0) * (y1 - y0) != (long long)cnt || x1 > TXv || y1 > vt.TY[v]) {
-                idx_ok(st, (long long)id, -1, 36);
-                cnt = 0;
-            }
-            if (cnt && !idx_ok(st, (long long)off + cnt - 1, cap_pairs, 37)) cnt = 0;
-            if (cnt)
-                for (int y = y0; y < y1; ++y)
-                    for (int x = x0; x < x1; ++x) {
-                        tkeys[off] = tbase + (uint32_t)(y * TXv + x);
-                        tvals[off] = id;
-                        ++off;
-                    }
-        }
+        const uint32_t off = base + scan256(cnt, s_warp, &tot);
+        if (i < S) offs[i] = off;
         base += tot;
+    }
+}
+
+constexpr int kEmitPairs = 2048;   // pairs written per CTA and round
+
+// Load-balanced emission: CTA rounds write pairs [p0, p0 + 2048).  The splats
+// that own those pairs (at most 2048, every compacted splat owns >= 1) are
+// staged with their rectangle's first tile, width and the view's tile row
+// length; each pair finds its splat by binary search over the staged offsets
+// and writes (tile id, splat id) -- pair t of a splat is tile (t % w, t / w)
+// of its rectangle, row-major.
+__global__ void __launch_bounds__(kSortThreads) emit_pairs_kernel(
+    const uint32_t *__restrict__ ids, const uint32_t *__restrict__ n_ptr, const uint32_t *__restrict__ np_ptr,
+    const uint32_t *__restrict__ offs, const int32_t *__restrict__ tiles, const float4 *__restrict__ rec,
+    const int32_t *__restrict__ view_start, int k, uint32_t *__restrict__ tkeys, uint32_t *__restrict__ tvals,
+    ViewTable vt, long long cap_cand, const gs_status *st)
+{
+    if (has_error(st)) return;
+    const uint32_t S = *n_ptr, P = *np_ptr;
+    __shared__ uint32_t s_off[kEmitPairs], s_t00[kEmitPairs], s_id[kEmitPairs];
+    __shared__ uint16_t s_w[kEmitPairs], s_tx[kEmitPairs];
+    __shared__ uint32_t s_first, s_count;
+    for (uint32_t p0 = blockIdx.x * (uint32_t)kEmitPairs; p0 < P; p0 += gridDim.x * (uint32_t)kEmitPairs) {
+        const uint32_t p1 = min(P, p0 + (uint32_t)kEmitPairs);
+        if (threadIdx.x == 0) {   // splats owning p0 and p1 - 1: last s with offs[s] <= p
+            uint32_t a = 0, b = S - 1;
+            while (a < b) { const uint32_t m = (a + b + 1) >> 1; if (offs[m] <= p0) a = m; else b = m - 1; }
+            uint32_t c = a, d = S - 1;
+            while (c < d) { const uint32_t m = (c + d + 1) >> 1; if (offs[m] <= p1 - 1) c = m; else d = m - 1; }
+            s_first = a;
+            s_count = idx_ok(st, (long long)(c - a), kEmitPairs, 39) ? c - a + 1 : 0;
+        }
+        __syncthreads();
+        const uint32_t sa = s_first, ns = s_count;
+        for (uint32_t j = threadIdx.x; j < ns; j += kSortThreads) {
+            const uint32_t sidx = sa + j;
+            const uint32_t id = ids[sidx];
+            uint32_t t00 = 0, w = 1, tx = 1;
+            if (idx_ok(st, id, cap_cand, 36)) {
+                const float4 r2 = __ldg(&rec[3 * (size_t)id + 2]);
+                const uint32_t rx = __float_as_uint(r2.z), ry = __float_as_uint(r2.w);
+                const int x0 = rx & 0xffff, x1 = rx >> 16, y0 = ry & 0xffff, y1 = ry >> 16;
+                const int v = view_of_row(view_start, vt.V, (int)(id / (uint32_t)k));
+                const int cnt = __ldg(tiles + id);
+                if ((long long)(x1 - x0) * (y1 - y0) != (long long)cnt || x1 > vt.TX[v] || y1 > vt.TY[v] || x1 <= x0)
+                    idx_ok(st, (long long)id, -1, 36);
+                w = (uint32_t)max(x1 - x0, 1);
+                tx = (uint32_t)vt.TX[v];
+                t00 = (uint32_t)vt.tile_base[v] + (uint32_t)(y0 * vt.TX[v] + x0);
+            }
+            s_off[j] = offs[sidx];
+            s_t00[j] = t00;
+            s_w[j] = (uint16_t)w;
+            s_tx[j] = (uint16_t)tx;
+            s_id[j] = id;
+        }
+        __syncthreads();
+        for (uint32_t p = p0 + threadIdx.x; ns > 0 && p < p1; p += kSortThreads) {
+            uint32_t a = 0, b = ns - 1;
+            while (a < b) { const uint32_t m = (a + b + 1) >> 1; if (s_off[m] <= p) a = m; else b = m - 1; }
+            const uint32_t t = p - s_off[a], w = s_w[a];
+            const uint32_t yy = t / w, xx = t - yy * w;
+            tkeys[p] = s_t00[a] + yy * (uint32_t)s_tx[a] + xx;
+            tvals[p] = s_id[a];
+        }
+        __syncthreads();
     }
 }
 
@@ -395,7 +443,7 @@ __global__ void __launch_bounds__(256) keys_kernel(const uint32_t *__restrict__ 
 
 // ------------------------------------------------------------------ driver
 struct SortLayout {
-    size_t ids_a, ids_b, dk_a, dk_b, tk_a, tk_b, tv_b, hist, totals, sums, counts, total;
+    size_t ids_a, ids_b, dk_a, dk_b, offs, tk_a, tk_b, tv_b, hist, totals, sums, counts, total;
     int nb;
 };
 
@@ -411,6 +459,7 @@ static SortLayout layout(long long cap_cand, long long cap_pairs)
     L.ids_b = take(sizeof(uint32_t) * std::max<long long>(cap_cand, 1));
     L.dk_a = take(sizeof(uint32_t) * std::max<long long>(cap_cand, 1));
     L.dk_b = take(sizeof(uint32_t) * std::max<long long>(cap_cand, 1));
+    L.offs = take(sizeof(uint32_t) * std::max<long long>(cap_cand, 1));
     L.tk_a = take(sizeof(uint32_t) * std::max<long long>(cap_pairs, 1));
     L.tk_b = take(sizeof(uint32_t) * std::max<long long>(cap_pairs, 1));
     L.tv_b = take(sizeof(uint32_t) * std::max<long long>(cap_pairs, 1));
@@ -455,7 +504,7 @@ int launch_bin_sort(const gs_splats *sp, int k, const int32_t *view_start, long 
     uint32_t *ids_a = (uint32_t *)(w + L.ids_a), *ids_b = (uint32_t *)(w + L.ids_b);
     uint32_t *dk_a = (uint32_t *)(w + L.dk_a), *dk_b = (uint32_t *)(w + L.dk_b);
     uint32_t *tk_a = (uint32_t *)(w + L.tk_a), *tk_b = (uint32_t *)(w + L.tk_b);
-    uint32_t *tv_b = (uint32_t *)(w + L.tv_b);
+    uint32_t *tv_b = (uint32_t *)(w + L.tv_b), *offs = (uint32_t *)(w + L.offs);
     uint32_t *hist = (uint32_t *)(w + L.hist), *totals = (uint32_t *)(w + L.totals);
     uint32_t *sums = (uint32_t *)(w + L.sums), *counts = (uint32_t *)(w + L.counts);
     const float4 *rec = reinterpret_cast<const float4 *>(sp->rec);
@@ -480,9 +529,10 @@ int launch_bin_sort(const gs_splats *sp, int k, const int32_t *view_start, long 
     // choose the emission buffers so that the last pass lands in bins->vals
     uint32_t *ek = tk_a, *ev = (passes % 2 == 0) ? bins->vals : tv_b;
     uint32_t *ok = tk_b, *ov = (passes % 2 == 0) ? tv_b : bins->vals;
-    emit_pairs_kernel<<<nb, kSortThreads, 0, s>>>(ids_s, n_splats, sp->tiles, rec, view_start, k, sums, ek,
-                                                  ev, vt, cap_cand, bins->cap_pairs, st);
-    count_launches(3);
+    pair_offsets_kernel<<<nb, kSortThreads, 0, s>>>(ids_s, n_splats, sp->tiles, sums, offs, cap_cand, st);
+    emit_pairs_kernel<<<sm_count() * 4, kSortThreads, 0, s>>>(ids_s, n_splats, n_pairs, offs, sp->tiles, rec,
+                                                              view_start, k, ek, ev, vt, cap_cand, st);
+    count_launches(4);
     // 4. stable sort on the tile id
     uint32_t *tk_s, *tv_s;
     radix_sort(ek, ev, ok, ov, n_pairs, tile_bits, hist, totals, nb, st, s, &tk_s, &tv_s);

@@ -216,8 +216,8 @@ __device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const u
     }
 }
 
-// Persistent reverse pass: each warp takes work units u = 4 item + w from the
-// counter and runs block w of item u / 4.
+// Persistent reverse pass: each warp takes work units u = 4 i + w from the
+// counter and runs block w of item i.
 __global__ void __launch_bounds__(kRThreads) render_bwd_kernel(
     const float4 *__restrict__ rec, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
     ViewTable vt, RenderPlan plan, float bg0, float bg1, float bg2, const float *__restrict__ d_image,

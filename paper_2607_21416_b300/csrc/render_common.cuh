@@ -195,7 +195,8 @@ __device__ __forceinline__ int next_unit(int32_t *counter)
 struct RenderPlan {
     const int32_t *item_base;   // [T+1]
     int32_t *counters;          // [4] work-unit counters: forward, fix-up, backward
-    int32_t *fix;               // [max_items] items with pixels to composite again
+    int32_t *fix;               // [max_items] flags: items with pixels to composite again
+    int32_t *fix_list;          // [max_items] those items, counters[3] of them
     float *state;               // [max_items][kStateWords][256]
     int L;
     int max_items;

@@ -248,8 +248,9 @@ __device__ __forceinline__ void chunk_unit(const float4 *__restrict__ rec, const
     }
 }
 
-// Persistent compositing: each warp takes work units u = 4 item + w from the
-// counter and composites block w of item u / 4.
+// Persistent compositing: each warp takes work units u = 4 i + w from the
+// counter and composites block w of item i (the fix-up pass: of the i-th
+// marked item).
 template <bool COUNT, bool FIX>
 __global__ void __launch_bounds__(kRThreads) chunk_kernel(const float4 *__restrict__ rec,
                                                           const uint32_t *__restrict__ vals,
@@ -263,11 +264,14 @@ __global__ void __launch_bounds__(kRThreads) chunk_kernel(const float4 *__restri
     if (has_error(st)) return;
     __shared__ WarpStage WS[kRThreads / 32];
     WarpStage &W = WS[threadIdx.x >> 5];
-    const int n_units = 4 * __ldg(plan.item_base + vt.total_tiles);
+    const int n_units =
+        4 * (FIX ? *(volatile const int32_t *)(plan.counters + 3) : __ldg(plan.item_base + vt.total_tiles));
     int32_t *counter = plan.counters + (FIX ? 1 : 0);
-    for (int u = next_unit(counter); u < n_units; u = next_unit(counter))
+    for (int u = next_unit(counter); u < n_units; u = next_unit(counter)) {
+        const int b = FIX ? plan.fix_list[u >> 2] : (u >> 2);
         chunk_unit<COUNT, FIX>(rec, vals, ranges, vt, plan, bg0, bg1, bg2, image, T_final, last, n_eval, cap_cand, st,
-                               u >> 2, u & 3, W);
+                               b, u & 3, W);
+    }
 }
 
 // Multi-chunk tiles, per pixel: chunk 0 is exact; every later chunk k is
@@ -336,7 +340,7 @@ __global__ void __launch_bounds__(kRThreads) combine_kernel(const uint32_t *__re
                 c1[pix] = C1;
                 c2[pix] = C2;
                 lp[pix] = -1;
-                plan.fix[item] = 1;
+                if (atomicExch(plan.fix + item, 1) == 0) plan.fix_list[atomicAdd(plan.counters + 3, 1)] = item;
                 if (last) last[vt.pix_base[tc.v] + (long long)py * vt.W[tc.v] + tc.px] = lastg;
                 marked = true;
                 break;
@@ -392,10 +396,12 @@ size_t render_workspace_bytes(const ViewTable &vt, long long cap_pairs, int L)
 {
     const long long items = render_max_items(vt, cap_pairs, L);
     return align_up(sizeof(int32_t) * ((size_t)vt.total_tiles + 1), 256) + 256 +
-           align_up(sizeof(int32_t) * (size_t)items, 256) + align_up(sizeof(float) * (size_t)items * kStateWords * kRT, 256);
+           2 * align_up(sizeof(int32_t) * (size_t)items, 256) +
+           align_up(sizeof(float) * (size_t)items * kStateWords * kRT, 256);
 }
 
-// Workspace: item_base [T + 1] | counters [4] | fix flags [max_items] | state [max_items][kStateWords][256]
+// Workspace: item_base [T + 1] | counters [4] | fix flags [max_items] | fix list [max_items] |
+// state [max_items][kStateWords][256]
 RenderPlan render_plan(const ViewTable &vt, long long cap_pairs, int L, void *ws)
 {
     RenderPlan p;
@@ -404,10 +410,11 @@ RenderPlan render_plan(const ViewTable &vt, long long cap_pairs, int L, void *ws
     char *w = reinterpret_cast<char *>(ws);
     const size_t o0 = align_up(sizeof(int32_t) * ((size_t)vt.total_tiles + 1), 256);
     const size_t o1 = o0 + 256;
-    const size_t o2 = o1 + align_up(sizeof(int32_t) * (size_t)p.max_items, 256);
+    const size_t o2 = o1 + 2 * align_up(sizeof(int32_t) * (size_t)p.max_items, 256);
     p.item_base = reinterpret_cast<int32_t *>(w);
     p.counters = reinterpret_cast<int32_t *>(w + o0);
     p.fix = reinterpret_cast<int32_t *>(w + o1);
+    p.fix_list = reinterpret_cast<int32_t *>(w + o1 + align_up(sizeof(int32_t) * (size_t)p.max_items, 256));
     p.state = reinterpret_cast<float *>(w + o2);
     return p;
 }
