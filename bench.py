@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     p.add_argument("--anchors", type=int, default=200000)
     p.add_argument("--views", type=int, default=8)
+    p.add_argument("--chunk", type=int, default=0,
+                   help="splats per compositing work item (0: the library default)")
     p.add_argument("--state", default="recompute", choices=["recompute", "store"],
                    help="per-pixel forward state of single-chunk tiles: recomputed in the backward "
                         "or written by the forward (8 B per pixel)")
@@ -131,7 +133,7 @@ def run_ours(args, rank, world, dist):
     store = args.state == "store"
     torch.cuda.reset_peak_memory_stats()
     ms = pipeline.MappingStep(views, anchors, precision=prec, cap_rows=int(1.2 * scene.N * 0.6 * views.V),
-                              store_state=store)
+                              store_state=store, chunk=args.chunk)
     ms.prepare(target)    # sizes the buffers (host-synchronised) and captures the public step's graph
     rp = ms.rp
     torch.cuda.synchronize()

@@ -238,10 +238,13 @@ int gs_bin_sort(const gs_splats *sp, int32_t k, const int32_t *view_start, int64
  * stop before a splat whose T(1 - alpha) < 1e-4; C += c alpha T; T *= 1 -
  * alpha.  image = C + T bg.  bg: HOST float[3].
  * Work items: each tile's list is cut into chunks of `chunk` splats (0 selects
- * 2048; otherwise 256 .. 2^24), one CTA each, so that a few very long tiles
- * do not serialise the launch; a chunk starts from the product of the
- * transmittances of the chunks in front of it, which reproduces the
- * front-to-back order exactly.  ws / ws_bytes: gs_render_workspace bytes,
+ * 512; otherwise 256 .. 2^24), and every 16x4 pixel block of every chunk is a
+ * work unit that persistent warps take from a device counter, so that a few
+ * very long tiles do not serialise the launch.  Later chunks of a tile are
+ * composited on their own transmittance and scaled by the transmittance in
+ * front of them; a chunk that holds a pixel's stop is composited again from
+ * its entering transmittance, which reproduces the front-to-back order and
+ * the stop rule exactly.  ws / ws_bytes: gs_render_workspace bytes,
  * 256-byte aligned; gs_render_bwd needs the same workspace, untouched, and
  * the same `chunk`.  T_final (float per pixel) and last (int32 per pixel:
  * 1-based list position of the last composited splat) are optional outputs

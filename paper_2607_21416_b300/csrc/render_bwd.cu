@@ -111,29 +111,24 @@ __device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const u
     p0.B0 = p0.B1 = p0.B2 = p1.B0 = p1.B1 = p1.B2 = 0.f;
     p0.last = p1.last = 0;
     if (it.nk > 1) {
-        // forward state: end transmittance, last position, colour behind the chunk
+        // forward state of the chunk: entering transmittance (activity), end
+        // transmittance, last position, colour composited behind it
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
             PixBwd &ps = half ? p1 : p0;
             const int pix = tc.pid0 + half * kTile;
-            float T0 = 1.f, Tf = 1.f;
-            for (int j = 0; j < it.nk; ++j) {
-                if (!(T0 >= kTMin)) break;
-                const int item = it.base + j;
-                if (j > it.k) {
-                    ps.B0 += state_plane(plan.state, item, 2)[pix];
-                    ps.B1 += state_plane(plan.state, item, 3)[pix];
-                    ps.B2 += state_plane(plan.state, item, 4)[pix];
-                }
-                Tf = state_plane(plan.state, item, 1)[pix];
-                if (j == it.k) {
-                    ps.T = Tf;
-                    ps.last = reinterpret_cast<const int *>(state_plane(plan.state, item, 5))[pix];
-                }
-                if (j < it.nk - 1) T0 = __fmul_rn(T0, state_plane(plan.state, item, 0)[pix]);
+            const int item = it.base + it.k;
+            const float T0 = state_plane(plan.state, item, 0)[pix];
+            if (T0 >= kTMin && (half ? tc.in1 : tc.in0)) {
+                ps.T = state_plane(plan.state, item, 1)[pix];
+                ps.last = reinterpret_cast<const int *>(state_plane(plan.state, item, 5))[pix];
+                // colour behind the chunk: final colour - prefix up to the chunk
+                ps.B0 = state_plane(plan.state, it.base, 7)[pix] - state_plane(plan.state, item, 2)[pix];
+                ps.B1 = state_plane(plan.state, it.base, 8)[pix] - state_plane(plan.state, item, 3)[pix];
+                ps.B2 = state_plane(plan.state, it.base, 9)[pix] - state_plane(plan.state, item, 4)[pix];
+            } else {
+                ps.last = 0;
             }
-            if (!(half ? tc.in1 : tc.in0)) ps.last = 0;
-            ps.B0 = fmaf(Tf, bg0, ps.B0); ps.B1 = fmaf(Tf, bg1, ps.B1); ps.B2 = fmaf(Tf, bg2, ps.B2);
         }
     } else if (T_final_in) {
         if (tc.in0) { p0.T = T_final_in[vt.pix_base[v] + pix0]; p0.last = min(last_in[vt.pix_base[v] + pix0], n_items); }

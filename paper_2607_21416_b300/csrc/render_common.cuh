@@ -11,16 +11,16 @@
 // transmittance in front of it.  That is Eq. 1 exactly unless a pixel's stop
 // (T' < 1e-4) falls inside the chunk; those (chunk, pixel) pairs are
 // composited again from the now known entering transmittance (fix-up).
-// After the forward, each item of a multi-chunk tile holds per pixel:
-//   Tprod  product of (1 - alpha) over the chunk's splats (0 when chunk 0
-//          stopped the pixel; it may stop early once below 1e-4, which decides
-//          every later chunk)
+// After the forward, each item k of a multi-chunk tile holds per pixel:
+//   T0     transmittance in front of the chunk: the running product of the
+//          chunks' own products; the chunk is active iff T0 >= 1e-4 (0 for
+//          the chunks behind the pixel's stop)
 //   Tend   transmittance after the chunk's compositing (stop rule applied)
-//   C[3]   the chunk's colour contribution
+//   P[3]   colour composited up to and including this chunk (prefix)
 //   last   1-based position (in the chunk) of its last composited splat
-// so chunk k starts from T0_k = prod_{j<k} Tprod_j (it is active iff T0_k >=
-// 1e-4), and the backward pass of chunk k needs only T0_k, its own Tend/last
-// and the colour of the chunks behind it.
+// and the tile's first item also holds the pixel's final colour F[3] (image
+// value, background included), so the reverse pass of chunk k starts from
+// Tend, last and the colour behind the chunk, F - P_k, in O(1).
 #pragma once
 
 #include "gs_internal.cuh"
@@ -29,7 +29,8 @@ namespace gs {
 
 constexpr int kRT = kTilePix;      // pixels per tile / work item
 constexpr int kRThreads = 128;     // threads per work item: two pixels each (rows y and y + 8)
-constexpr int kStateWords = 7;     // Tprod, Tend, C0, C1, C2, last, composited count  (x 256 pixels)
+constexpr int kStateWords = 10;    // T0 (Tprod during the forward), Tend, P0..2 (C during the forward), last,
+                                   // composited count, F0..2 (first item only)  (x 256 pixels)
 
 // 2^x on the special-function unit (ex2.approx, max relative error ~2^-22).
 __device__ __forceinline__ float ex2_approx(float x)

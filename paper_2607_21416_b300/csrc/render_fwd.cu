@@ -227,14 +227,17 @@ __device__ __forceinline__ void chunk_unit(const float4 *__restrict__ rec, const
             if (!(half ? act1 : act0)) continue;
             float *c0 = state_plane(plan.state, item, 2), *c1 = state_plane(plan.state, item, 3);
             float *c2 = state_plane(plan.state, item, 4);
-            const float f0 = c0[pix], f1 = c1[pix], f2 = c2[pix];   // colour in front of the chunk
+            const float f0 = c0[pix] + ps.C0, f1 = c1[pix] + ps.C1, f2 = c2[pix] + ps.C2;   // prefix incl. this chunk
             state_plane(plan.state, item, 1)[pix] = ps.T;
-            c0[pix] = ps.C0;
-            c1[pix] = ps.C1;
-            c2[pix] = ps.C2;
+            c0[pix] = f0;
+            c1[pix] = f1;
+            c2[pix] = f2;
             reinterpret_cast<int *>(state_plane(plan.state, item, 5))[pix] = ps.last;
-            write_image(vt, tc.v, tc.px, py, f0 + ps.C0, f1 + ps.C1, f2 + ps.C2, ps.T,
-                        ps.last > 0 ? it.k * plan.L + ps.last : -1, bg0, bg1, bg2, image, T_final, last);
+            state_plane(plan.state, it.base, 7)[pix] = fmaf(ps.T, bg0, f0);
+            state_plane(plan.state, it.base, 8)[pix] = fmaf(ps.T, bg1, f1);
+            state_plane(plan.state, it.base, 9)[pix] = fmaf(ps.T, bg2, f2);
+            write_image(vt, tc.v, tc.px, py, f0, f1, f2, ps.T, ps.last > 0 ? it.k * plan.L + ps.last : -1, bg0, bg1,
+                        bg2, image, T_final, last);
             continue;
         }
         // per-chunk state; a stop in chunk 0 is marked by Tprod = 0
@@ -296,57 +299,86 @@ __global__ void __launch_bounds__(kRThreads) combine_kernel(const uint32_t *__re
     const uint32_t s_start = ranges[2 * t], s_end = ranges[2 * t + 1];
     unsigned long long nev = 0, ncomp = 0;
     for (int half = 0; half < 2; ++half) {
-        if (!(half ? tc.in1 : tc.in0)) continue;
         const int pix = tc.pid0 + half * kTile;
         const int py = tc.py + half;
+        const bool inside = half ? tc.in1 : tc.in0;
         float C0 = state_plane(plan.state, base, 2)[pix];
         float C1 = state_plane(plan.state, base, 3)[pix];
         float C2 = state_plane(plan.state, base, 4)[pix];
         const int l0 = reinterpret_cast<const int *>(state_plane(plan.state, base, 5))[pix];
         int lastg = l0 > 0 ? l0 : 0;
-        float T0 = state_plane(plan.state, base, 0)[pix];
-        if (T0 == 0.f) {   // chunk 0 stopped the pixel
-            write_image(vt, tc.v, tc.px, py, C0, C1, C2, state_plane(plan.state, base, 1)[pix], lastg, bg0, bg1, bg2,
-                        image, T_final, last);
-            continue;
-        }
+        float *t00 = state_plane(plan.state, base, 0);
+        float T0 = t00[pix];   // chunk 0's own product (0: it stopped the pixel)
+        t00[pix] = 1.f;        // chunk 0 is always active
+        int k = 1;
         bool marked = false;
-        for (int k = 1; k < nk; ++k) {
-            if (!(T0 >= kTMin)) break;
-            const int item = base + k;
-            float *te = state_plane(plan.state, item, 1);
-            float *c0 = state_plane(plan.state, item, 2), *c1 = state_plane(plan.state, item, 3);
-            float *c2 = state_plane(plan.state, item, 4);
-            int *lp = reinterpret_cast<int *>(state_plane(plan.state, item, 5));
-            const float T1 = __fmul_rn(T0, state_plane(plan.state, item, 0)[pix]);
-            if (T1 >= kTMin) {   // no stop inside: the chunk's true contribution
-                const float g0 = T0 * c0[pix], g1 = T0 * c1[pix], g2 = T0 * c2[pix];
-                c0[pix] = g0;
-                c1[pix] = g1;
-                c2[pix] = g2;
-                te[pix] = T1;
-                C0 += g0;
-                C1 += g1;
-                C2 += g2;
-                if (lp[pix] > 0) lastg = k * plan.L + lp[pix];
-                if (COUNT) {
-                    nev += min((uint32_t)plan.L, s_end - (s_start + (uint32_t)k * (uint32_t)plan.L));
-                    ncomp += reinterpret_cast<const int *>(state_plane(plan.state, item, 6))[pix];
+        if (T0 == 0.f) {       // chunk 0 stopped the pixel
+            T0 = state_plane(plan.state, base, 1)[pix];
+        } else {
+            // chunk k + 1's state is read before chunk k's is written (different
+            // items: no overlap), so the walk is not one load latency per chunk
+            float nTp = 0.f, na0 = 0.f, na1 = 0.f, na2 = 0.f;
+            int nl = 0, nc = 0;
+            auto fetch = [&](int kk) {
+                const int it2 = base + kk;
+                nTp = state_plane(plan.state, it2, 0)[pix];
+                na0 = state_plane(plan.state, it2, 2)[pix];
+                na1 = state_plane(plan.state, it2, 3)[pix];
+                na2 = state_plane(plan.state, it2, 4)[pix];
+                nl = reinterpret_cast<const int *>(state_plane(plan.state, it2, 5))[pix];
+                if (COUNT) nc = reinterpret_cast<const int *>(state_plane(plan.state, it2, 6))[pix];
+            };
+            if (k < nk) fetch(k);
+            for (; k < nk; ++k) {
+                if (!(T0 >= kTMin)) break;
+                const int item = base + k;
+                const float Tp = nTp, a0 = na0, a1 = na1, a2 = na2;
+                const int lk = nl, ck = nc;
+                if (k + 1 < nk) fetch(k + 1);
+                float *tp = state_plane(plan.state, item, 0);
+                float *te = state_plane(plan.state, item, 1);
+                float *c0 = state_plane(plan.state, item, 2), *c1 = state_plane(plan.state, item, 3);
+                float *c2 = state_plane(plan.state, item, 4);
+                int *lp = reinterpret_cast<int *>(state_plane(plan.state, item, 5));
+                tp[pix] = T0;
+                const float T1 = __fmul_rn(T0, Tp);
+                if (T1 >= kTMin) {   // no stop inside: the chunk's true contribution
+                    C0 += T0 * a0;
+                    C1 += T0 * a1;
+                    C2 += T0 * a2;
+                    c0[pix] = C0;
+                    c1[pix] = C1;
+                    c2[pix] = C2;
+                    te[pix] = T1;
+                    if (lk > 0) lastg = k * plan.L + lk;
+                    if (COUNT && inside) {
+                        nev += min((uint32_t)plan.L, s_end - (s_start + (uint32_t)k * (uint32_t)plan.L));
+                        ncomp += ck;
+                    }
+                    T0 = T1;
+                } else {             // the pixel's stop lies in chunk k
+                    te[pix] = T0;
+                    c0[pix] = C0;
+                    c1[pix] = C1;
+                    c2[pix] = C2;
+                    lp[pix] = -1;
+                    if (inside) {
+                        if (atomicExch(plan.fix + item, 1) == 0) plan.fix_list[atomicAdd(plan.counters + 3, 1)] = item;
+                        if (last) last[vt.pix_base[tc.v] + (long long)py * vt.W[tc.v] + tc.px] = lastg;
+                    }
+                    marked = true;
+                    ++k;
+                    break;
                 }
-                T0 = T1;
-            } else {             // the pixel's stop lies in chunk k
-                te[pix] = T0;
-                c0[pix] = C0;
-                c1[pix] = C1;
-                c2[pix] = C2;
-                lp[pix] = -1;
-                if (atomicExch(plan.fix + item, 1) == 0) plan.fix_list[atomicAdd(plan.counters + 3, 1)] = item;
-                if (last) last[vt.pix_base[tc.v] + (long long)py * vt.W[tc.v] + tc.px] = lastg;
-                marked = true;
-                break;
             }
         }
-        if (!marked) write_image(vt, tc.v, tc.px, py, C0, C1, C2, T0, lastg, bg0, bg1, bg2, image, T_final, last);
+        for (; k < nk; ++k) state_plane(plan.state, base + k, 0)[pix] = 0.f;   // behind the stop: inactive
+        if (!marked) {
+            state_plane(plan.state, base, 7)[pix] = fmaf(T0, bg0, C0);
+            state_plane(plan.state, base, 8)[pix] = fmaf(T0, bg1, C1);
+            state_plane(plan.state, base, 9)[pix] = fmaf(T0, bg2, C2);
+            if (inside) write_image(vt, tc.v, tc.px, py, C0, C1, C2, T0, lastg, bg0, bg1, bg2, image, T_final, last);
+        }
     }
     if (COUNT) count_add(n_eval, nev, ncomp);
 }
