@@ -113,6 +113,17 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ ours
+def whole_job(total_ms, npix_per_rank, steps, world, dist, device=None):
+    """Replicas: the longest timed region over the ranks and the whole-job
+    throughput (every rank renders npix_per_rank pixels per step), in Mpix/s."""
+    import torch
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, npix_per_rank * world * steps / (total_ms * 1e-3) / 1e6
+
+
 def run_ours(args, rank, world, dist):
     import torch
 
@@ -206,13 +217,8 @@ def run_ours(args, rank, world, dist):
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    total_ms = float(sum(step_ms))
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms, mpix = whole_job(float(sum(step_ms)), npix, args.steps, world, dist, dev)
     ms_per_step = total_ms / args.steps
-    mpix = npix * world * args.steps / (total_ms * 1e-3) / 1e6
 
     # ---- end to end through the public API with host buffers: MappingStep.step copies the
     # target images and cameras from pinned host memory, replays the iteration and reads the
@@ -293,6 +299,28 @@ OPS_COMPOSITED_BWD = 29
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 148, 128, 2032.0
 
 
+def profiled_traffic(kernel_file, sources):
+    """DRAM bytes per launch recorded in a committed ncu summary, or None when
+    the kernel's sources changed since that capture (their SHA-256 differ)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", kernel_file)
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    traffic = None
+    for line in text.splitlines():
+        if line.startswith("traffic_bytes_per_launch:"):
+            traffic = int(line.split(":")[1])
+        elif line.startswith("source_sha256 "):
+            name, digest = line[len("source_sha256 "):].split(":")
+            src = os.path.join(ROOT, "paper_2607_21416_b300", "csrc", name.strip())
+            if name.strip() not in sources or not os.path.exists(src):
+                return None
+            if hashlib.sha256(open(src, "rb").read()).hexdigest() != digest.strip():
+                return None
+    return traffic
+
+
 def roofline(dom, ms, counts, n_pairs, n_rows, rp, scene, peaks):
     hbm = peaks.get("hbm_gbs", 6400.0)
     alu_peak = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12   # T FP32 lane ops/s (nominal)
@@ -309,7 +337,8 @@ def roofline(dom, ms, counts, n_pairs, n_rows, rp, scene, peaks):
         a = ops / (ms * 1e-3) / 1e12
         return {"kernel": "render_bwd_kernel (+project_bwd_kernel, same call)", "bound": "alu",
                 "achieved": a, "peak": alu_peak, "unit": "T FP32 ops/s", "frac": a / alu_peak,
-                "traffic": None,
+                "traffic": profiled_traffic("render_bwd_kernel_keyframe_batch_8x1241x376.md",
+                                            ("render_bwd.cu", "render_common.cuh")),
                 "work_per_launch": f"{ex} examined + {rev} reverse-examined + {comp} composited pairs"}
     if dom == "bin_sort":
         S = n_rows * scene.k
