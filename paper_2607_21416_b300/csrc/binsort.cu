@@ -356,7 +356,7 @@ constexpr int kEmitPairs = 2048;   // pairs written per CTA and round
 // of its rectangle, row-major.
 __global__ void __launch_bounds__(kSortThreads) emit_pairs_kernel(
     const uint32_t *__restrict__ ids, const uint32_t *__restrict__ n_ptr, const uint32_t *__restrict__ np_ptr,
-    const uint32_t *__restrict__ offs, const int32_t *__restrict__ tiles, const float4 *__restrict__ rec,
+    const uint32_t *__restrict__ offs, const float4 *__restrict__ rec,
     const int32_t *__restrict__ view_start, int k, uint32_t *__restrict__ tkeys, uint32_t *__restrict__ tvals,
     ViewTable vt, long long cap_cand, const gs_status *st)
 {
@@ -386,8 +386,9 @@ __global__ void __launch_bounds__(kSortThreads) emit_pairs_kernel(
                 const uint32_t rx = __float_as_uint(r2.z), ry = __float_as_uint(r2.w);
                 const int x0 = rx & 0xffff, x1 = rx >> 16, y0 = ry & 0xffff, y1 = ry >> 16;
                 const int v = view_of_row(view_start, vt.V, (int)(id / (uint32_t)k));
-                const int cnt = __ldg(tiles + id);
-                if ((long long)(x1 - x0) * (y1 - y0) != (long long)cnt || x1 > vt.TX[v] || y1 > vt.TY[v] || x1 <= x0)
+                // the splat's tile count from its offsets (no second read of tiles_touched)
+                const long long cnt = (long long)(sidx + 1 < S ? offs[sidx + 1] : P) - (long long)offs[sidx];
+                if ((long long)(x1 - x0) * (y1 - y0) != cnt || x1 > vt.TX[v] || y1 > vt.TY[v] || x1 <= x0)
                     idx_ok(st, (long long)id, -1, 36);
                 w = (uint32_t)max(x1 - x0, 1);
                 tx = (uint32_t)vt.TX[v];
@@ -530,7 +531,7 @@ int launch_bin_sort(const gs_splats *sp, int k, const int32_t *view_start, long 
     uint32_t *ek = tk_a, *ev = (passes % 2 == 0) ? bins->vals : tv_b;
     uint32_t *ok = tk_b, *ov = (passes % 2 == 0) ? tv_b : bins->vals;
     pair_offsets_kernel<<<nb, kSortThreads, 0, s>>>(ids_s, n_splats, sp->tiles, sums, offs, cap_cand, st);
-    emit_pairs_kernel<<<sm_count() * 4, kSortThreads, 0, s>>>(ids_s, n_splats, n_pairs, offs, sp->tiles, rec,
+    emit_pairs_kernel<<<sm_count() * 4, kSortThreads, 0, s>>>(ids_s, n_splats, n_pairs, offs, rec,
                                                               view_start, k, ek, ev, vt, cap_cand, st);
     count_launches(4);
     // 4. stable sort on the tile id

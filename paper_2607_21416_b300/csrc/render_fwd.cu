@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(kRThreads) chunk_kernel(const float4 *__restri
 // the pixel's stop and is marked for the fix-up, with T0 and the colour in
 // front of it in its Tend / colour planes and last = -1.
 template <bool COUNT>
-__global__ void __launch_bounds__(kRThreads) combine_kernel(const uint32_t *__restrict__ ranges, ViewTable vt,
+__global__ void __launch_bounds__(2 * kRThreads) combine_kernel(const uint32_t *__restrict__ ranges, ViewTable vt,
                                                             RenderPlan plan, float bg0, float bg1, float bg2,
                                                             float *__restrict__ image, float *__restrict__ T_final,
                                                             int32_t *__restrict__ last,
@@ -295,10 +295,12 @@ __global__ void __launch_bounds__(kRThreads) combine_kernel(const uint32_t *__re
     const int t = blockIdx.x;
     const int base = plan.item_base[t], nk = plan.item_base[t + 1] - base;
     if (nk <= 1) return;
-    const TileCoord tc = tile_coord(vt, t, threadIdx.x);
+    // one pixel per thread: tile thread (threadIdx & 127), pixel row half (threadIdx >> 7)
+    const TileCoord tc = tile_coord(vt, t, threadIdx.x & (kRThreads - 1));
     const uint32_t s_start = ranges[2 * t], s_end = ranges[2 * t + 1];
     unsigned long long nev = 0, ncomp = 0;
-    for (int half = 0; half < 2; ++half) {
+    {
+        const int half = threadIdx.x >> 7;
         const int pix = tc.pid0 + half * kTile;
         const int py = tc.py + half;
         const bool inside = half ? tc.in1 : tc.in0;
@@ -459,7 +461,7 @@ static void launch_items(const float4 *rec, const gs_bins *bins, const ViewTable
     chunk_kernel<COUNT, false><<<persistent_grid((const void *)chunk_kernel<COUNT, false>), kRThreads, 0, s>>>(rec, bins->vals, bins->ranges, vt, plan, bg[0],
                                                                    bg[1], bg[2], image, T_final, last, n_eval, cap,
                                                                    st);
-    combine_kernel<COUNT><<<vt.total_tiles, kRThreads, 0, s>>>(bins->ranges, vt, plan, bg[0], bg[1], bg[2], image,
+    combine_kernel<COUNT><<<vt.total_tiles, 2 * kRThreads, 0, s>>>(bins->ranges, vt, plan, bg[0], bg[1], bg[2], image,
                                                               T_final, last, n_eval, st);
     chunk_kernel<COUNT, true><<<persistent_grid((const void *)chunk_kernel<COUNT, true>), kRThreads, 0, s>>>(rec, bins->vals, bins->ranges, vt, plan, bg[0],
                                                                   bg[1], bg[2], image, T_final, last, n_eval, cap,
