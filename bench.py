@@ -325,6 +325,7 @@ def roofline(dom, ms, counts, n_pairs, n_rows, rp, scene, peaks):
     hbm = peaks.get("hbm_gbs", 6400.0)
     alu_peak = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12   # T FP32 lane ops/s (nominal)
     ex, comp, rev = counts["examined"], counts["composited"], counts["reverse_examined"]
+    ex1, comp1 = counts["examined_single_item_tiles"], counts["composited_single_item_tiles"]
     if dom == "render_fwd":
         ops = ex * OPS_EXAMINED + comp * OPS_COMPOSITED_FWD
         a = ops / (ms * 1e-3) / 1e12
@@ -332,14 +333,17 @@ def roofline(dom, ms, counts, n_pairs, n_rows, rp, scene, peaks):
                 "unit": "T FP32 ops/s", "frac": a / alu_peak, "traffic": None,
                 "work_per_launch": f"{ex} examined + {comp} composited pixel-splat pairs"}
     if dom == "render_bwd":
-        ops = (ex * OPS_EXAMINED + comp * OPS_COMPOSITED_FWD          # recomputed forward
+        # the forward is recomputed only for tiles whose list is one work item;
+        # chunks of longer lists start from the state the forward left
+        ops = (ex1 * OPS_EXAMINED + comp1 * OPS_COMPOSITED_FWD        # recomputed forward
                + rev * OPS_EXAMINED + comp * OPS_COMPOSITED_BWD)      # reverse traversal
         a = ops / (ms * 1e-3) / 1e12
         return {"kernel": "render_bwd_kernel (+project_bwd_kernel, same call)", "bound": "alu",
                 "achieved": a, "peak": alu_peak, "unit": "T FP32 ops/s", "frac": a / alu_peak,
                 "traffic": profiled_traffic("render_bwd_kernel_keyframe_batch_8x1241x376.md",
                                             ("render_bwd.cu", "render_common.cuh")),
-                "work_per_launch": f"{ex} examined + {rev} reverse-examined + {comp} composited pairs"}
+                "work_per_launch": f"{ex1} examined (recomputed, single-item tiles) + {rev} reverse-examined + "
+                                   f"{comp1} + {comp} composited pairs"}
     if dom == "bin_sort":
         S = n_rows * scene.k
         byts = S * 4 * 2 + n_pairs * 8 * 2 + n_pairs * 4
@@ -366,6 +370,8 @@ def work_counts(rp):
                    rp.n_eval)
     torch.cuda.synchronize()
     return {"examined": int(rp.n_eval[0].item()), "composited": int(rp.n_eval[1].item()),
+            "examined_single_item_tiles": int(rp.n_eval[2].item()),
+            "composited_single_item_tiles": int(rp.n_eval[3].item()),
             "reverse_examined": int(last.to(torch.int64).sum().item())}
 
 

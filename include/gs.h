@@ -248,9 +248,11 @@ int gs_bin_sort(const gs_splats *sp, int32_t k, const int32_t *view_start, int64
  * 256-byte aligned; gs_render_bwd needs the same workspace, untouched, and
  * the same `chunk`.  T_final (float per pixel) and last (int32 per pixel:
  * 1-based list position of the last composited splat) are optional outputs
- * (NULL to skip).  n_eval (device int64[2], NULL to skip) receives the number
- * of (pixel, splat) pairs examined and the number composited (a counting
- * variant of the kernel runs when it is given). */
+ * (NULL to skip).  n_eval (device int64[4], NULL to skip) receives the number
+ * of (pixel, splat) pairs examined (every list position up to the pixel's
+ * stop), the number composited, and the same two counts over the tiles whose
+ * list forms a single work item (a counting variant of the kernels runs when
+ * it is given). */
 int gs_render_fwd(const gs_splats *sp, const gs_bins *bins, const gs_view *views, int32_t V,
                   const float *bg, int32_t chunk, void *ws, size_t ws_bytes, float *image,
                   float *T_final, int32_t *last, int64_t *n_eval, gs_status *status, void *stream);

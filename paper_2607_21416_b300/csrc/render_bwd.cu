@@ -63,7 +63,8 @@ __device__ __forceinline__ bool bwd_step(PixBwd &ps, const float4 a, const float
     const float ag = splat_alpha(q, bb.y);
     const float alpha = fminf(kAlphaMax, ag);
     if (alpha < kAlphaMin) return false;
-    const float inv = __frcp_rn(1.f - alpha);
+    float inv;                             // 1 / (1 - alpha) on the SFU (relative error ~2^-23; the
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(1.f - alpha));   // operand lies in [0.01, 1))
     ps.T = ps.T * inv;                     // transmittance in front of this splat
     const float w = alpha * ps.T;
     acc[6] = fmaf(w, ps.g0, acc[6]);

@@ -126,15 +126,23 @@ __device__ __forceinline__ void write_image(const ViewTable &vt, int v, int px, 
     if (last && lastg >= 0) last[vt.pix_base[v] + p] = lastg;
 }
 
-// Warp totals of the examined / composited pair counts into n_eval[0..1].
-__device__ __forceinline__ void count_add(unsigned long long *n_eval, unsigned long long nev, unsigned long long ncomp)
+// Warp totals of the examined / composited pair counts into n_eval[0..1]
+// (and [2..3] for a tile whose list is a single work item).
+__device__ __forceinline__ void count_add(unsigned long long *n_eval, unsigned long long nev, unsigned long long ncomp,
+                                          bool single = false)
 {
     for (int o = 16; o > 0; o >>= 1) {
         nev += __shfl_down_sync(0xffffffffu, nev, o);
         ncomp += __shfl_down_sync(0xffffffffu, ncomp, o);
     }
-    if ((threadIdx.x & 31) == 0 && nev) atomicAdd(n_eval, nev);
-    if ((threadIdx.x & 31) == 0 && ncomp) atomicAdd(n_eval + 1, ncomp);
+    if ((threadIdx.x & 31) == 0 && nev) {
+        atomicAdd(n_eval, nev);
+        if (single) atomicAdd(n_eval + 2, nev);
+    }
+    if ((threadIdx.x & 31) == 0 && ncomp) {
+        atomicAdd(n_eval + 1, ncomp);
+        if (single) atomicAdd(n_eval + 3, ncomp);
+    }
 }
 
 // Compositing of one work item (FIX: the fix-up pass over marked chunks).
@@ -210,7 +218,7 @@ __device__ __forceinline__ void chunk_unit(const float4 *__restrict__ rec, const
             if (act0) { nev += p0.stop ? p0.stop : n_items; ncomp += p0.ncomp; }
             if (act1) { nev += p1.stop ? p1.stop : n_items; ncomp += p1.ncomp; }
         }
-        count_add(n_eval, nev, ncomp);
+        count_add(n_eval, nev, ncomp, !multi);
     }
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
@@ -478,7 +486,7 @@ int launch_render_fwd(const gs_splats *sp, const gs_bins *bins, const ViewTable 
     plan_kernel<<<1, 1024, 0, s>>>(bins->ranges, vt.total_tiles, L, plan.max_items,
                                    const_cast<int32_t *>(plan.item_base), plan.fix, plan.counters, st);
     if (n_eval) {
-        cudaMemsetAsync(n_eval, 0, 2 * sizeof(long long), s);
+        cudaMemsetAsync(n_eval, 0, 4 * sizeof(long long), s);
         launch_items<true>(rec, bins, vt, plan, bg, image, T_final, last,
                            reinterpret_cast<unsigned long long *>(n_eval), sp->cap, st, s);
     } else {

@@ -60,7 +60,7 @@ class RenderPass:
         self.loss = torch.zeros(1, device=device)
         self.T_final = torch.zeros(npix, device=device) if store_state else None
         self.last = torch.zeros(npix, device=device, dtype=torch.int32) if store_state else None
-        self.n_eval = torch.zeros(2, device=device, dtype=torch.int64)
+        self.n_eval = torch.zeros(4, device=device, dtype=torch.int64)
         self._alloc()
 
     def _alloc(self):

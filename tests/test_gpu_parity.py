@@ -144,7 +144,7 @@ def _render_fwd_case(s, view_start, k, prj, opacity, colour, keys, vals, ranges,
     img = torch.zeros(3 * vw.total_pixels, device="cuda")
     Tf = torch.zeros(vw.total_pixels, device="cuda")
     last = torch.zeros(vw.total_pixels, device="cuda", dtype=torch.int32)
-    nev = torch.zeros(2, device="cuda", dtype=torch.int64)
+    nev = torch.zeros(4, device="cuda", dtype=torch.int64)
     st = api.new_status()
     ws = api.workspace(api.render_workspace(vw, bins.cap_pairs, chunk))
     api.render_fwd(sp, bins, vw, bg, img, st, ws, chunk, Tf, last, nev)
@@ -162,6 +162,12 @@ def _render_fwd_case(s, view_start, k, prj, opacity, colour, keys, vals, ranges,
     assert np.allclose(to_np(Tf)[ok], ren.T_final[ok], rtol=1e-3, atol=1e-6)
     assert int(nev[0].item()) == pytest.approx(ren.nev, rel=1e-3)
     assert 0 < int(nev[1].item()) <= int(nev[0].item())
+    # the same counts over the tiles whose list is a single work item
+    lens = ranges[:, 1].astype(np.int64) - ranges[:, 0]
+    L_ = chunk if chunk else 512
+    assert 0 <= int(nev[2].item()) <= int(nev[0].item()) and 0 <= int(nev[3].item()) <= int(nev[1].item())
+    if (lens <= L_).all():
+        assert int(nev[2].item()) == int(nev[0].item()) and int(nev[3].item()) == int(nev[1].item())
     if chunk:
         lens = ranges[:, 1].astype(np.int64) - ranges[:, 0]
         assert (lens > chunk).any(), "case should contain tiles cut into several chunks"
