@@ -17,7 +17,7 @@
  *     builds on;
  *   - tile binning with (tile, depth) keys and a sort on (key, splat id);
  *   - front-to-back alpha compositing, Eq. 1;
- *   - the L1 photometric term of Eq. 3;
+ *   - the L1 photometric term of Eq. 3 and its structural (SSIM) term;
  *   - the analytic reverse pass of all of the above (the method is
  *     "differentiable", Sec. II/III-A), derived by hand from the forward
  *     definitions and checked against central finite differences.
@@ -588,6 +588,102 @@ double gso_l1(int V, const int *wh, const double *image, const double *target, d
             if (dimage) dimage[base + i] = (d > 0 ? 1.0 : (d < 0 ? -1.0 : 0.0)) / (double)n;
         }
         L += s / (double)n;
+        base += n;
+    }
+    return L;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Structural term of Eq. 3.  The paper takes its objective from the 3DGS
+ * work it cites: L = lambda L1 + (1 - lambda) L_SSIM with L_SSIM = 1 - SSIM.
+ * Readings (the paper gives no constants): SSIM of one view is the mean over
+ * pixels and channels of the SSIM map computed per channel with an 11x11
+ * Gaussian window (sigma 1.5, normalised to sum 1), zero padding outside the
+ * image ("same" size), C1 = 0.01^2, C2 = 0.03^2; L_SSIM is summed over the
+ * views like the L1 term.  For pixel p of one channel, with window weights
+ * G(i, j) and x, y the rendered and target images:
+ *   mu_x = sum G x,  mu_y = sum G y,  s_xx = sum G x^2,  s_yy = sum G y^2,
+ *   s_xy = sum G x y (sums over the window, zero outside the image),
+ *   var_x = s_xx - mu_x^2,  var_y = s_yy - mu_y^2,  cov = s_xy - mu_x mu_y,
+ *   S = (2 mu_x mu_y + C1)(2 cov + C2) / ((mu_x^2 + mu_y^2 + C1)(var_x + var_y + C2)).
+ * Reverse (derived by hand): with A1 = 2 mu_x mu_y + C1, A2 = 2 cov + C2,
+ * B1 = mu_x^2 + mu_y^2 + C1, B2 = var_x + var_y + C2,
+ *   dS/dmu_x = 2 mu_y A2 / (B1 B2) - 2 mu_x S / B1 + 2 mu_x S / B2 - 2 mu_y A1 / (B1 B2)
+ *   dS/ds_xx = -S / B2,   dS/ds_xy = 2 A1 / (B1 B2),
+ * and d/dx(r) = sum over the pixels p whose window holds r of
+ *   G(r - p) (dS/dmu_x(p) + 2 x(r) dS/ds_xx(p) + y(r) dS/ds_xy(p)).
+ * Returns L_SSIM = sum over views of (1 - mean S); ssim_map (3HW per view,
+ * nullable) receives S, dimage (nullable) dL_SSIM/dimage. */
+#define O_SSIM_R 5
+static void ssim_window(double g[2 * O_SSIM_R + 1])
+{
+    double sum = 0;
+    for (int i = -O_SSIM_R; i <= O_SSIM_R; ++i) {
+        g[i + O_SSIM_R] = exp(-(double)(i * i) / (2.0 * 1.5 * 1.5));
+        sum += g[i + O_SSIM_R];
+    }
+    for (int i = 0; i < 2 * O_SSIM_R + 1; ++i) g[i] /= sum;
+}
+
+double gso_ssim(int V, const int *wh, const double *image, const double *target, double *ssim_map,
+                double *dimage)
+{
+    const double C1 = 0.01 * 0.01, C2 = 0.03 * 0.03;
+    double g[2 * O_SSIM_R + 1];
+    ssim_window(g);
+    double L = 0;
+    long base = 0;
+    for (int v = 0; v < V; ++v) {
+        const int W = wh[2 * v], H = wh[2 * v + 1];
+        const long np = (long)W * H, n = 3 * np;
+        double *dmu = malloc(sizeof(double) * np), *dsxx = malloc(sizeof(double) * np);
+        double *dsxy = malloc(sizeof(double) * np);
+        double ssum = 0;
+        for (int ch = 0; ch < 3; ++ch) {
+            const double *x = image + base + ch * np, *y = target + base + ch * np;
+            for (int py = 0; py < H; ++py)
+                for (int px = 0; px < W; ++px) {
+                    double mx = 0, my = 0, sxx = 0, syy = 0, sxy = 0;
+                    for (int j = -O_SSIM_R; j <= O_SSIM_R; ++j)
+                        for (int i = -O_SSIM_R; i <= O_SSIM_R; ++i) {
+                            const int qx = px + i, qy = py + j;
+                            if (qx < 0 || qx >= W || qy < 0 || qy >= H) continue;
+                            const double w = g[i + O_SSIM_R] * g[j + O_SSIM_R];
+                            const double a = x[(long)qy * W + qx], b = y[(long)qy * W + qx];
+                            mx += w * a; my += w * b;
+                            sxx += w * a * a; syy += w * b * b; sxy += w * a * b;
+                        }
+                    const double vx = sxx - mx * mx, vy = syy - my * my, cv = sxy - mx * my;
+                    const double A1 = 2 * mx * my + C1, A2 = 2 * cv + C2;
+                    const double B1 = mx * mx + my * my + C1, B2 = vx + vy + C2;
+                    const double S = A1 * A2 / (B1 * B2);
+                    const long p = (long)py * W + px;
+                    if (ssim_map) ssim_map[base + ch * np + p] = S;
+                    ssum += S;
+                    dmu[p] = 2 * my * A2 / (B1 * B2) - 2 * mx * S / B1 + 2 * mx * S / B2 - 2 * my * A1 / (B1 * B2);
+                    dsxx[p] = -S / B2;
+                    dsxy[p] = 2 * A1 / (B1 * B2);
+                }
+            if (dimage) {
+                /* d(1 - mean S)/dS = -1 / n */
+                for (int ry = 0; ry < H; ++ry)
+                    for (int rx = 0; rx < W; ++rx) {
+                        const long r = (long)ry * W + rx;
+                        double acc = 0;
+                        for (int j = -O_SSIM_R; j <= O_SSIM_R; ++j)
+                            for (int i = -O_SSIM_R; i <= O_SSIM_R; ++i) {
+                                const int qx = rx - i, qy = ry - j;   /* p = r - (i, j): r = p + (i, j) */
+                                if (qx < 0 || qx >= W || qy < 0 || qy >= H) continue;
+                                const double w = g[i + O_SSIM_R] * g[j + O_SSIM_R];
+                                const long q = (long)qy * W + qx;
+                                acc += w * (dmu[q] + 2 * x[r] * dsxx[q] + y[r] * dsxy[q]);
+                            }
+                        dimage[base + ch * np + r] = -acc / (double)n;
+                    }
+            }
+        }
+        L += 1.0 - ssum / (double)n;
+        free(dmu); free(dsxx); free(dsxy);
         base += n;
     }
     return L;

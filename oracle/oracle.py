@@ -53,6 +53,13 @@ _u32 = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
 _u64 = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
 
 
+class _dpn:
+    """float64 array pointer that also accepts None (NULL)."""
+    @classmethod
+    def from_param(cls, a):
+        return None if a is None else _dp.from_param(a)
+
+
 def _declare(L):
     i, l, d = C.c_int, C.c_long, C.c_double
     L.gso_visibility.restype = l
@@ -71,6 +78,8 @@ def _declare(L):
                              C.POINTER(C.c_uint64)]
     L.gso_l1.restype = d
     L.gso_l1.argtypes = [i, _ip, _dp, _dp, _dp]
+    L.gso_ssim.restype = d
+    L.gso_ssim.argtypes = [i, _ip, _dp, _dp, _dpn, _dpn]
     L.gso_render_bwd.restype = i
     L.gso_render_bwd.argtypes = [i, _ip, l, _dp, _dp, _dp, _dp, _u32, _u32, _dp, _dp, _dp,
                                  _dp, _dp, _dp]
@@ -234,6 +243,24 @@ def l1(wh, image, target):
     d = np.zeros_like(image)
     L = lib().gso_l1(np.asarray(wh).reshape(-1, 2).shape[0], _i32(wh), image, target, d)
     return L, d
+
+
+def ssim(wh, image, target, want_map=False, want_grad=True):
+    """Structural term of Eq. 3: L_SSIM = sum over views of (1 - mean SSIM),
+    its gradient with respect to image and (optionally) the SSIM map."""
+    image = _f64(image).reshape(-1); target = _f64(target).reshape(-1)
+    wh = _i32(wh).reshape(-1, 2)
+    d = np.zeros_like(image) if want_grad else None
+    m = np.zeros_like(image) if want_map else None
+    L = lib().gso_ssim(wh.shape[0], wh, image, target, m, d)
+    return L, d, m
+
+
+def photometric(wh, image, target, lam=0.8):
+    """Eq. 3: L = lam L1 + (1 - lam) L_SSIM and dL/dimage; also the two terms."""
+    L1, d1 = l1(wh, image, target)
+    Ls, ds, _ = ssim(wh, image, target)
+    return lam * L1 + (1 - lam) * Ls, lam * d1 + (1 - lam) * ds, L1, Ls
 
 
 def render_bwd(wh, mean2d, conic, opacity, colour, ranges, vals, dimage, bg=(0.0, 0.0, 0.0)):
