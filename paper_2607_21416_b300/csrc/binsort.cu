@@ -9,8 +9,9 @@
 //      keep id order);
 //   3. scan the tile counts in depth order (per-splat pair offsets) and emit
 //      one (tile id, splat id) pair per covered tile, load-balanced: each
-//      CTA writes 2048 consecutive pairs and finds each pair's splat by
-//      binary search over the offsets;
+//      CTA round writes 2048 consecutive pairs; the scan also records the
+//      splat that owns each round's first pair, and each pair finds its splat
+//      by binary search over the round's staged offsets;
 //   4. stable radix sort of the pairs on the tile id (only the bits the tile
 //      count needs), which keeps depth-then-id order inside each tile;
 //   5. tile ranges [start, end) and, on request, the 64-bit keys.
@@ -275,7 +276,9 @@ __global__ void __launch_bounds__(1024) scan_block_sums(uint32_t *__restrict__ s
     }
 }
 
-// Pass B: write the covering splats' ids and depth keys in id order.
+// Pass B: write the covering splats' ids and depth keys in id order.  Each
+// thread owns 8 consecutive candidates of a 2048-candidate tile (one block
+// scan per tile).
 __global__ void __launch_bounds__(kSortThreads) compact_valid_kernel(
     const int32_t *__restrict__ tiles, const float4 *__restrict__ rec,
     const int32_t *__restrict__ view_start, int V, int k, long long cap_cand,
@@ -287,15 +290,33 @@ __global__ void __launch_bounds__(kSortThreads) compact_valid_kernel(
     uint32_t t0, t1;
     block_tiles(C, blockIdx.x, gridDim.x, &t0, &t1);
     __shared__ uint32_t s_warp[32];
+    const bool vec = (reinterpret_cast<uintptr_t>(tiles) & 15) == 0;
     uint32_t base = block_off[blockIdx.x];
-    for (uint32_t tb = t0 * kSortTile; tb < min(C, t1 * kSortTile); tb += kSortThreads) {
-        const uint32_t i = tb + threadIdx.x;
-        const uint32_t ok = (i < C) && __ldg(tiles + i) > 0;
+    for (uint32_t t = t0; t < t1; ++t) {
+        const uint32_t i0 = t * kSortTile + threadIdx.x * kSortItems;
+        int32_t tl[kSortItems];
+        if (vec && i0 + kSortItems <= C) {
+            const int4 u = __ldg(reinterpret_cast<const int4 *>(tiles + i0));
+            const int4 w = __ldg(reinterpret_cast<const int4 *>(tiles + i0) + 1);
+            tl[0] = u.x; tl[1] = u.y; tl[2] = u.z; tl[3] = u.w; tl[4] = w.x; tl[5] = w.y; tl[6] = w.z; tl[7] = w.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < kSortItems; ++j) tl[j] = i0 + j < C ? __ldg(tiles + i0 + j) : 0;
+        }
+        uint32_t n = 0;
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) n += tl[j] > 0;
         uint32_t tot;
-        const uint32_t off = scan256(ok, s_warp, &tot);
-        if (ok && idx_ok(st, (long long)base + off, C, 31)) {
-            ids[base + off] = i;
-            dkeys[base + off] = __float_as_uint(__ldg(&rec[3 * (size_t)i + 2]).y);
+        uint32_t off = base + scan256(n, s_warp, &tot);
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            if (tl[j] > 0) {
+                if (idx_ok(st, (long long)off, C, 31)) {
+                    ids[off] = i0 + j;
+                    dkeys[off] = __float_as_uint(__ldg(&rec[3 * (size_t)(i0 + j) + 2]).y);
+                }
+                ++off;
+            }
         }
         base += tot;
     }
@@ -320,11 +341,17 @@ __global__ void __launch_bounds__(kSortThreads) count_pairs_kernel(
     if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
 }
 
+constexpr int kEmitPairs = 2048;   // pairs written per CTA and round
+
 // Per-splat pair offsets in depth order: offs[i] = sum of the tile counts of
-// splats 0..i-1 (block prefixes from scan_block_sums).
+// splats 0..i-1 (block prefixes from scan_block_sums), 8 splats per thread
+// and one block scan per 2048 splats.  Every splat owns >= 1 pair, so each
+// emission round r (pairs [2048 r, 2048 r + 2048)) starts inside exactly one
+// splat's range [offs[i], offs[i] + count): that splat writes round_first[r].
 __global__ void __launch_bounds__(kSortThreads) pair_offsets_kernel(
     const uint32_t *__restrict__ ids, const uint32_t *__restrict__ n_ptr, const int32_t *__restrict__ tiles,
-    const uint32_t *__restrict__ block_off, uint32_t *__restrict__ offs, long long cap_cand, const gs_status *st)
+    const uint32_t *__restrict__ block_off, uint32_t *__restrict__ offs, uint32_t *__restrict__ round_first,
+    long long max_rounds, long long cap_cand, const gs_status *st)
 {
     if (has_error(st)) return;
     const uint32_t S = *n_ptr;
@@ -332,54 +359,109 @@ __global__ void __launch_bounds__(kSortThreads) pair_offsets_kernel(
     block_tiles(S, blockIdx.x, gridDim.x, &t0, &t1);
     __shared__ uint32_t s_warp[32];
     uint32_t base = block_off[blockIdx.x];
-    for (uint32_t tb = t0 * kSortTile; tb < min(S, t1 * kSortTile); tb += kSortThreads) {
-        const uint32_t i = tb + threadIdx.x;
-        uint32_t cnt = 0;
-        if (i < S) {
-            const uint32_t id = ids[i];
-            if (idx_ok(st, id, cap_cand, 35)) cnt = (uint32_t)__ldg(tiles + id);
+    for (uint32_t t = t0; t < t1; ++t) {
+        const uint32_t i0 = t * kSortTile + threadIdx.x * kSortItems;
+        uint32_t cnt[kSortItems];
+        uint32_t n = 0;
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            cnt[j] = 0;
+            if (i0 + j < S) {
+                const uint32_t id = ids[i0 + j];
+                if (idx_ok(st, id, cap_cand, 35)) cnt[j] = (uint32_t)__ldg(tiles + id);
+            }
+            n += cnt[j];
         }
         uint32_t tot;
-        const uint32_t off = base + scan256(cnt, s_warp, &tot);
-        if (i < S) offs[i] = off;
+        uint32_t off = base + scan256(n, s_warp, &tot);
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            if (i0 + j < S) {
+                offs[i0 + j] = off;
+                const unsigned long long end = (unsigned long long)off + cnt[j];
+                for (unsigned long long r = ((unsigned long long)off + kEmitPairs - 1) / kEmitPairs;
+                     r * kEmitPairs < end; ++r)
+                    if (idx_ok(st, (long long)r, max_rounds, 37)) round_first[r] = i0 + j;
+                off += cnt[j];
+            }
+        }
         base += tot;
     }
 }
 
-constexpr int kEmitPairs = 2048;   // pairs written per CTA and round
+// Exclusive max-scan over the 256 threads of a block.
+__device__ __forceinline__ uint32_t scanmax256_excl(uint32_t x, uint32_t *s_warp)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t v = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v = max(v, y);
+    }
+    if (lane == 31) s_warp[warp] = v;
+    __syncthreads();
+    uint32_t ex = __shfl_up_sync(0xffffffffu, v, 1);
+    if (lane == 0) ex = 0;
+    for (int w = 0; w < warp; ++w) ex = max(ex, s_warp[w]);
+    __syncthreads();
+    return ex;
+}
 
 // Load-balanced emission: CTA rounds write pairs [p0, p0 + 2048).  The splats
-// that own those pairs (at most 2048, every compacted splat owns >= 1) are
-// staged with their rectangle's first tile, width and the view's tile row
-// length; each pair finds its splat by binary search over the staged offsets
-// and writes (tile id, splat id) -- pair t of a splat is tile (t % w, t / w)
+// that own those pairs (at most 2048, every compacted splat owns >= 1; the
+// first from round_first, the last from the next round's first) are staged
+// with their rectangle's first tile, width and the view's tile row length
+// (every thread's loads issued together); each staged splat marks the
+// round-local position of its first pair in s_own and a max-scan fills every
+// pair's position with its owner.  Pair t of a splat is tile (t % w, t / w)
 // of its rectangle, row-major.
 __global__ void __launch_bounds__(kSortThreads) emit_pairs_kernel(
     const uint32_t *__restrict__ ids, const uint32_t *__restrict__ n_ptr, const uint32_t *__restrict__ np_ptr,
-    const uint32_t *__restrict__ offs, const float4 *__restrict__ rec,
+    const uint32_t *__restrict__ offs, const uint32_t *__restrict__ round_first, const float4 *__restrict__ rec,
     const int32_t *__restrict__ view_start, int k, uint32_t *__restrict__ tkeys, uint32_t *__restrict__ tvals,
     ViewTable vt, long long cap_cand, const gs_status *st)
 {
     if (has_error(st)) return;
+    constexpr int kPer = kEmitPairs / kSortThreads;   // staged splats / pairs per thread and round
     const uint32_t S = *n_ptr, P = *np_ptr;
     __shared__ uint32_t s_off[kEmitPairs], s_t00[kEmitPairs], s_id[kEmitPairs];
+    __shared__ __align__(16) uint32_t s_own[kEmitPairs];
     __shared__ uint16_t s_w[kEmitPairs], s_tx[kEmitPairs];
-    __shared__ uint32_t s_first, s_count;
+    __shared__ uint32_t s_first, s_count, s_warp[32];
+    const int tid = threadIdx.x;
+    uint4 *own4 = reinterpret_cast<uint4 *>(s_own);
     for (uint32_t p0 = blockIdx.x * (uint32_t)kEmitPairs; p0 < P; p0 += gridDim.x * (uint32_t)kEmitPairs) {
         const uint32_t p1 = min(P, p0 + (uint32_t)kEmitPairs);
-        if (threadIdx.x == 0) {   // splats owning p0 and p1 - 1: last s with offs[s] <= p
-            uint32_t a = 0, b = S - 1;
-            while (a < b) { const uint32_t m = (a + b + 1) >> 1; if (offs[m] <= p0) a = m; else b = m - 1; }
-            uint32_t c = a, d = S - 1;
-            while (c < d) { const uint32_t m = (c + d + 1) >> 1; if (offs[m] <= p1 - 1) c = m; else d = m - 1; }
+        if (tid == 0) {   // splats owning p0 and p1 - 1
+            const uint32_t r = p0 / (uint32_t)kEmitPairs;
+            const uint32_t a = round_first[r];
+            uint32_t c = S - 1;
+            if (p1 < P) {   // the splat owning p1, unless p1 starts it
+                c = round_first[r + 1];
+                if (idx_ok(st, (long long)c, S, 39) && offs[c] == p1) --c;
+            }
+            const bool ok = idx_ok(st, (long long)a, S, 39) && idx_ok(st, (long long)c, S, 39) &&
+                            idx_ok(st, (long long)c - (long long)a, kEmitPairs, 39);
             s_first = a;
-            s_count = idx_ok(st, (long long)(c - a), kEmitPairs, 39) ? c - a + 1 : 0;
+            s_count = ok ? c - a + 1 : 0;
         }
+        own4[2 * tid] = make_uint4(0u, 0u, 0u, 0u);
+        own4[2 * tid + 1] = make_uint4(0u, 0u, 0u, 0u);
         __syncthreads();
         const uint32_t sa = s_first, ns = s_count;
-        for (uint32_t j = threadIdx.x; j < ns; j += kSortThreads) {
-            const uint32_t sidx = sa + j;
-            const uint32_t id = ids[sidx];
+        uint32_t idv[kPer];
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const uint32_t j = tid + u * kSortThreads;
+            idv[u] = j < ns ? ids[sa + j] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const uint32_t j = tid + u * kSortThreads;
+            if (j >= ns) continue;
+            const uint32_t sidx = sa + j, id = idv[u];
+            const uint32_t o = offs[sidx];
             uint32_t t00 = 0, w = 1, tx = 1;
             if (idx_ok(st, id, cap_cand, 36)) {
                 const float4 r2 = __ldg(&rec[3 * (size_t)id + 2]);
@@ -387,23 +469,37 @@ __global__ void __launch_bounds__(kSortThreads) emit_pairs_kernel(
                 const int x0 = rx & 0xffff, x1 = rx >> 16, y0 = ry & 0xffff, y1 = ry >> 16;
                 const int v = view_of_row(view_start, vt.V, (int)(id / (uint32_t)k));
                 // the splat's tile count from its offsets (no second read of tiles_touched)
-                const long long cnt = (long long)(sidx + 1 < S ? offs[sidx + 1] : P) - (long long)offs[sidx];
+                const long long cnt = (long long)(sidx + 1 < S ? offs[sidx + 1] : P) - (long long)o;
                 if ((long long)(x1 - x0) * (y1 - y0) != cnt || x1 > vt.TX[v] || y1 > vt.TY[v] || x1 <= x0)
                     idx_ok(st, (long long)id, -1, 36);
                 w = (uint32_t)max(x1 - x0, 1);
                 tx = (uint32_t)vt.TX[v];
                 t00 = (uint32_t)vt.tile_base[v] + (uint32_t)(y0 * vt.TX[v] + x0);
             }
-            s_off[j] = offs[sidx];
+            s_off[j] = o;
             s_t00[j] = t00;
             s_w[j] = (uint16_t)w;
             s_tx[j] = (uint16_t)tx;
             s_id[j] = id;
+            const uint32_t at = o > p0 ? o - p0 : 0u;   // the first staged splat starts at or before p0
+            if (idx_ok(st, (long long)at, kEmitPairs, 39)) s_own[at] = j;
         }
         __syncthreads();
-        for (uint32_t p = p0 + threadIdx.x; ns > 0 && p < p1; p += kSortThreads) {
-            uint32_t a = 0, b = ns - 1;
-            while (a < b) { const uint32_t m = (a + b + 1) >> 1; if (s_off[m] <= p) a = m; else b = m - 1; }
+        {   // fill forward: thread t owns positions 8t .. 8t + 7
+            const uint4 lo = own4[2 * tid], hi = own4[2 * tid + 1];
+            uint32_t v[kPer] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+            uint32_t m = 0;
+#pragma unroll
+            for (int u = 0; u < kPer; ++u) { m = max(m, v[u]); v[u] = m; }
+            const uint32_t pre = scanmax256_excl(m, s_warp);
+#pragma unroll
+            for (int u = 0; u < kPer; ++u) v[u] = max(v[u], pre);
+            own4[2 * tid] = make_uint4(v[0], v[1], v[2], v[3]);
+            own4[2 * tid + 1] = make_uint4(v[4], v[5], v[6], v[7]);
+        }
+        __syncthreads();
+        for (uint32_t i = tid; ns > 0 && p0 + i < p1; i += kSortThreads) {
+            const uint32_t p = p0 + i, a = s_own[i];
             const uint32_t t = p - s_off[a], w = s_w[a];
             const uint32_t yy = t / w, xx = t - yy * w;
             tkeys[p] = s_t00[a] + yy * (uint32_t)s_tx[a] + xx;
@@ -444,11 +540,12 @@ __global__ void __launch_bounds__(256) keys_kernel(const uint32_t *__restrict__ 
 
 // ------------------------------------------------------------------ driver
 struct SortLayout {
-    size_t ids_a, ids_b, dk_a, dk_b, offs, tk_a, tk_b, tv_b, hist, totals, sums, counts, total;
+    size_t ids_a, ids_b, dk_a, dk_b, offs, rfirst, tk_a, tk_b, tv_b, hist, totals, sums, counts, total;
+    long long max_rounds;
     int nb;
 };
 
-static int sort_blocks() { return std::min(1024, sm_count() * 2); }
+static int sort_blocks() { return std::min(1024, sm_count() * 4); }
 
 static SortLayout layout(long long cap_cand, long long cap_pairs)
 {
@@ -461,6 +558,8 @@ static SortLayout layout(long long cap_cand, long long cap_pairs)
     L.dk_a = take(sizeof(uint32_t) * std::max<long long>(cap_cand, 1));
     L.dk_b = take(sizeof(uint32_t) * std::max<long long>(cap_cand, 1));
     L.offs = take(sizeof(uint32_t) * std::max<long long>(cap_cand, 1));
+    L.max_rounds = std::max<long long>(cap_pairs, 0) / kEmitPairs + 2;
+    L.rfirst = take(sizeof(uint32_t) * (size_t)L.max_rounds);
     L.tk_a = take(sizeof(uint32_t) * std::max<long long>(cap_pairs, 1));
     L.tk_b = take(sizeof(uint32_t) * std::max<long long>(cap_pairs, 1));
     L.tv_b = take(sizeof(uint32_t) * std::max<long long>(cap_pairs, 1));
@@ -506,6 +605,7 @@ int launch_bin_sort(const gs_splats *sp, int k, const int32_t *view_start, long 
     uint32_t *dk_a = (uint32_t *)(w + L.dk_a), *dk_b = (uint32_t *)(w + L.dk_b);
     uint32_t *tk_a = (uint32_t *)(w + L.tk_a), *tk_b = (uint32_t *)(w + L.tk_b);
     uint32_t *tv_b = (uint32_t *)(w + L.tv_b), *offs = (uint32_t *)(w + L.offs);
+    uint32_t *rfirst = (uint32_t *)(w + L.rfirst);
     uint32_t *hist = (uint32_t *)(w + L.hist), *totals = (uint32_t *)(w + L.totals);
     uint32_t *sums = (uint32_t *)(w + L.sums), *counts = (uint32_t *)(w + L.counts);
     const float4 *rec = reinterpret_cast<const float4 *>(sp->rec);
@@ -530,8 +630,9 @@ int launch_bin_sort(const gs_splats *sp, int k, const int32_t *view_start, long 
     // choose the emission buffers so that the last pass lands in bins->vals
     uint32_t *ek = tk_a, *ev = (passes % 2 == 0) ? bins->vals : tv_b;
     uint32_t *ok = tk_b, *ov = (passes % 2 == 0) ? tv_b : bins->vals;
-    pair_offsets_kernel<<<nb, kSortThreads, 0, s>>>(ids_s, n_splats, sp->tiles, sums, offs, cap_cand, st);
-    emit_pairs_kernel<<<sm_count() * 4, kSortThreads, 0, s>>>(ids_s, n_splats, n_pairs, offs, rec,
+    pair_offsets_kernel<<<nb, kSortThreads, 0, s>>>(ids_s, n_splats, sp->tiles, sums, offs, rfirst, L.max_rounds,
+                                                    cap_cand, st);
+    emit_pairs_kernel<<<sm_count() * 4, kSortThreads, 0, s>>>(ids_s, n_splats, n_pairs, offs, rfirst, rec,
                                                               view_start, k, ek, ev, vt, cap_cand, st);
     count_launches(4);
     // 4. stable sort on the tile id

@@ -46,16 +46,23 @@ __device__ __forceinline__ float warp_sum8(const float v[8])
     return r;
 }
 
-// Reverse state of one pixel.
+// Reverse state of one pixel: transmittance, S = g . (colour composited
+// behind the current splat, background included) with g = dL/dC of the pixel.
 struct PixBwd {
-    float T, B0, B1, B2, g0, g1, g2;
+    float T, S, g0, g1, g2;
     int last;
 };
 
-// Gradient terms of one pixel for staged splat j, added to acc[9] =
-// (d mean x, d mean y, d conic a, b, c, d opacity, d r, d g, d b).
-__device__ __forceinline__ bool bwd_step(PixBwd &ps, const float4 a, const float4 bb, float cb, float io, float px,
-                                         float py, float acc[9])
+// Gradient terms of one pixel for a staged splat, added to the per-splat sums
+// acc[9] = (m_x, m_y, m_xx, m_xy, m_yy, sum dal exp(power), d r, d g, d b) with
+// dp = dL/dpower and the moments m_x = sum dp dx, m_y = sum dp dy, m_xx = sum
+// dp dx^2, m_xy = sum dp dx dy, m_yy = sum dp dy^2 over the pixels; after the
+// warp reduction they become d mean2d and d conic (conic_grads) and the
+// opacity sum is divided by the opacity.  Eq. 1 gives, for splat i with
+// transmittance T_i in front of it, dC/dalpha_i = T_i c_i - B_i / (1 - alpha_i)
+// (B_i: colour behind i), so only the scalar g . B_i is carried.
+__device__ __forceinline__ bool bwd_step(PixBwd &ps, const float4 a, const float4 bb, float cb, float px, float py,
+                                         float acc[9])
 {
     float dx, dy;
     const float q = splat_q(a, bb.x, px, py, &dx, &dy);
@@ -70,23 +77,51 @@ __device__ __forceinline__ bool bwd_step(PixBwd &ps, const float4 a, const float
     acc[6] = fmaf(w, ps.g0, acc[6]);
     acc[7] = fmaf(w, ps.g1, acc[7]);
     acc[8] = fmaf(w, ps.g2, acc[8]);
-    const float gc = ps.g0 * bb.z + ps.g1 * bb.w + ps.g2 * cb;
-    const float gB = ps.g0 * ps.B0 + ps.g1 * ps.B1 + ps.g2 * ps.B2;
-    const float dal = gc * ps.T - gB * inv;
-    ps.B0 = fmaf(bb.z, w, ps.B0);
-    ps.B1 = fmaf(bb.w, w, ps.B1);
-    ps.B2 = fmaf(cb, w, ps.B2);
-    if (ag < kAlphaMax) {
-        acc[5] = fmaf(dal, ag * io, acc[5]);          // d opacity = dal * exp(power)
-        const float dp = dal * alpha;                 // d power
-        const float dpl = dp * 0.6931471805599453f;   // power = ln 2 * (A dx^2 + B dx dy + C dy^2)
-        acc[0] = fmaf(dpl, fmaf(2.f * a.z, dx, a.w * dy), acc[0]);
-        acc[1] = fmaf(dpl, fmaf(2.f * bb.x, dy, a.w * dx), acc[1]);
-        acc[2] = fmaf(-0.5f * dp, dx * dx, acc[2]);
-        acc[3] = fmaf(-dp, dx * dy, acc[3]);
-        acc[4] = fmaf(-0.5f * dp, dy * dy, acc[4]);
+    const float gc = fmaf(ps.g0, bb.z, fmaf(ps.g1, bb.w, ps.g2 * cb));
+    const float dal = fmaf(gc, ps.T, -ps.S * inv);
+    ps.S = fmaf(gc, w, ps.S);
+    if (ag < kAlphaMax) {                  // the clamped branch passes no gradient to o exp(power)
+        acc[5] = fmaf(dal, ag, acc[5]);
+        const float dp = dal * alpha;      // d power (alpha = o exp(power))
+        const float t = dp * dx, u = dp * dy;
+        acc[0] += t;
+        acc[1] += u;
+        acc[2] = fmaf(t, dx, acc[2]);
+        acc[3] = fmaf(t, dy, acc[3]);
+        acc[4] = fmaf(u, dy, acc[4]);
     }
     return true;
+}
+
+// Per-splat gradient from the reduced sums for the calling lane's value index
+// vi (warp_sum8 layout; `other` is the total of index vi ^ 1).  power = ln 2
+// ((A dx + B dy) dx + C dy^2) with the record's A, B, C, and power = -(c_a
+// dx^2 + c_c dy^2) / 2 - c_b dx dy with the conic (c_a, c_b, c_c), so
+//   d mean x = ln 2 (2 A m_x + B m_y),  d mean y = ln 2 (2 C m_y + B m_x),
+//   d c_a = -m_xx / 2,  d c_b = -m_xy,  d c_c = -m_yy / 2,
+// and d opacity = (sum dal exp(power)) / opacity.  The lane's role is fixed,
+// so the selection is branch-free: g = cs total + co other.
+struct LaneRole {
+    bool mx, my, op, mean;
+    float k;   // constant factor of the other indices
+};
+__device__ __forceinline__ LaneRole lane_role(int vi)
+{
+    LaneRole r;
+    r.mx = vi == 0;
+    r.my = vi == 1;
+    r.op = vi == 5;
+    r.mean = vi < 2;
+    r.k = (vi == 2 || vi == 4) ? -0.5f : (vi == 3 ? -1.f : 1.f);
+    return r;
+}
+__device__ __forceinline__ float conic_grads(const LaneRole &r, float total, float other, float4 a, float4 bb,
+                                             float io)
+{
+    constexpr float ln2 = 0.6931471805599453f;
+    const float cs = r.mx ? (2.f * ln2) * a.z : (r.my ? (2.f * ln2) * bb.x : (r.op ? io : r.k));
+    const float co = r.mean ? ln2 * a.w : 0.f;
+    return fmaf(cs, total, co * other);
 }
 
 __device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const uint32_t *__restrict__ vals,
@@ -109,8 +144,14 @@ __device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const u
     const int n_items = (int)(it.s1 - it.s0);
     PixBwd p0, p1;
     p0.T = p1.T = 1.f;
-    p0.B0 = p0.B1 = p0.B2 = p1.B0 = p1.B1 = p1.B2 = 0.f;
+    p0.S = p1.S = 0.f;
     p0.last = p1.last = 0;
+    p0.g0 = p0.g1 = p0.g2 = p1.g0 = p1.g1 = p1.g2 = 0.f;
+    {
+        const float *dimg = d_image + 3 * vt.pix_base[v];
+        if (tc.in0) { p0.g0 = dimg[pix0]; p0.g1 = dimg[W * H + pix0]; p0.g2 = dimg[2 * W * H + pix0]; }
+        if (tc.in1) { p1.g0 = dimg[pix1]; p1.g1 = dimg[W * H + pix1]; p1.g2 = dimg[2 * W * H + pix1]; }
+    }
     if (it.nk > 1) {
         // forward state of the chunk: entering transmittance (activity), end
         // transmittance, last position, colour composited behind it
@@ -124,9 +165,10 @@ __device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const u
                 ps.T = state_plane(plan.state, item, 1)[pix];
                 ps.last = reinterpret_cast<const int *>(state_plane(plan.state, item, 5))[pix];
                 // colour behind the chunk: final colour - prefix up to the chunk
-                ps.B0 = state_plane(plan.state, it.base, 7)[pix] - state_plane(plan.state, item, 2)[pix];
-                ps.B1 = state_plane(plan.state, it.base, 8)[pix] - state_plane(plan.state, item, 3)[pix];
-                ps.B2 = state_plane(plan.state, it.base, 9)[pix] - state_plane(plan.state, item, 4)[pix];
+                const float B0 = state_plane(plan.state, it.base, 7)[pix] - state_plane(plan.state, item, 2)[pix];
+                const float B1 = state_plane(plan.state, it.base, 8)[pix] - state_plane(plan.state, item, 3)[pix];
+                const float B2 = state_plane(plan.state, it.base, 9)[pix] - state_plane(plan.state, item, 4)[pix];
+                ps.S = fmaf(ps.g0, B0, fmaf(ps.g1, B1, ps.g2 * B2));
             } else {
                 ps.last = 0;
             }
@@ -134,8 +176,8 @@ __device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const u
     } else if (T_final_in) {
         if (tc.in0) { p0.T = T_final_in[vt.pix_base[v] + pix0]; p0.last = min(last_in[vt.pix_base[v] + pix0], n_items); }
         if (tc.in1) { p1.T = T_final_in[vt.pix_base[v] + pix1]; p1.last = min(last_in[vt.pix_base[v] + pix1], n_items); }
-        p0.B0 = p0.T * bg0; p0.B1 = p0.T * bg1; p0.B2 = p0.T * bg2;
-        p1.B0 = p1.T * bg0; p1.B1 = p1.T * bg1; p1.B2 = p1.T * bg2;
+        p0.S = p0.T * fmaf(p0.g0, bg0, fmaf(p0.g1, bg1, p0.g2 * bg2));
+        p1.S = p1.T * fmaf(p1.g0, bg0, fmaf(p1.g1, bg1, p1.g2 * bg2));
     } else {
         // recompute the forward transmittance and the last composited position (per warp)
         bool d0 = !tc.in0, d1 = !tc.in1;
@@ -174,16 +216,12 @@ __device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const u
             }
             __syncwarp();
         }
-        p0.B0 = p0.T * bg0; p0.B1 = p0.T * bg1; p0.B2 = p0.T * bg2;
-        p1.B0 = p1.T * bg0; p1.B1 = p1.T * bg1; p1.B2 = p1.T * bg2;
-    }
-    p0.g0 = p0.g1 = p0.g2 = p1.g0 = p1.g1 = p1.g2 = 0.f;
-    {
-        const float *dimg = d_image + 3 * vt.pix_base[v];
-        if (tc.in0) { p0.g0 = dimg[pix0]; p0.g1 = dimg[W * H + pix0]; p0.g2 = dimg[2 * W * H + pix0]; }
-        if (tc.in1) { p1.g0 = dimg[pix1]; p1.g1 = dimg[W * H + pix1]; p1.g2 = dimg[2 * W * H + pix1]; }
+        p0.S = p0.T * fmaf(p0.g0, bg0, fmaf(p0.g1, bg1, p0.g2 * bg2));
+        p1.S = p1.T * fmaf(p1.g0, bg0, fmaf(p1.g1, bg1, p1.g2 * bg2));
     }
     // back to front over the warp's chunk positions [0, maxlast), 32 at a time
+    const int vi = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+    const LaneRole role = lane_role(vi);
     const int maxlast = min(__reduce_max_sync(0xffffffffu, max(p0.last, p1.last)), n_items);
     for (int hi = maxlast; hi > 0; hi -= 32) {
         const int pl = hi - 1 - lane;   // lane l <-> position hi - 1 - l: hits come back to front
@@ -193,18 +231,20 @@ __device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const u
             const int p = WSw.pos[e];
             float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             bool contrib = false;
+            const float4 a = WSw.a[e];
+            const float4 bb = WSw.b[e];
             if (p < p0.last || p < p1.last) {
-                const float4 a = WSw.a[e];
-                const float4 bb = WSw.b[e];
-                const float cb = WSw.c[e], io = WSw.io[e];
-                if (p < p0.last) contrib |= bwd_step(p0, a, bb, cb, io, fpx, fy0, acc);
-                if (p < p1.last) contrib |= bwd_step(p1, a, bb, cb, io, fpx, fy1, acc);
+                const float cb = WSw.c[e];
+                if (p < p0.last) contrib |= bwd_step(p0, a, bb, cb, fpx, fy0, acc);
+                if (p < p1.last) contrib |= bwd_step(p1, a, bb, cb, fpx, fy1, acc);
             }
             if (__any_sync(0xffffffffu, contrib)) {
                 const float t8 = warp_sum8(acc);
                 const float t9 = warp_sum(acc[8]);
+                const float other = __shfl_xor_sync(0xffffffffu, t8, 4);
+                const float g = conic_grads(role, t8, other, a, bb, WSw.io[e]);
                 float *o = sgrad + 9 * (size_t)WSw.id[e];
-                if ((lane & 3) == 0) atomicAdd(o + (((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1)), t8);
+                if ((lane & 3) == 0) atomicAdd(o + vi, g);
                 if (lane == 1) atomicAdd(o + 8, t9);
             }
         }

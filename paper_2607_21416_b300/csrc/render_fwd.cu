@@ -291,6 +291,8 @@ __global__ void __launch_bounds__(kRThreads) chunk_kernel(const float4 *__restri
 // chunk can then meet the stop rule; the first chunk where that fails holds
 // the pixel's stop and is marked for the fix-up, with T0 and the colour in
 // front of it in its Tend / colour planes and last = -1.
+constexpr int kCombineAhead = 16;   // chunk states loaded per group by the combine walk
+
 template <bool COUNT>
 __global__ void __launch_bounds__(2 * kRThreads) combine_kernel(const uint32_t *__restrict__ ranges, ViewTable vt,
                                                             RenderPlan plan, float bg0, float bg1, float bg2,
@@ -325,60 +327,71 @@ __global__ void __launch_bounds__(2 * kRThreads) combine_kernel(const uint32_t *
         if (T0 == 0.f) {       // chunk 0 stopped the pixel
             T0 = state_plane(plan.state, base, 1)[pix];
         } else {
-            // chunk k + 1's state is read before chunk k's is written (different
-            // items: no overlap), so the walk is not one load latency per chunk
-            float nTp = 0.f, na0 = 0.f, na1 = 0.f, na2 = 0.f;
-            int nl = 0, nc = 0;
-            auto fetch = [&](int kk) {
-                const int it2 = base + kk;
-                nTp = state_plane(plan.state, it2, 0)[pix];
-                na0 = state_plane(plan.state, it2, 2)[pix];
-                na1 = state_plane(plan.state, it2, 3)[pix];
-                na2 = state_plane(plan.state, it2, 4)[pix];
-                nl = reinterpret_cast<const int *>(state_plane(plan.state, it2, 5))[pix];
-                if (COUNT) nc = reinterpret_cast<const int *>(state_plane(plan.state, it2, 6))[pix];
-            };
-            if (k < nk) fetch(k);
-            for (; k < nk; ++k) {
-                if (!(T0 >= kTMin)) break;
-                const int item = base + k;
-                const float Tp = nTp, a0 = na0, a1 = na1, a2 = na2;
-                const int lk = nl, ck = nc;
-                if (k + 1 < nk) fetch(k + 1);
-                float *tp = state_plane(plan.state, item, 0);
-                float *te = state_plane(plan.state, item, 1);
-                float *c0 = state_plane(plan.state, item, 2), *c1 = state_plane(plan.state, item, 3);
-                float *c2 = state_plane(plan.state, item, 4);
-                int *lp = reinterpret_cast<int *>(state_plane(plan.state, item, 5));
-                tp[pix] = T0;
-                const float T1 = __fmul_rn(T0, Tp);
-                if (T1 >= kTMin) {   // no stop inside: the chunk's true contribution
-                    C0 += T0 * a0;
-                    C1 += T0 * a1;
-                    C2 += T0 * a2;
-                    c0[pix] = C0;
-                    c1[pix] = C1;
-                    c2[pix] = C2;
-                    te[pix] = T1;
-                    if (lk > 0) lastg = k * plan.L + lk;
-                    if (COUNT && inside) {
-                        nev += min((uint32_t)plan.L, s_end - (s_start + (uint32_t)k * (uint32_t)plan.L));
-                        ncomp += ck;
+            // the chunks' states are read kCombineAhead at a time before any of
+            // them is written (different items: no overlap), so the walk waits
+            // for one load latency per group instead of one per chunk
+            bool go = true;
+            while (go && k < nk) {
+                const int k0 = k;
+                float gTp[kCombineAhead], ga0[kCombineAhead], ga1[kCombineAhead], ga2[kCombineAhead];
+                int gl[kCombineAhead], gc[kCombineAhead];
+#pragma unroll
+                for (int g = 0; g < kCombineAhead; ++g) {
+                    gTp[g] = ga0[g] = ga1[g] = ga2[g] = 0.f;
+                    gl[g] = gc[g] = 0;
+                    if (k0 + g < nk) {
+                        const int it2 = base + k0 + g;
+                        gTp[g] = state_plane(plan.state, it2, 0)[pix];
+                        ga0[g] = state_plane(plan.state, it2, 2)[pix];
+                        ga1[g] = state_plane(plan.state, it2, 3)[pix];
+                        ga2[g] = state_plane(plan.state, it2, 4)[pix];
+                        gl[g] = reinterpret_cast<const int *>(state_plane(plan.state, it2, 5))[pix];
+                        if (COUNT) gc[g] = reinterpret_cast<const int *>(state_plane(plan.state, it2, 6))[pix];
                     }
-                    T0 = T1;
-                } else {             // the pixel's stop lies in chunk k
-                    te[pix] = T0;
-                    c0[pix] = C0;
-                    c1[pix] = C1;
-                    c2[pix] = C2;
-                    lp[pix] = -1;
-                    if (inside) {
-                        if (atomicExch(plan.fix + item, 1) == 0) plan.fix_list[atomicAdd(plan.counters + 3, 1)] = item;
-                        if (last) last[vt.pix_base[tc.v] + (long long)py * vt.W[tc.v] + tc.px] = lastg;
+                }
+#pragma unroll
+                for (int g = 0; g < kCombineAhead; ++g) {
+                    const int kk = k0 + g;
+                    if (!go || kk >= nk) continue;
+                    if (!(T0 >= kTMin)) { k = kk; go = false; continue; }
+                    const int item = base + kk;
+                    float *tp = state_plane(plan.state, item, 0);
+                    float *te = state_plane(plan.state, item, 1);
+                    float *c0 = state_plane(plan.state, item, 2), *c1 = state_plane(plan.state, item, 3);
+                    float *c2 = state_plane(plan.state, item, 4);
+                    int *lp = reinterpret_cast<int *>(state_plane(plan.state, item, 5));
+                    tp[pix] = T0;
+                    const float T1 = __fmul_rn(T0, gTp[g]);
+                    if (T1 >= kTMin) {   // no stop inside: the chunk's true contribution
+                        C0 += T0 * ga0[g];
+                        C1 += T0 * ga1[g];
+                        C2 += T0 * ga2[g];
+                        c0[pix] = C0;
+                        c1[pix] = C1;
+                        c2[pix] = C2;
+                        te[pix] = T1;
+                        if (gl[g] > 0) lastg = kk * plan.L + gl[g];
+                        if (COUNT && inside) {
+                            nev += min((uint32_t)plan.L, s_end - (s_start + (uint32_t)kk * (uint32_t)plan.L));
+                            ncomp += gc[g];
+                        }
+                        T0 = T1;
+                        k = kk + 1;
+                    } else {             // the pixel's stop lies in chunk kk
+                        te[pix] = T0;
+                        c0[pix] = C0;
+                        c1[pix] = C1;
+                        c2[pix] = C2;
+                        lp[pix] = -1;
+                        if (inside) {
+                            if (atomicExch(plan.fix + item, 1) == 0)
+                                plan.fix_list[atomicAdd(plan.counters + 3, 1)] = item;
+                            if (last) last[vt.pix_base[tc.v] + (long long)py * vt.W[tc.v] + tc.px] = lastg;
+                        }
+                        marked = true;
+                        k = kk + 1;
+                        go = false;
                     }
-                    marked = true;
-                    ++k;
-                    break;
                 }
             }
         }
