@@ -53,33 +53,41 @@ struct PixBwd {
     int last;
 };
 
-// Gradient terms of one pixel for a staged splat, added to the per-splat sums
-// acc[9] = (m_x, m_y, m_xx, m_xy, m_yy, sum dal exp(power), d r, d g, d b) with
-// dp = dL/dpower and the moments m_x = sum dp dx, m_y = sum dp dy, m_xx = sum
-// dp dx^2, m_xy = sum dp dx dy, m_yy = sum dp dy^2 over the pixels; after the
-// warp reduction they become d mean2d and d conic (conic_grads) and the
-// opacity sum is divided by the opacity.  Eq. 1 gives, for splat i with
-// transmittance T_i in front of it, dC/dalpha_i = T_i c_i - B_i / (1 - alpha_i)
-// (B_i: colour behind i), so only the scalar g . B_i is carried.
-__device__ __forceinline__ bool bwd_step(PixBwd &ps, const float4 a, const float4 bb, float cb, float px, float py,
-                                         float acc[9])
+// The alpha decision of Eq. 1 for one pixel (the forward's, operation for
+// operation): true iff the splat is composited at (px, py), with the offset
+// and the unclamped alpha o exp(power).
+__device__ __forceinline__ bool alpha_test(const float4 a, const float4 bb, float px, float py, float *dx, float *dy,
+                                           float *ag)
 {
-    float dx, dy;
-    const float q = splat_q(a, bb.x, px, py, &dx, &dy);
+    const float q = splat_q(a, bb.x, px, py, dx, dy);
     if (q > 0.f) return false;
-    const float ag = splat_alpha(q, bb.y);
+    *ag = splat_alpha(q, bb.y);
+    return fminf(kAlphaMax, *ag) >= kAlphaMin;
+}
+
+// Gradient terms of one pixel for a staged splat it composites, added to the
+// per-splat sums acc[9] = (m_x, m_y, m_xx, m_xy, m_yy, sum dal exp(power),
+// d r, d g, d b) with dp = dL/dpower and the moments m_x = sum dp dx, m_y =
+// sum dp dy, m_xx = sum dp dx^2, m_xy = sum dp dx dy, m_yy = sum dp dy^2 over
+// the pixels; after the warp reduction they become d mean2d and d conic
+// (conic_grads) and the opacity sum is divided by the opacity.  Eq. 1 gives,
+// for splat i with transmittance T_i in front of it, dC/dalpha_i = T_i c_i -
+// B_i / (1 - alpha_i) (B_i: colour behind i), so only the scalar S = g . B_i
+// is carried.  T and S are the pixel's reverse state, updated in place.
+__device__ __forceinline__ void bwd_composite(float &T, float &S, float g0, float g1, float g2, const float4 bb,
+                                              float cb, float dx, float dy, float ag, float acc[9])
+{
     const float alpha = fminf(kAlphaMax, ag);
-    if (alpha < kAlphaMin) return false;
     float inv;                             // 1 / (1 - alpha) on the SFU (relative error ~2^-23; the
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(1.f - alpha));   // operand lies in [0.01, 1))
-    ps.T = ps.T * inv;                     // transmittance in front of this splat
-    const float w = alpha * ps.T;
-    acc[6] = fmaf(w, ps.g0, acc[6]);
-    acc[7] = fmaf(w, ps.g1, acc[7]);
-    acc[8] = fmaf(w, ps.g2, acc[8]);
-    const float gc = fmaf(ps.g0, bb.z, fmaf(ps.g1, bb.w, ps.g2 * cb));
-    const float dal = fmaf(gc, ps.T, -ps.S * inv);
-    ps.S = fmaf(gc, w, ps.S);
+    T = T * inv;                           // transmittance in front of this splat
+    const float w = alpha * T;
+    acc[6] = fmaf(w, g0, acc[6]);
+    acc[7] = fmaf(w, g1, acc[7]);
+    acc[8] = fmaf(w, g2, acc[8]);
+    const float gc = fmaf(g0, bb.z, fmaf(g1, bb.w, g2 * cb));
+    const float dal = fmaf(gc, T, -S * inv);
+    S = fmaf(gc, w, S);
     if (ag < kAlphaMax) {                  // the clamped branch passes no gradient to o exp(power)
         acc[5] = fmaf(dal, ag, acc[5]);
         const float dp = dal * alpha;      // d power (alpha = o exp(power))
@@ -90,7 +98,6 @@ __device__ __forceinline__ bool bwd_step(PixBwd &ps, const float4 a, const float
         acc[3] = fmaf(t, dy, acc[3]);
         acc[4] = fmaf(u, dy, acc[4]);
     }
-    return true;
 }
 
 // Per-splat gradient from the reduced sums for the calling lane's value index
@@ -135,12 +142,19 @@ __device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const u
     if (!item_of(b, plan.item_base, vt.total_tiles, ranges, plan.L, &it)) return;
     const int lane = threadIdx.x & 31, tid = warp * 32 + lane;
     const TileCoord tc = tile_coord(vt, it.t, tid);
-    const float fpx = (float)tc.px, fy0 = (float)tc.py, fy1 = (float)(tc.py + 1);
-    const float bx0 = (float)tc.x0, bx1 = bx0 + (float)(kTile - 1);
-    const float by0 = (float)(tc.y0 + 4 * warp), by1 = by0 + 3.f;
+    // lane l of warp w owns pixels (x0 + c, y) and (x0 + c + 8, y) with c = l & 7 and y = y0 + 4 w +
+    // (l >> 3): a splat narrower than 9 pixels is composited by at most one pixel of each lane, so
+    // one composite pass per staged splat suffices (a second one only where a lane needs both)
+    const int col = lane & 7, row = 4 * warp + (lane >> 3);
     const int v = tc.v;
     const long long W = vt.W[v], H = vt.H[v];
-    const long long pix0 = (long long)tc.py * W + tc.px, pix1 = pix0 + W;
+    const int px0 = tc.x0 + col, py = tc.y0 + row;
+    const bool in0 = px0 < W && py < H, in1 = px0 + 8 < W && py < H;
+    const int pid0 = row * kTile + col, pid1 = pid0 + 8;
+    const float fx0 = (float)px0, fx1 = (float)(px0 + 8), fy = (float)py;
+    const float bx0 = (float)tc.x0, bx1 = bx0 + (float)(kTile - 1);
+    const float by0 = (float)(tc.y0 + 4 * warp), by1 = by0 + 3.f;
+    const long long pix0 = (long long)py * W + px0, pix1 = pix0 + 8;
     const int n_items = (int)(it.s1 - it.s0);
     PixBwd p0, p1;
     p0.T = p1.T = 1.f;
@@ -149,8 +163,8 @@ __device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const u
     p0.g0 = p0.g1 = p0.g2 = p1.g0 = p1.g1 = p1.g2 = 0.f;
     {
         const float *dimg = d_image + 3 * vt.pix_base[v];
-        if (tc.in0) { p0.g0 = dimg[pix0]; p0.g1 = dimg[W * H + pix0]; p0.g2 = dimg[2 * W * H + pix0]; }
-        if (tc.in1) { p1.g0 = dimg[pix1]; p1.g1 = dimg[W * H + pix1]; p1.g2 = dimg[2 * W * H + pix1]; }
+        if (in0) { p0.g0 = dimg[pix0]; p0.g1 = dimg[W * H + pix0]; p0.g2 = dimg[2 * W * H + pix0]; }
+        if (in1) { p1.g0 = dimg[pix1]; p1.g1 = dimg[W * H + pix1]; p1.g2 = dimg[2 * W * H + pix1]; }
     }
     if (it.nk > 1) {
         // forward state of the chunk: entering transmittance (activity), end
@@ -158,10 +172,10 @@ __device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const u
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
             PixBwd &ps = half ? p1 : p0;
-            const int pix = tc.pid0 + half * kTile;
+            const int pix = half ? pid1 : pid0;
             const int item = it.base + it.k;
             const float T0 = state_plane(plan.state, item, 0)[pix];
-            if (T0 >= kTMin && (half ? tc.in1 : tc.in0)) {
+            if (T0 >= kTMin && (half ? in1 : in0)) {
                 ps.T = state_plane(plan.state, item, 1)[pix];
                 ps.last = reinterpret_cast<const int *>(state_plane(plan.state, item, 5))[pix];
                 // colour behind the chunk: final colour - prefix up to the chunk
@@ -174,13 +188,13 @@ __device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const u
             }
         }
     } else if (T_final_in) {
-        if (tc.in0) { p0.T = T_final_in[vt.pix_base[v] + pix0]; p0.last = min(last_in[vt.pix_base[v] + pix0], n_items); }
-        if (tc.in1) { p1.T = T_final_in[vt.pix_base[v] + pix1]; p1.last = min(last_in[vt.pix_base[v] + pix1], n_items); }
+        if (in0) { p0.T = T_final_in[vt.pix_base[v] + pix0]; p0.last = min(last_in[vt.pix_base[v] + pix0], n_items); }
+        if (in1) { p1.T = T_final_in[vt.pix_base[v] + pix1]; p1.last = min(last_in[vt.pix_base[v] + pix1], n_items); }
         p0.S = p0.T * fmaf(p0.g0, bg0, fmaf(p0.g1, bg1, p0.g2 * bg2));
         p1.S = p1.T * fmaf(p1.g0, bg0, fmaf(p1.g1, bg1, p1.g2 * bg2));
     } else {
         // recompute the forward transmittance and the last composited position (per warp)
-        bool d0 = !tc.in0, d1 = !tc.in1;
+        bool d0 = !in0, d1 = !in1;
         for (uint32_t b0 = it.s0; b0 < it.s1; b0 += 32) {
             if (__all_sync(0xffffffffu, d0 && d1)) break;
             const uint32_t pos = b0 + lane;
@@ -192,7 +206,7 @@ __device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const u
                 const int q1 = WSw.pos[e] + 1;
                 float dx, dy;
                 if (!d0) {
-                    const float q = splat_q(a, bb.x, fpx, fy0, &dx, &dy);
+                    const float q = splat_q(a, bb.x, fx0, fy, &dx, &dy);
                     if (q <= 0.f) {
                         const float alpha = fminf(kAlphaMax, splat_alpha(q, bb.y));
                         if (alpha >= kAlphaMin) {
@@ -203,7 +217,7 @@ __device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const u
                     }
                 }
                 if (!d1) {
-                    const float q = splat_q(a, bb.x, fpx, fy1, &dx, &dy);
+                    const float q = splat_q(a, bb.x, fx1, fy, &dx, &dy);
                     if (q <= 0.f) {
                         const float alpha = fminf(kAlphaMax, splat_alpha(q, bb.y));
                         if (alpha >= kAlphaMin) {
@@ -229,16 +243,27 @@ __device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const u
                                    true, bx0, bx1, by0, by1);
         for (int e = 0; e < cnt; ++e) {
             const int p = WSw.pos[e];
-            float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            bool contrib = false;
             const float4 a = WSw.a[e];
             const float4 bb = WSw.b[e];
-            if (p < p0.last || p < p1.last) {
-                const float cb = WSw.c[e];
-                if (p < p0.last) contrib |= bwd_step(p0, a, bb, cb, fpx, fy0, acc);
-                if (p < p1.last) contrib |= bwd_step(p1, a, bb, cb, fpx, fy1, acc);
+            float dx0 = 0.f, dy0 = 0.f, ag0 = 0.f, dx1 = 0.f, dy1 = 0.f, ag1 = 0.f;
+            const bool c0 = p < p0.last && alpha_test(a, bb, fx0, fy, &dx0, &dy0, &ag0);
+            const bool c1 = p < p1.last && alpha_test(a, bb, fx1, fy, &dx1, &dy1, &ag1);
+            const bool contrib = c0 || c1;
+            if (!__any_sync(0xffffffffu, contrib)) continue;
+            float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            const float cb = WSw.c[e];
+            {   // pixel 0 where it composites the splat, else pixel 1
+                const bool u1 = !c0;
+                float T = u1 ? p1.T : p0.T, S = u1 ? p1.S : p0.S;
+                if (contrib) {
+                    bwd_composite(T, S, u1 ? p1.g0 : p0.g0, u1 ? p1.g1 : p0.g1, u1 ? p1.g2 : p0.g2, bb, cb,
+                                  u1 ? dx1 : dx0, u1 ? dy1 : dy0, u1 ? ag1 : ag0, acc);
+                    if (u1) { p1.T = T; p1.S = S; } else { p0.T = T; p0.S = S; }
+                }
             }
-            if (__any_sync(0xffffffffu, contrib)) {
+            if (__any_sync(0xffffffffu, c0 && c1) && c0 && c1)   // a lane that composites it at both pixels
+                bwd_composite(p1.T, p1.S, p1.g0, p1.g1, p1.g2, bb, cb, dx1, dy1, ag1, acc);
+            {
                 const float t8 = warp_sum8(acc);
                 const float t9 = warp_sum(acc[8]);
                 const float other = __shfl_xor_sync(0xffffffffu, t8, 4);
