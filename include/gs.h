@@ -14,6 +14,7 @@
  *   gs_bin_sort    splats -> (tile, depth)-sorted splat ids + tile ranges
  *   gs_render_fwd  Eq. 1 per 16x16 tile, front to back
  *   gs_l1_loss     L1 term of Eq. 3 and its gradient
+ *   gs_photometric_loss  full Eq. 3 (L1 + SSIM terms) and its gradient
  *   gs_render_bwd  reverse of Eq. 1 and of the projection
  *   gs_decode_bwd  reverse of the decoders (Eq. 6, Eq. 2), summed over views
  *
@@ -262,6 +263,25 @@ int gs_render_fwd(const gs_splats *sp, const gs_bins *bins, const gs_view *views
  * written to d_image (same layout as image). */
 int gs_l1_loss(const float *image, const float *target, const gs_view *views, int32_t V,
                float *loss, float *d_image, void *stream);
+
+/* The full photometric objective of Eq. 3 (Sec. III-A), which the paper takes
+ * from the 3DGS work it cites: L = lambda L1 + (1 - lambda) L_SSIM with
+ * L_SSIM = 1 - SSIM.  SSIM of a view is the mean over pixels and channels of
+ * the SSIM map computed per channel with an 11x11 Gaussian window (sigma 1.5,
+ * normalised), zero padding outside the image, C1 = 0.01^2, C2 = 0.03^2 (the
+ * paper states none of these; lambda = 0.8 is the usual choice).  Both terms
+ * are per-view means summed over the views, as in gs_l1_loss.
+ * image, target: device float, [V][3][H][W] planar (the layout of
+ * gs_render_fwd's image).  lambda in [0, 1].  loss: device float[3],
+ * overwritten with (L, L1, L_SSIM).  d_image: dL/dimage, same layout,
+ * overwritten; it is the input gs_render_bwd takes.  ws: caller-owned device
+ * workspace of gs_photometric_workspace bytes, 256-byte aligned (9 floats per
+ * pixel and 6 per 16x16 tile).  Errors: GS_ERR_INVALID_ARG for null pointers,
+ * a bad view set, lambda outside [0, 1] or a small / unaligned workspace. */
+size_t gs_photometric_workspace(const gs_view *views, int32_t V);
+int gs_photometric_loss(const float *image, const float *target, const gs_view *views, int32_t V,
+                        float lambda, void *ws, size_t ws_bytes, float *loss, float *d_image,
+                        void *stream);
 
 /* Reverse of Eq. 1 and of the projection.  Per pixel, from the back: with
  * w_i = alpha_i T_i and B_i the colour composited behind splat i (plus

@@ -83,6 +83,8 @@ EXPORTS = {
     "gs_render_fwd": (C.c_int, [P(gs_splats), P(gs_bins), P(gs_view), i32, P(C.c_float), i32, vp, sz,
                                 vp, vp, vp, vp, vp, vp]),
     "gs_l1_loss": (C.c_int, [vp, vp, P(gs_view), i32, vp, vp, vp]),
+    "gs_photometric_workspace": (sz, [P(gs_view), i32]),
+    "gs_photometric_loss": (C.c_int, [vp, vp, P(gs_view), i32, C.c_float, vp, sz, vp, vp, vp]),
     "gs_render_bwd": (C.c_int, [P(gs_gauss3d), vp, P(gs_splats), P(gs_bins), P(gs_view), i32,
                                 P(C.c_float), i32, vp, sz, vp, vp, vp, P(gs_splat_grad),
                                 P(gs_gauss3d_grad), vp, vp]),

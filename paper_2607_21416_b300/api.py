@@ -271,6 +271,18 @@ def l1_loss(image, target, views: Views, loss, d_image, stream=None):
                                          _ptr(d_image), _stream(stream)))
 
 
+def photometric_workspace(views: Views):
+    return int(L.load().gs_photometric_workspace(views.ptr, views.V))
+
+
+def photometric_loss(image, target, views: Views, lam, ws, loss, d_image, stream=None):
+    """Eq. 3: loss[0:3] = (lam L1 + (1 - lam) L_SSIM, L1, L_SSIM); d_image = dL/dimage."""
+    lib = L.load()
+    L.check("gs_photometric_loss", lib.gs_photometric_loss(_ptr(image), _ptr(target), views.ptr, views.V,
+                                                           float(lam), _ptr(ws), ws.numel(), _ptr(loss),
+                                                           _ptr(d_image), _stream(stream)))
+
+
 def render_bwd(g: Gauss3D, sp: Splats, bins: Bins, views: Views, bg, d_image, sgrad, out: Gauss3DGrad,
                status, ws, chunk=0, T_final=None, last=None, stream=None):
     lib = L.load()

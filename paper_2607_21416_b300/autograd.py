@@ -6,6 +6,7 @@ and backward passes run in libgs kernels:
     g = decode(anchors..., views)            # GsDecode: a0 visibility + a1 decoding (Eq. 2, Eq. 6)
     image = render(g, views)                 # GsRender: a2 projection, a3 binning, a4 compositing (Eq. 1)
     loss = l1_loss(image, target, views)     # GsL1: Eq. 3, L1 term
+    (or photometric_loss(image, target, views, lam=0.8): all of Eq. 3)
     loss.backward()                          # a6 render backward (with the projection), a7 decode backward
 
 They run eagerly and synchronise with the host once per call to check the
@@ -169,3 +170,24 @@ class GsL1(torch.autograd.Function):
 def l1_loss(image, target, views: api.Views) -> torch.Tensor:
     """Sum over views of the per-view mean absolute error (Eq. 3, L1 term)."""
     return GsL1.apply(image, target, views)
+
+
+class GsPhotometric(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, image, target, views, lam):
+        loss = torch.zeros(3, device=image.device)
+        d_image = torch.zeros_like(image)
+        ws = api.workspace(api.photometric_workspace(views), image.device)
+        api.photometric_loss(image.detach().contiguous(), target.contiguous(), views, lam, ws, loss, d_image)
+        ctx.save_for_backward(d_image)
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, grad):
+        (d_image,) = ctx.saved_tensors
+        return d_image * grad, None, None, None
+
+
+def photometric_loss(image, target, views: api.Views, lam: float = 0.8) -> torch.Tensor:
+    """Eq. 3: lam L1 + (1 - lam)(1 - SSIM), each a per-view mean summed over views."""
+    return GsPhotometric.apply(image, target, views, float(lam))

@@ -199,6 +199,23 @@ int gs_l1_loss(const float *image, const float *target, const gs_view *views, in
     return launch_l1(image, target, vt, loss, d_image, (cudaStream_t)stream);
 }
 
+size_t gs_photometric_workspace(const gs_view *views, int32_t V)
+{
+    ViewTable vt;
+    return make_view_table(views, V, &vt) ? photometric_workspace_bytes(vt) : 0;
+}
+
+int gs_photometric_loss(const float *image, const float *target, const gs_view *views, int32_t V, float lambda,
+                        void *ws, size_t ws_bytes, float *loss, float *d_image, void *stream)
+{
+    ViewTable vt;
+    if (!image || !target || !loss || !d_image || !make_view_table(views, V, &vt)) return GS_ERR_INVALID_ARG;
+    if (!(lambda >= 0.f && lambda <= 1.f) || !ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 ||
+        ws_bytes < photometric_workspace_bytes(vt))
+        return GS_ERR_INVALID_ARG;
+    return launch_photometric(image, target, vt, lambda, ws, loss, d_image, (cudaStream_t)stream);
+}
+
 int gs_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *sp, const gs_bins *bins,
                   const gs_view *views, int32_t V, const float *bg, int32_t chunk, void *ws, size_t ws_bytes,
                   const float *d_image, const float *T_final, const int32_t *last, gs_splat_grad *sgrad,

@@ -49,6 +49,9 @@ int launch_render_fwd(const gs_splats *sp, const gs_bins *bins, const ViewTable 
                       cudaStream_t s);
 int launch_l1(const float *image, const float *target, const ViewTable &vt, float *loss, float *d_image,
               cudaStream_t s);
+size_t photometric_workspace_bytes(const ViewTable &vt);
+int launch_photometric(const float *image, const float *target, const ViewTable &vt, float lam, void *ws,
+                       float *loss, float *d_image, cudaStream_t s);
 int launch_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *sp, const gs_bins *bins,
                       const ViewTable &vt, const float bg[3], int L, void *ws, const float *d_image,
                       const float *T_final, const int32_t *last, gs_splat_grad *sgrad, gs_gauss3d_grad *out,

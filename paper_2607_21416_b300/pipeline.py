@@ -1,7 +1,8 @@
 """One mapping iteration of the rendering path, built from the libgs calls.
 
 `RenderPass` owns capacity-sized device buffers for a keyframe batch and runs
-decode -> project -> bin/sort -> render -> L1 -> render backward -> decode
+decode -> project -> bin/sort -> render -> loss (L1 term of Eq. 3, or all of
+Eq. 3 with its SSIM term) -> render backward -> decode
 backward on one CUDA stream with no host synchronisation in between, so the
 whole sequence can be captured into one CUDA graph.  Capacity overflow is
 detected on the device (status word) and handled by `ensure_capacity`, which
@@ -38,7 +39,7 @@ class RenderPass:
     def __init__(self, views: api.Views, anchors: api.Anchors | None = None, k: int = 1,
                  cap_rows: int | None = None, cap_pairs: int | None = None,
                  precision: int = L.GS_PREC_FP32, store_state: bool = True,
-                 bg=(0.0, 0.0, 0.0), device="cuda", keys=False, chunk=0):
+                 bg=(0.0, 0.0, 0.0), device="cuda", keys=False, chunk=0, loss="l1", lam=0.8):
         self.views = views
         self.anchors = anchors
         self.k = anchors.k if anchors is not None else k
@@ -48,6 +49,10 @@ class RenderPass:
         self.device = device
         self.want_keys = keys
         self.chunk = int(chunk)
+        if loss not in ("l1", "photometric"):
+            raise ValueError(f"loss must be 'l1' or 'photometric', not {loss!r}")
+        self.loss_kind = loss
+        self.lam = float(lam)
         V = views.V
         if cap_rows is None:
             cap_rows = (anchors.N * V) if anchors is not None else 1
@@ -57,7 +62,10 @@ class RenderPass:
         npix = views.total_pixels
         self.image = torch.zeros(3 * npix, device=device)
         self.d_image = torch.zeros(3 * npix, device=device)
-        self.loss = torch.zeros(1, device=device)
+        # l1: [L1]; photometric: [lam L1 + (1 - lam) L_SSIM, L1, L_SSIM]
+        self.loss = torch.zeros(1 if loss == "l1" else 3, device=device)
+        self.photo_ws = (api.workspace(api.photometric_workspace(views), device) if loss == "photometric"
+                         else None)
         self.T_final = torch.zeros(npix, device=device) if store_state else None
         self.last = torch.zeros(npix, device=device, dtype=torch.int32) if store_state else None
         self.n_eval = torch.zeros(4, device=device, dtype=torch.int64)
@@ -101,7 +109,12 @@ class RenderPass:
         return self.image
 
     def loss_l1(self, target, stream=None):
-        api.l1_loss(self.image, target, self.views, self.loss, self.d_image, stream)
+        """The configured loss of Eq. 3 (its L1 term, or all of it) and dL/dimage."""
+        if self.loss_kind == "l1":
+            api.l1_loss(self.image, target, self.views, self.loss, self.d_image, stream)
+        else:
+            api.photometric_loss(self.image, target, self.views, self.lam, self.photo_ws, self.loss,
+                                 self.d_image, stream)
         return self.loss
 
     def backward(self, d_image=None, stream=None):
@@ -118,7 +131,7 @@ class RenderPass:
         return self.ggrad
 
     def step(self, target, stream=None):
-        """forward + L1 + backward (one mapping iteration without the optimizer)."""
+        """forward + loss + backward (one mapping iteration without the optimizer)."""
         self.forward(stream=stream)
         self.loss_l1(target, stream)
         self.backward(stream=stream)
@@ -172,11 +185,12 @@ class MappingStep:
     """
 
     def __init__(self, views: api.Views, anchors: api.Anchors, precision: int = L.GS_PREC_BF16,
-                 cap_rows: int | None = None, store_state: bool = False, chunk: int = 0, device="cuda"):
+                 cap_rows: int | None = None, store_state: bool = False, chunk: int = 0, device="cuda",
+                 loss: str = "l1", lam: float = 0.8):
         self.views = views
         self.anchors = anchors
         self.rp = RenderPass(views, anchors, cap_rows=cap_rows, precision=precision, store_state=store_state,
-                             chunk=chunk, device=device)
+                             chunk=chunk, device=device, loss=loss, lam=lam)
         self.target = torch.zeros(3 * views.total_pixels, device=device)
         self.stream = torch.cuda.Stream(device=device)
         self.graph = None
@@ -217,7 +231,7 @@ class MappingStep:
                 if cams_host is not None:
                     self.views.cams.copy_(cams_host, non_blocking=True)
                 self.graph.replay()
-                self._loss_host.copy_(self.rp.loss, non_blocking=True)
+                self._loss_host.copy_(self.rp.loss[:1], non_blocking=True)
                 self._status_host.copy_(self.rp.status, non_blocking=True)
             self.stream.synchronize()
             code = int(np.int32(int(self._status_host[0]) & 0xFFFFFFFF))
