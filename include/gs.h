@@ -275,8 +275,8 @@ int gs_l1_loss(const float *image, const float *target, const gs_view *views, in
  * gs_render_fwd's image).  lambda in [0, 1].  loss: device float[3],
  * overwritten with (L, L1, L_SSIM).  d_image: dL/dimage, same layout,
  * overwritten; it is the input gs_render_bwd takes.  ws: caller-owned device
- * workspace of gs_photometric_workspace bytes, 256-byte aligned (9 floats per
- * pixel and 6 per 16x16 tile).  Errors: GS_ERR_INVALID_ARG for null pointers,
+ * workspace of gs_photometric_workspace bytes, 256-byte aligned (8 bytes per
+ * work unit of 32 columns x 64 rows of one channel).  Errors: GS_ERR_INVALID_ARG for null pointers,
  * a bad view set, lambda outside [0, 1] or a small / unaligned workspace. */
 size_t gs_photometric_workspace(const gs_view *views, int32_t V);
 int gs_photometric_loss(const float *image, const float *target, const gs_view *views, int32_t V,
