@@ -18,6 +18,7 @@
  *   - tile binning with (tile, depth) keys and a sort on (key, splat id);
  *   - front-to-back alpha compositing, Eq. 1;
  *   - the L1 photometric term of Eq. 3 and its structural (SSIM) term;
+ *   - the optimizer step (Adam) and the densification statistics;
  *   - the analytic reverse pass of all of the above (the method is
  *     "differentiable", Sec. II/III-A), derived by hand from the forward
  *     definitions and checked against central finite differences.
@@ -687,6 +688,75 @@ double gso_ssim(int V, const int *wh, const double *image, const double *target,
         base += n;
     }
     return L;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Optimizer step.  The paper minimises Eq. 3 by gradient-based refinement of
+ * the anchor features, offsets, scalings and decoder weights (Sec. III,
+ * "System Overview"; the anchor positions themselves change only at loop
+ * closures); the optimizer is the one of the 3DGS / Scaffold-GS training the
+ * paper builds on: Adam with bias correction.  In place, one tensor:
+ *   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
+ *   p = p - lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps). */
+void gso_adam(long n, double *param, const double *grad, double *m, double *v, long step, double lr, double b1,
+              double b2, double eps)
+{
+    const double c1 = 1.0 - pow(b1, (double)step), c2 = 1.0 - pow(b2, (double)step);
+    for (long i = 0; i < n; ++i) {
+        m[i] = b1 * m[i] + (1.0 - b1) * grad[i];
+        v[i] = b2 * v[i] + (1.0 - b2) * grad[i] * grad[i];
+        param[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
+    }
+}
+
+/* Densification statistics of the incremental Scaffold-GS growth and pruning
+ * the paper adopts (Sec. III, "System Overview": refinement, densification
+ * and pruning).  Accumulated over the rows (view, anchor) of one iteration:
+ *   every row:  anchor_denom[a] += 1,
+ *               opacity_accum[a] += sum over its k Gaussians of max(opacity, 0);
+ *   every rendered Gaussian (row, i) (tiles > 0):
+ *               grad_accum[a k + i] += |dL/d mean2d| (pixel units),
+ *               offset_denom[a k + i] += 1.
+ * sgrad: 9 floats per candidate, the first two dL/d mean2d. */
+void gso_densify_stats(long rows, int k, const int *row_anchor, const int *tiles, const double *opacity,
+                       const double *sgrad, double *grad_accum, int *offset_denom, double *opacity_accum,
+                       int *anchor_denom)
+{
+    for (long r = 0; r < rows; ++r) {
+        const int a = row_anchor[r];
+        double so = 0;
+        for (int i = 0; i < k; ++i) {
+            const long c = r * k + i;
+            so += opacity[c] > 0 ? opacity[c] : 0.0;
+            if (tiles[c] > 0) {
+                const double gx = sgrad[9 * c], gy = sgrad[9 * c + 1];
+                grad_accum[(long)a * k + i] += sqrt(gx * gx + gy * gy);
+                offset_denom[(long)a * k + i] += 1;
+            }
+        }
+        opacity_accum[a] += so;
+        anchor_denom[a] += 1;
+    }
+}
+
+/* Growth / pruning candidates from the statistics, with the caller's
+ * thresholds (the paper states none): an offset grows where it was rendered
+ * in at least min_count views and its mean gradient norm is >= grad_thr; an
+ * anchor is pruned where it was visible in at least min_count views and its
+ * mean opacity sum is < opacity_thr.  The means are taken in single precision
+ * (float accumulators divided by their counts), as the device computes them. */
+void gso_densify_masks(long N, int k, const float *grad_accum, const int *offset_denom, const float *opacity_accum,
+                       const int *anchor_denom, float grad_thr, float opacity_thr, int min_count,
+                       unsigned char *grow, unsigned char *prune)
+{
+    for (long j = 0; j < N * k; ++j) {
+        const int d = offset_denom[j];
+        grow[j] = (unsigned char)(d >= min_count && d > 0 && grad_accum[j] / (float)d >= grad_thr);
+    }
+    for (long a = 0; a < N; ++a) {
+        const int d = anchor_denom[a];
+        prune[a] = (unsigned char)(d >= min_count && d > 0 && opacity_accum[a] / (float)d < opacity_thr);
+    }
 }
 
 /* ------------------------------------------------------------------------ */

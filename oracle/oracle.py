@@ -51,6 +51,7 @@ _lp = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
 _u8 = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
 _u32 = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
 _u64 = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
+_f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
 
 
 class _dpn:
@@ -80,6 +81,12 @@ def _declare(L):
     L.gso_l1.argtypes = [i, _ip, _dp, _dp, _dp]
     L.gso_ssim.restype = d
     L.gso_ssim.argtypes = [i, _ip, _dp, _dp, _dpn, _dpn]
+    L.gso_adam.restype = None
+    L.gso_adam.argtypes = [l, _dp, _dp, _dp, _dp, l, d, d, d, d]
+    L.gso_densify_stats.restype = None
+    L.gso_densify_stats.argtypes = [l, i, _ip, _ip, _dp, _dp, _dp, _ip, _dp, _ip]
+    L.gso_densify_masks.restype = None
+    L.gso_densify_masks.argtypes = [l, i, _f32p, _ip, _f32p, _ip, C.c_float, C.c_float, i, _u8, _u8]
     L.gso_render_bwd.restype = i
     L.gso_render_bwd.argtypes = [i, _ip, l, _dp, _dp, _dp, _dp, _u32, _u32, _dp, _dp, _dp,
                                  _dp, _dp, _dp]
@@ -261,6 +268,38 @@ def photometric(wh, image, target, lam=0.8):
     L1, d1 = l1(wh, image, target)
     Ls, ds, _ = ssim(wh, image, target)
     return lam * L1 + (1 - lam) * Ls, lam * d1 + (1 - lam) * ds, L1, Ls
+
+
+def adam(param, grad, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-15):
+    """One Adam step with bias correction (t = step >= 1); returns new (param, m, v)."""
+    p, m, v = _f64(param).copy(), _f64(m).copy(), _f64(v).copy()
+    lib().gso_adam(p.size, p.reshape(-1), _f64(grad).reshape(-1), m.reshape(-1), v.reshape(-1), int(step),
+                   float(lr), float(b1), float(b2), float(eps))
+    return p, m, v
+
+
+def densify_stats(row_anchor, tiles, opacity, sgrad, N, k, accum=None):
+    """Accumulates one iteration's densification statistics into `accum` =
+    (grad_accum [N k], offset_denom [N k], opacity_accum [N], anchor_denom [N])."""
+    if accum is None:
+        accum = (np.zeros(N * k), np.zeros(N * k, np.int32), np.zeros(N), np.zeros(N, np.int32))
+    ga, od, oa, ad = (np.ascontiguousarray(a) for a in accum)
+    ra = _i32(row_anchor)
+    lib().gso_densify_stats(ra.size, int(k), ra, _i32(tiles), _f64(opacity).reshape(-1),
+                            _f64(sgrad).reshape(-1), ga, od, oa, ad)
+    return ga, od, oa, ad
+
+
+def densify_masks(grad_accum, offset_denom, opacity_accum, anchor_denom, k, grad_thr, opacity_thr, min_count):
+    """Growth mask [N k] and pruning mask [N] (uint8) from float32 statistics."""
+    ga = np.ascontiguousarray(grad_accum, np.float32)
+    oa = np.ascontiguousarray(opacity_accum, np.float32)
+    N = oa.size
+    grow = np.zeros(N * k, np.uint8)
+    prune = np.zeros(N, np.uint8)
+    lib().gso_densify_masks(N, int(k), ga, _i32(offset_denom), oa, _i32(anchor_denom), float(grad_thr),
+                            float(opacity_thr), int(min_count), grow, prune)
+    return grow, prune
 
 
 def render_bwd(wh, mean2d, conic, opacity, colour, ranges, vals, dimage, bg=(0.0, 0.0, 0.0)):
