@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     p.add_argument("--no-photometric", action="store_true",
                    help="skip timing the full objective of Eq. 3 (SSIM term) on the batch")
+    p.add_argument("--no-optim", action="store_true",
+                   help="skip timing the optimizer step and the densification statistics")
     p.add_argument("--anchors", type=int, default=200000)
     p.add_argument("--views", type=int, default=8)
     p.add_argument("--chunk", type=int, default=0,
@@ -267,6 +269,43 @@ def run_ours(args, rank, world, dist):
                               "work_per_launch": f"{alg} B (36 B per pixel: image, target, gradient)"}}
         del pws, pd
 
+    # ---- after the reverse pass: Adam over the optimised anchor tensors and the decoder weights
+    # (one launch), and the densification statistics of the iteration, each timed on its own
+    optim = None
+    if not args.no_optim:
+        import dataclasses
+        work = dataclasses.replace(anchors, feat=anchors.feat.clone(), offsets=anchors.offsets.clone(),
+                                   log_scaling=anchors.log_scaling.clone(), mlp=anchors.mlp.clone())
+        opt = pipeline.Optimizer(work, rp.agrad)   # on copies: the plain-path comparison below reads `anchors`
+        stats = pipeline.DensifyStats(anchors)
+        n_par = sum(int(g[0].numel()) for g in opt.groups)
+        oe0, oe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+        def timed(fn):
+            ts = []
+            for it in range(3 + 20):
+                flush.zero_()
+                oe0.record()
+                fn()
+                oe1.record()
+                torch.cuda.synchronize()
+                if it >= 3:
+                    ts.append(oe0.elapsed_time(oe1))
+            return statistics.mean(ts)
+
+        adam_ms = timed(opt.step)
+        stats_ms = timed(lambda: stats.accumulate(rp))
+        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6400.0) \
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6400.0
+        gbs = 28 * n_par / (adam_ms * 1e-3) / 1e9
+        optim = {"adam_ms": adam_ms, "parameters": n_par, "densify_stats_ms": stats_ms,
+                 "roofline": {"kernel": "adam_kernel", "bound": "hbm", "achieved": gbs, "peak": hbm,
+                              "unit": "GB/s", "frac": gbs / hbm, "traffic": None,
+                              "peak_of": "measured" if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json"))
+                              else "fallback",
+                              "work_per_launch": f"{28 * n_par} B (28 B per parameter)"}}
+        del opt, stats, work
+
     # ---- plain FP32 path: views one at a time, state stored, eager launches
     plain = None
     if not args.no_plain:
@@ -318,6 +357,7 @@ def run_ours(args, rank, world, dist):
     return dict(value=mpix, ms_per_step=ms_per_step, stages=stages, clocks=clk, e2e_ms=e2e_ms,
                 e2e_mpix=e2e_mpix, plain=plain, roofline=roof, n_rows=n_rows, n_pairs=n_pairs,
                 counts=counts, launches=launches_per_step, npix=npix, peak_hbm_gb=peak_hbm_gb, photo=photo,
+                optim=optim,
                 h2d=ms.h2d_bytes + int(cams_host.numel() * 4), d2h=ms.d2h_bytes)
 
 
@@ -542,7 +582,7 @@ def main():
                 "stages_ms": r["stages"], "plain_path": r["plain"], "peak_hbm_gb": r["peak_hbm_gb"],
                 "speedup_vs_plain": (r["value"] / r["plain"]["value"]) if r["plain"] else None,
                 "counts": dict(rows=r["n_rows"], pairs=r["n_pairs"], pixels=r["npix"], **r["counts"]),
-                "photometric_loss": r["photo"]}
+                "photometric_loss": r["photo"], "optimizer": r["optim"]}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -17,6 +17,8 @@
  *   gs_photometric_loss  full Eq. 3 (L1 + SSIM terms) and its gradient
  *   gs_render_bwd  reverse of Eq. 1 and of the projection
  *   gs_decode_bwd  reverse of the decoders (Eq. 6, Eq. 2), summed over views
+ *   gs_adam_step, gs_densify_stats, gs_densify_masks  optimizer step and
+ *                  growth / pruning statistics after the reverse pass
  *
  * Conventions shared by every call
  * --------------------------------
@@ -282,6 +284,59 @@ size_t gs_photometric_workspace(const gs_view *views, int32_t V);
 int gs_photometric_loss(const float *image, const float *target, const gs_view *views, int32_t V,
                         float lambda, void *ws, size_t ws_bytes, float *loss, float *d_image,
                         void *stream);
+
+/* ---- After the reverse pass: optimizer step and densification statistics.
+ * The paper refines, densifies and prunes the anchor map to minimise Eq. 3
+ * (Sec. III, "System Overview") with the training of the incremental
+ * Scaffold-GS it adopts; it states neither the optimizer nor its settings.
+ *
+ * gs_adam_step: one Adam step with bias correction (t = step >= 1) over up
+ * to GS_ADAM_MAX_GROUPS float tensors in one launch, in place:
+ *   m = b1 m + (1 - b1) g;  v = b2 v + (1 - b2) g^2;
+ *   p -= lr / (1 - b1^t) * m / (sqrt(v) / sqrt(1 - b2^t) + eps).
+ * groups: HOST array of n_groups descriptors; param / m / v are device
+ * arrays of n floats updated in place (m, v start at zero), grad is read.
+ * beta1, beta2, eps are doubles so that 1 - beta is formed without the
+ * cancellation a single-precision 0.999 would bring (it is off by 1.3e-5).
+ * Anchor positions are not in the paper's optimised set: they change only at
+ * loop closures (ibid.), so callers leave them out.  Errors:
+ * GS_ERR_INVALID_ARG for n_groups outside 1..GS_ADAM_MAX_GROUPS, step < 1, a
+ * null pointer with n > 0, n < 0, or b1, b2 outside [0, 1), eps < 0. */
+#define GS_ADAM_MAX_GROUPS 16
+typedef struct gs_adam_group {
+    float *param;
+    const float *grad;
+    float *m;
+    float *v;
+    int64_t n;
+    float lr;
+} gs_adam_group;
+int gs_adam_step(const gs_adam_group *groups, int32_t n_groups, int64_t step, double beta1, double beta2,
+                 double eps, void *stream);
+
+/* gs_densify_stats: adds one iteration's statistics of the Scaffold-GS
+ * growth and pruning rules into caller-owned accumulators (zero them at the
+ * start of an interval):
+ *   every decoded row (view, anchor a):  anchor_denom[a] += 1,
+ *       opacity_accum[a] += sum over its k Gaussians of max(opacity, 0);
+ *   every rendered Gaussian (row, i), tiles[row k + i] > 0:
+ *       grad_accum[a k + i] += |dL/d mean2d| (pixel units, the first two
+ *       values of its gs_render_bwd splat gradient), offset_denom[a k + i] += 1.
+ * g: the decoded rows (row_anchor, view_start, opacity, k, cap_rows); V its
+ * views; tiles: gs_splats.tiles; sgrad: the splat gradients [C][9] of
+ * gs_render_bwd.  Accumulators: device float [N k], int32 [N k], float [N],
+ * int32 [N].  An anchor index outside [0, N) is reported through status.
+ *
+ * gs_densify_masks: growth candidates grow[a k + i] = (offset_denom >=
+ * min_count and grad_accum / offset_denom >= grad_thr) and pruning candidates
+ * prune[a] = (anchor_denom >= min_count and opacity_accum / anchor_denom <
+ * opacity_thr), the means in single precision (device uint8 outputs). */
+int gs_densify_stats(const gs_gauss3d *g, int32_t V, const int32_t *tiles, const float *sgrad, int32_t N,
+                     float *grad_accum, int32_t *offset_denom, float *opacity_accum, int32_t *anchor_denom,
+                     gs_status *status, void *stream);
+int gs_densify_masks(int64_t N, int32_t k, const float *grad_accum, const int32_t *offset_denom,
+                     const float *opacity_accum, const int32_t *anchor_denom, float grad_thr,
+                     float opacity_thr, int32_t min_count, uint8_t *grow, uint8_t *prune, void *stream);
 
 /* Reverse of Eq. 1 and of the projection.  Per pixel, from the back: with
  * w_i = alpha_i T_i and B_i the colour composited behind splat i (plus

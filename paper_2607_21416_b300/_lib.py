@@ -63,6 +63,12 @@ class gs_anchor_grad(C.Structure):
     _fields_ = [("dxyz", vp), ("dfeat", vp), ("dlog_scaling", vp), ("doffsets", vp), ("dmlp", vp)]
 
 
+class gs_adam_group(C.Structure):
+    _fields_ = [("param", vp), ("grad", vp), ("m", vp), ("v", vp), ("n", i64), ("lr", C.c_float)]
+
+
+GS_ADAM_MAX_GROUPS = 16
+
 P = C.POINTER
 
 EXPORTS = {
@@ -84,6 +90,9 @@ EXPORTS = {
                                 vp, vp, vp, vp, vp, vp]),
     "gs_l1_loss": (C.c_int, [vp, vp, P(gs_view), i32, vp, vp, vp]),
     "gs_photometric_workspace": (sz, [P(gs_view), i32]),
+    "gs_adam_step": (C.c_int, [P(gs_adam_group), i32, i64, C.c_double, C.c_double, C.c_double, vp]),
+    "gs_densify_stats": (C.c_int, [P(gs_gauss3d), i32, vp, vp, i32, vp, vp, vp, vp, vp, vp]),
+    "gs_densify_masks": (C.c_int, [i64, i32, vp, vp, vp, vp, C.c_float, C.c_float, i32, vp, vp, vp]),
     "gs_photometric_loss": (C.c_int, [vp, vp, P(gs_view), i32, C.c_float, vp, sz, vp, vp, vp]),
     "gs_render_bwd": (C.c_int, [P(gs_gauss3d), vp, P(gs_splats), P(gs_bins), P(gs_view), i32,
                                 P(C.c_float), i32, vp, sz, vp, vp, vp, P(gs_splat_grad),

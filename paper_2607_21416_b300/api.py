@@ -283,6 +283,36 @@ def photometric_loss(image, target, views: Views, lam, ws, loss, d_image, stream
                                                            _ptr(d_image), _stream(stream)))
 
 
+def adam_step(groups, step, beta1=0.9, beta2=0.999, eps=1e-15, stream=None):
+    """One Adam step over `groups` = [(param, grad, m, v, lr), ...] (contiguous
+    float32 device tensors, updated in place), one launch."""
+    lib = L.load()
+    arr = (L.gs_adam_group * len(groups))(*[
+        L.gs_adam_group(_ptr(p), _ptr(g), _ptr(m), _ptr(v), int(p.numel()), float(lr))
+        for p, g, m, v, lr in groups])
+    L.check("gs_adam_step", lib.gs_adam_step(arr, len(groups), int(step), float(beta1), float(beta2),
+                                             float(eps), _stream(stream)))
+
+
+def densify_stats(g: Gauss3D, views: Views, sp: Splats, sgrad, N, grad_accum, offset_denom, opacity_accum,
+                  anchor_denom, status, stream=None):
+    lib = L.load()
+    gs_ = g.struct()
+    L.check("gs_densify_stats", lib.gs_densify_stats(C.byref(gs_), views.V, _ptr(sp.tiles), _ptr(sgrad), int(N),
+                                                     _ptr(grad_accum), _ptr(offset_denom), _ptr(opacity_accum),
+                                                     _ptr(anchor_denom), _ptr(status), _stream(stream)))
+
+
+def densify_masks(k, grad_accum, offset_denom, opacity_accum, anchor_denom, grad_thr, opacity_thr, min_count,
+                  grow, prune, stream=None):
+    lib = L.load()
+    N = int(opacity_accum.numel())
+    L.check("gs_densify_masks", lib.gs_densify_masks(N, int(k), _ptr(grad_accum), _ptr(offset_denom),
+                                                     _ptr(opacity_accum), _ptr(anchor_denom), float(grad_thr),
+                                                     float(opacity_thr), int(min_count), _ptr(grow), _ptr(prune),
+                                                     _stream(stream)))
+
+
 def render_bwd(g: Gauss3D, sp: Splats, bins: Bins, views: Views, bg, d_image, sgrad, out: Gauss3DGrad,
                status, ws, chunk=0, T_final=None, last=None, stream=None):
     lib = L.load()

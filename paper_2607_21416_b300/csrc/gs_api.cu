@@ -216,6 +216,41 @@ int gs_photometric_loss(const float *image, const float *target, const gs_view *
     return launch_photometric(image, target, vt, lambda, ws, loss, d_image, (cudaStream_t)stream);
 }
 
+int gs_adam_step(const gs_adam_group *groups, int32_t n_groups, int64_t step, double beta1, double beta2, double eps,
+                 void *stream)
+{
+    if (!groups || n_groups < 1 || n_groups > GS_ADAM_MAX_GROUPS || step < 1) return GS_ERR_INVALID_ARG;
+    if (!(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(eps >= 0.0)) return GS_ERR_INVALID_ARG;
+    for (int i = 0; i < n_groups; ++i) {
+        const gs_adam_group &g = groups[i];
+        if (g.n < 0 || (g.n > 0 && (!g.param || !g.grad || !g.m || !g.v))) return GS_ERR_INVALID_ARG;
+    }
+    return launch_adam(groups, n_groups, step, beta1, beta2, eps, (cudaStream_t)stream);
+}
+
+int gs_densify_stats(const gs_gauss3d *g, int32_t V, const int32_t *tiles, const float *sgrad, int32_t N,
+                     float *grad_accum, int32_t *offset_denom, float *opacity_accum, int32_t *anchor_denom,
+                     gs_status *status, void *stream)
+{
+    if (!g || !g->row_anchor || !g->view_start || !g->opacity || g->k < 1 || g->cap_rows < 0 || V < 1 ||
+        V > GS_MAX_VIEWS || !tiles || !sgrad || N < 0 || !grad_accum || !offset_denom || !opacity_accum ||
+        !anchor_denom || !status)
+        return GS_ERR_INVALID_ARG;
+    return launch_densify_stats(g, V, tiles, sgrad, N, grad_accum, offset_denom, opacity_accum, anchor_denom, status,
+                                (cudaStream_t)stream);
+}
+
+int gs_densify_masks(int64_t N, int32_t k, const float *grad_accum, const int32_t *offset_denom,
+                     const float *opacity_accum, const int32_t *anchor_denom, float grad_thr, float opacity_thr,
+                     int32_t min_count, uint8_t *grow, uint8_t *prune, void *stream)
+{
+    if (N < 0 || k < 1 || !grad_accum || !offset_denom || !opacity_accum || !anchor_denom || !grow || !prune)
+        return GS_ERR_INVALID_ARG;
+    if (N == 0) return GS_OK;
+    return launch_densify_masks(N, k, grad_accum, offset_denom, opacity_accum, anchor_denom, grad_thr, opacity_thr,
+                                min_count, grow, prune, (cudaStream_t)stream);
+}
+
 int gs_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *sp, const gs_bins *bins,
                   const gs_view *views, int32_t V, const float *bg, int32_t chunk, void *ws, size_t ws_bytes,
                   const float *d_image, const float *T_final, const int32_t *last, gs_splat_grad *sgrad,

@@ -50,6 +50,13 @@ int launch_render_fwd(const gs_splats *sp, const gs_bins *bins, const ViewTable 
 int launch_l1(const float *image, const float *target, const ViewTable &vt, float *loss, float *d_image,
               cudaStream_t s);
 size_t photometric_workspace_bytes(const ViewTable &vt);
+int launch_adam(const gs_adam_group *groups, int ng, long long step, double b1, double b2, double eps, cudaStream_t s);
+int launch_densify_stats(const gs_gauss3d *g, int V, const int32_t *tiles, const float *sgrad, int N,
+                         float *grad_accum, int32_t *offset_denom, float *opacity_accum, int32_t *anchor_denom,
+                         gs_status *st, cudaStream_t s);
+int launch_densify_masks(long long N, int k, const float *grad_accum, const int32_t *offset_denom,
+                         const float *opacity_accum, const int32_t *anchor_denom, float grad_thr, float opacity_thr,
+                         int min_count, uint8_t *grow, uint8_t *prune, cudaStream_t s);
 int launch_photometric(const float *image, const float *target, const ViewTable &vt, float lam, void *ws,
                        float *loss, float *d_image, cudaStream_t s);
 int launch_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *sp, const gs_bins *bins,

@@ -245,3 +245,60 @@ class MappingStep:
     @property
     def d2h_bytes(self):
         return 4 + 16
+
+
+class Optimizer:
+    """Adam over the anchor parameters the paper optimises -- features,
+    offsets, log-scalings and the packed decoder weights -- in one launch per
+    step (`gs_adam_step`).  Anchor positions are left out: the paper moves
+    them only at loop closures.  The learning rates default to the
+    Scaffold-GS values (the paper gives none); `lr` overrides them by name.
+    Run it after the iteration's reverse pass (outside a captured graph: the
+    bias correction changes every step)."""
+
+    DEFAULT_LR = {"feat": 0.0075, "offsets": 0.01, "log_scaling": 0.007, "mlp": 0.004}
+
+    def __init__(self, anchors: api.Anchors, grads: api.AnchorGrad, lr=None, betas=(0.9, 0.999), eps=1e-15):
+        rates = dict(self.DEFAULT_LR)
+        rates.update(lr or {})
+        self.betas, self.eps, self.t = betas, float(eps), 0
+        self.names = list(rates)
+        self.groups = []
+        for n in self.names:
+            p, g = getattr(anchors, n), getattr(grads, "d" + n)
+            self.groups.append([p, g, torch.zeros_like(p), torch.zeros_like(p), float(rates[n])])
+
+    def set_lr(self, name, lr):
+        self.groups[self.names.index(name)][4] = float(lr)
+
+    def step(self, stream=None):
+        self.t += 1
+        api.adam_step([tuple(g) for g in self.groups], self.t, self.betas[0], self.betas[1], self.eps, stream)
+
+
+class DensifyStats:
+    """Accumulators of the growth / pruning statistics (`gs_densify_stats`)
+    over a densification interval, and the candidate masks from them."""
+
+    def __init__(self, anchors: api.Anchors, device="cuda"):
+        self.N, self.k = anchors.N, anchors.k
+        self.grad_accum = torch.zeros(self.N * self.k, device=device)
+        self.offset_denom = torch.zeros(self.N * self.k, device=device, dtype=torch.int32)
+        self.opacity_accum = torch.zeros(self.N, device=device)
+        self.anchor_denom = torch.zeros(self.N, device=device, dtype=torch.int32)
+
+    def reset(self):
+        for t in (self.grad_accum, self.offset_denom, self.opacity_accum, self.anchor_denom):
+            t.zero_()
+
+    def accumulate(self, rp: RenderPass, stream=None):
+        """Adds the statistics of the iteration `rp` has just run (after its backward)."""
+        api.densify_stats(rp.g, rp.views, rp.splats, rp.sgrad, self.N, self.grad_accum, self.offset_denom,
+                          self.opacity_accum, self.anchor_denom, rp.status, stream)
+
+    def masks(self, grad_thr, opacity_thr, min_count=1, stream=None):
+        grow = torch.zeros(self.N * self.k, device=self.grad_accum.device, dtype=torch.uint8)
+        prune = torch.zeros(self.N, device=self.grad_accum.device, dtype=torch.uint8)
+        api.densify_masks(self.k, self.grad_accum, self.offset_denom, self.opacity_accum, self.anchor_denom,
+                          grad_thr, opacity_thr, min_count, grow, prune, stream)
+        return grow, prune
