@@ -19,6 +19,8 @@
  *   - front-to-back alpha compositing, Eq. 1;
  *   - the L1 photometric term of Eq. 3 and its structural (SSIM) term;
  *   - the optimizer step (Adam) and the densification statistics;
+ *   - map maintenance: voxelisation (Eq. 4) and the loop-closure
+ *     deformation (Eq. 7);
  *   - the analytic reverse pass of all of the above (the method is
  *     "differentiable", Sec. II/III-A), derived by hand from the forward
  *     definitions and checked against central finite differences.
@@ -34,6 +36,7 @@
  * Camera record: double[16] = fx, fy, cx, cy, R[9] (row-major world->camera),
  * t[3]; resolution int[2] = width, height.
  */
+#include <limits.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -757,6 +760,118 @@ void gso_densify_masks(long N, int k, const float *grad_accum, const int *offset
         const int d = anchor_denom[a];
         prune[a] = (unsigned char)(d >= min_count && d > 0 && opacity_accum[a] / (float)d < opacity_thr);
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Map maintenance.
+ *
+ * Voxelisation, Eq. 4: V = unique(round(P / eps)) * eps.  Reading: round to
+ * the nearest integer with ties to even, the quotient and the rounding taken
+ * in single precision (p / eps as one correctly rounded float division, the
+ * precision the device decides in); voxel index (i, j, l) is packed into the
+ * 64-bit key ((i + 2^20) << 42) | ((j + 2^20) << 21) | (l + 2^20), so indices
+ * must satisfy |index| < 2^20.  The output is the keys in ascending order that
+ * are not in `existing` (sorted ascending; the anchors already in the map),
+ * with their centres index * eps (one float multiply).  Returns the count,
+ * -(count) when it exceeds cap (nothing past cap written), or LONG_MIN when an
+ * index is out of range. */
+static int cmp_u64(const void *a, const void *b)
+{
+    const uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+long gso_voxelize(long P, const float *pts, float eps, const uint64_t *existing, long n_existing, uint64_t *keys_out,
+                  float *centers_out, long cap)
+{
+    const float lim = 1048576.0f;   /* 2^20 */
+    uint64_t *k = (uint64_t *)malloc(sizeof(uint64_t) * (P > 0 ? P : 1));
+    for (long i = 0; i < P; ++i) {
+        uint64_t key = 0;
+        for (int a = 0; a < 3; ++a) {
+            const float q = pts[3 * i + a] / eps;
+            const float r = rintf(q);
+            if (!(r > -lim && r < lim)) { free(k); return LONG_MIN; }
+            key = (key << 21) | (uint64_t)((long)r + 1048576L);
+        }
+        k[i] = key;
+    }
+    qsort(k, (size_t)P, sizeof(uint64_t), cmp_u64);
+    long n = 0;
+    for (long i = 0; i < P; ++i) {
+        if (i > 0 && k[i] == k[i - 1]) continue;
+        if (n_existing > 0 && bsearch(&k[i], existing, (size_t)n_existing, sizeof(uint64_t), cmp_u64)) continue;
+        if (n < cap) {
+            keys_out[n] = k[i];
+            for (int a = 0; a < 3; ++a) {
+                const long idx = (long)((k[i] >> (42 - 21 * a)) & 0x1FFFFF) - 1048576L;
+                centers_out[3 * n + a] = (float)idx * eps;
+            }
+        }
+        ++n;
+    }
+    free(k);
+    return n <= cap ? n : -n;
+}
+
+/* Loop-closure deformation, Eq. 7.  For keyframe i with old and new
+ * world-to-camera poses T_old,i and T_new,i, Delta T_i = T_new,i^-1 T_old,i
+ * maps an anchor x to R_new^T (R_old x + t_old - t_new).  It applies to the
+ * anchors inside keyframe i's local view frustum; readings: that frustum is
+ * the visibility rule of the decoder (in front of the near plane 0.2, inside
+ * the image grown by 15 % per side, under the old pose) cut at depth z_far,
+ * and an anchor inside several corrected frusta takes the transform of the
+ * nearest keyframe (smallest distance to the old camera centre, lowest index
+ * on ties).  Anchors outside every frustum keep their position.  assigned[a]
+ * = the keyframe used, or -1; flag[a] marks decisions within `band`
+ * (relative) of a frustum edge or of a tie, which single precision may take
+ * differently. */
+void gso_loop_closure(int N, const double *xyz, int K, const double *cams_old, const double *cams_new,
+                      const int *wh, double z_far, double band, double *xyz_out, int *assigned, unsigned char *flag)
+{
+    ocam *co = (ocam *)malloc(sizeof(ocam) * (K > 0 ? K : 1));
+    ocam *cn = (ocam *)malloc(sizeof(ocam) * (K > 0 ? K : 1));
+    load_cams(K, cams_old, wh, co);
+    load_cams(K, cams_new, wh, cn);
+    for (int a = 0; a < N; ++a) {
+        const double *x = xyz + 3 * a;
+        int best = -1, fl = 0;
+        double bd = 0, second = -1;
+        for (int i = 0; i < K; ++i) {
+            const ocam *c = co + i;
+            double p[3];
+            to_cam(c, x, p);
+            fl |= near_rel(p[2], O_NEAR, band) || near_rel(p[2], z_far, band);
+            if (!(p[2] > O_NEAR && p[2] <= z_far)) continue;
+            const double lox = -O_MARGIN * c->W, hix = (1.0 + O_MARGIN) * c->W;
+            const double loy = -O_MARGIN * c->H, hiy = (1.0 + O_MARGIN) * c->H;
+            const double u = c->fx * p[0] / p[2] + c->cx, w = c->fy * p[1] / p[2] + c->cy;
+            fl |= fabs(u - lox) <= band * (fabs(lox) + 1) || fabs(u - hix) <= band * hix ||
+                  fabs(w - loy) <= band * (fabs(loy) + 1) || fabs(w - hiy) <= band * hiy;
+            if (!(u >= lox && u < hix && w >= loy && w < hiy)) continue;
+            const double d = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
+            if (best < 0 || d < bd) {
+                second = best < 0 ? -1 : bd;
+                best = i;
+                bd = d;
+            } else if (second < 0 || d < second) {
+                second = d;
+            }
+        }
+        if (best >= 0 && second >= 0 && fabs(second - bd) <= band * bd) fl = 1;
+        double y[3] = {x[0], x[1], x[2]};
+        if (best >= 0) {
+            const ocam *o = co + best, *n = cn + best;
+            double p[3];
+            to_cam(o, x, p);
+            const double q[3] = {p[0] - n->t[0], p[1] - n->t[1], p[2] - n->t[2]};
+            for (int r = 0; r < 3; ++r) y[r] = n->R[r] * q[0] + n->R[3 + r] * q[1] + n->R[6 + r] * q[2];
+        }
+        xyz_out[3 * a] = y[0]; xyz_out[3 * a + 1] = y[1]; xyz_out[3 * a + 2] = y[2];
+        assigned[a] = best;
+        if (flag) flag[a] = (unsigned char)fl;
+    }
+    free(co); free(cn);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -54,6 +54,13 @@ _u64 = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
 _f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
 
 
+class _u64n:
+    """uint64 array pointer that also accepts None (NULL)."""
+    @classmethod
+    def from_param(cls, a):
+        return None if a is None else _u64.from_param(a)
+
+
 class _dpn:
     """float64 array pointer that also accepts None (NULL)."""
     @classmethod
@@ -85,6 +92,10 @@ def _declare(L):
     L.gso_adam.argtypes = [l, _dp, _dp, _dp, _dp, l, d, d, d, d]
     L.gso_densify_stats.restype = None
     L.gso_densify_stats.argtypes = [l, i, _ip, _ip, _dp, _dp, _dp, _ip, _dp, _ip]
+    L.gso_voxelize.restype = l
+    L.gso_voxelize.argtypes = [l, _f32p, C.c_float, _u64n, l, _u64, _f32p, l]
+    L.gso_loop_closure.restype = None
+    L.gso_loop_closure.argtypes = [i, _dp, i, _dp, _dp, _ip, d, d, _dp, _ip, _u8]
     L.gso_densify_masks.restype = None
     L.gso_densify_masks.argtypes = [l, i, _f32p, _ip, _f32p, _ip, C.c_float, C.c_float, i, _u8, _u8]
     L.gso_render_bwd.restype = i
@@ -300,6 +311,43 @@ def densify_masks(grad_accum, offset_denom, opacity_accum, anchor_denom, k, grad
     lib().gso_densify_masks(N, int(k), ga, _i32(offset_denom), oa, _i32(anchor_denom), float(grad_thr),
                             float(opacity_thr), int(min_count), grow, prune)
     return grow, prune
+
+
+KEY_BIAS = 1 << 20
+
+
+def voxelize(points, eps, existing=None, cap=None):
+    """Eq. 4: the new voxel keys (ascending uint64) of float32 points at voxel
+    size eps, minus `existing` (sorted uint64), and their float32 centres.
+    Raises ValueError for a voxel index outside (-2^20, 2^20)."""
+    pts = np.ascontiguousarray(points, np.float32).reshape(-1, 3)
+    P = pts.shape[0]
+    cap = P if cap is None else int(cap)
+    keys = np.zeros(max(cap, 1), np.uint64)
+    centres = np.zeros((max(cap, 1), 3), np.float32)
+    ex = None if existing is None or len(existing) == 0 else np.ascontiguousarray(existing, np.uint64)
+    n = lib().gso_voxelize(P, pts.reshape(-1), np.float32(eps), ex, 0 if ex is None else ex.size, keys,
+                           centres.reshape(-1), cap)
+    if n == np.iinfo(np.int64).min:
+        raise ValueError("voxel index out of range")
+    if n < 0:
+        return None, None, -n
+    return keys[:n], centres[:n], n
+
+
+def loop_closure(xyz, cams_old, cams_new, wh, z_far, band=BAND):
+    """Eq. 7 applied with the nearest-keyframe rule: new anchor positions,
+    the keyframe used per anchor (-1: none) and near-threshold flags."""
+    x = _f64(xyz).reshape(-1, 3)
+    N = x.shape[0]
+    wh = _i32(wh).reshape(-1, 2)
+    K = wh.shape[0]
+    out = np.zeros_like(x)
+    assigned = np.zeros(N, np.int32)
+    flag = np.zeros(N, np.uint8)
+    lib().gso_loop_closure(N, x.reshape(-1), K, _f64(cams_old).reshape(-1), _f64(cams_new).reshape(-1), wh,
+                           float(z_far), float(band), out.reshape(-1), assigned, flag)
+    return out, assigned, flag
 
 
 def render_bwd(wh, mean2d, conic, opacity, colour, ranges, vals, dimage, bg=(0.0, 0.0, 0.0)):
