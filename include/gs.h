@@ -19,6 +19,7 @@
  *   gs_decode_bwd  reverse of the decoders (Eq. 6, Eq. 2), summed over views
  *   gs_adam_step, gs_densify_stats, gs_densify_masks  optimizer step and
  *                  growth / pruning statistics after the reverse pass
+ *   gs_voxelize, gs_loop_closure  map maintenance (Eq. 4, Eq. 7)
  *
  * Conventions shared by every call
  * --------------------------------
@@ -337,6 +338,42 @@ int gs_densify_stats(const gs_gauss3d *g, int32_t V, const int32_t *tiles, const
 int gs_densify_masks(int64_t N, int32_t k, const float *grad_accum, const int32_t *offset_denom,
                      const float *opacity_accum, const int32_t *anchor_denom, float grad_thr,
                      float opacity_thr, int32_t min_count, uint8_t *grow, uint8_t *prune, void *stream);
+
+/* ---- Map maintenance.
+ *
+ * gs_voxelize (Eq. 4, Sec. III "System Overview": the fused point cloud is
+ * discretised onto the anchor voxel grid, keeping unique entries): the voxel
+ * index of a point is rint(p / eps) per axis (one correctly rounded single
+ * precision division, ties to even), packed into the 64-bit key
+ * ((i + 2^20) << 42) | ((j + 2^20) << 21) | (l + 2^20).  Writes, in ascending
+ * key order, the distinct keys that are not in `existing` and their centres
+ * index * eps.  points: device float [P][3], 0 <= P < 2^31; existing: device
+ * uint64 [n_existing], sorted ascending (the keys of the anchors already in
+ * the map; NULL when n_existing = 0); keys_out [cap_out] uint64 and
+ * centers_out [cap_out][3] float: device outputs; n_out: device uint32, the
+ * number written.  ws: gs_voxelize_workspace(P) bytes, 256-byte aligned.
+ * Errors in status: GS_ERR_INVALID_ARG (site 80) for an index outside
+ * (-2^20, 2^20); GS_ERR_CAPACITY with the needed count when it exceeds
+ * cap_out (nothing written, *n_out = 0). */
+size_t gs_voxelize_workspace(int64_t P);
+int gs_voxelize(const float *points, int64_t P, float eps, const uint64_t *existing, int64_t n_existing,
+                uint64_t *keys_out, float *centers_out, int64_t cap_out, uint32_t *n_out, void *ws,
+                size_t ws_bytes, gs_status *status, void *stream);
+
+/* gs_loop_closure (Eq. 7, Sec. III "Loop Closures"): for each corrected
+ * keyframe i with old and new world-to-camera poses, Delta T_i = T_new,i^-1
+ * T_old,i moves an anchor x to R_new^T (R_old x + t_old - t_new).  It applies
+ * to the anchors inside keyframe i's view frustum under its old pose -- in
+ * front of the near plane 0.2, inside the image grown by 15 % per side (the
+ * decoder's visibility rule), no deeper than z_far -- and an anchor inside
+ * several frusta takes the nearest keyframe (distance to the old camera
+ * centre; lowest index on ties; the paper leaves this open).  Other anchors
+ * keep their position.  xyz: device float [N][3], updated in place;
+ * old_cams / new_cams: device gs_camera [K]; wh: device int32 [K][2] (width,
+ * height); assigned: device int32 [N] (the keyframe used, -1 for none) or
+ * NULL.  Offsets, features and scalings are left as they are. */
+int gs_loop_closure(float *xyz, int32_t N, const gs_camera *old_cams, const gs_camera *new_cams,
+                    const int32_t *wh, int32_t K, float z_far, int32_t *assigned, void *stream);
 
 /* Reverse of Eq. 1 and of the projection.  Per pixel, from the back: with
  * w_i = alpha_i T_i and B_i the colour composited behind splat i (plus

@@ -313,6 +313,31 @@ def densify_masks(k, grad_accum, offset_denom, opacity_accum, anchor_denom, grad
                                                      _stream(stream)))
 
 
+def voxelize_workspace(P):
+    return int(L.load().gs_voxelize_workspace(int(P)))
+
+
+def voxelize(points, eps, keys_out, centers_out, n_out, ws, status, existing=None, stream=None):
+    """Eq. 4 on device points [P, 3] float32: new voxel keys (ascending, int64
+    tensor holding the uint64 keys) and centres; n_out: uint32[1] count."""
+    lib = L.load()
+    P = int(points.shape[0]) if points.dim() > 1 else int(points.numel()) // 3
+    ne = 0 if existing is None else int(existing.numel())
+    L.check("gs_voxelize", lib.gs_voxelize(_ptr(points), P, float(eps), _ptr(existing) if ne else None, ne,
+                                           _ptr(keys_out), _ptr(centers_out), int(keys_out.numel()), _ptr(n_out),
+                                           _ptr(ws), ws.numel(), _ptr(status), _stream(stream)))
+
+
+def loop_closure(xyz, old_cams, new_cams, wh, z_far, assigned=None, stream=None):
+    """Eq. 7: moves the anchors xyz [N, 3] (device, in place) by the pose
+    updates of the keyframes (old_cams / new_cams: device [K, 16] float32;
+    wh: device int32 [K, 2]); assigned: optional int32 [N] (-1: none)."""
+    lib = L.load()
+    L.check("gs_loop_closure", lib.gs_loop_closure(_ptr(xyz), int(xyz.shape[0]), _ptr(old_cams), _ptr(new_cams),
+                                                   _ptr(wh), int(old_cams.shape[0]), float(z_far),
+                                                   _ptr(assigned), _stream(stream)))
+
+
 def render_bwd(g: Gauss3D, sp: Splats, bins: Bins, views: Views, bg, d_image, sgrad, out: Gauss3DGrad,
                status, ws, chunk=0, T_final=None, last=None, stream=None):
     lib = L.load()

@@ -650,4 +650,188 @@ int launch_bin_sort(const gs_splats *sp, int k, const int32_t *view_start, long 
     return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 
+// ------------------------------------------------------------ voxelisation
+// Eq. 4: V = unique(round(P / eps)) * eps, for the map's incremental growth.
+// Each point's voxel index (i, j, l) = rint(p / eps) (one correctly rounded
+// single-precision division, ties to even) is packed into the 64-bit key
+// ((i + 2^20) << 42) | ((j + 2^20) << 21) | (l + 2^20); the keys are sorted
+// with the radix sort above (low word, then high word, stable), and the first
+// key of every run that is not among the caller's existing keys is written in
+// ascending order with its centre index * eps.
+constexpr int kVoxBias = 1 << 20;
+
+__global__ void __launch_bounds__(256) voxel_keys_kernel(const float *__restrict__ pts, uint32_t P, float eps,
+                                                         uint32_t *__restrict__ lo, uint32_t *__restrict__ hi,
+                                                         uint32_t *__restrict__ lo_sort, uint32_t *__restrict__ idx,
+                                                         uint32_t *__restrict__ count, gs_status *st)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) *count = P;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
+        unsigned long long key = 0;
+        bool ok = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float r = rintf(__fdiv_rn(__ldg(pts + 3 * (size_t)i + a), eps));
+            ok = ok && r > -(float)kVoxBias && r < (float)kVoxBias;
+            key = (key << 21) | (unsigned long long)(ok ? (int)r + kVoxBias : 0);
+        }
+        if (!ok) set_error(st, GS_ERR_INVALID_ARG, 80);
+        lo[i] = (uint32_t)key;
+        hi[i] = (uint32_t)(key >> 32);
+        lo_sort[i] = (uint32_t)key;
+        idx[i] = i;
+    }
+}
+
+__global__ void __launch_bounds__(256) gather_u32_kernel(const uint32_t *__restrict__ src,
+                                                         const uint32_t *__restrict__ idx,
+                                                         uint32_t *__restrict__ dst, const uint32_t *__restrict__ n_ptr,
+                                                         const gs_status *st)
+{
+    if (has_error(st)) return;
+    const uint32_t n = *n_ptr;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t j = idx[i];
+        dst[i] = idx_ok(st, j, n, 81) ? src[j] : 0u;
+    }
+}
+
+// Whether sorted position i starts a run whose key is not in `existing`.
+__device__ __forceinline__ bool voxel_is_new(uint32_t i, const uint32_t *__restrict__ hi,
+                                             const uint32_t *__restrict__ lo,
+                                             const unsigned long long *__restrict__ existing, long long n_ex,
+                                             unsigned long long *key)
+{
+    const unsigned long long k = ((unsigned long long)hi[i] << 32) | lo[i];
+    *key = k;
+    if (i > 0 && k == (((unsigned long long)hi[i - 1] << 32) | lo[i - 1])) return false;
+    long long a = 0, b = n_ex;   // first position with existing >= k
+    while (a < b) {
+        const long long m = (a + b) >> 1;
+        if (existing[m] < k) a = m + 1; else b = m;
+    }
+    return !(a < n_ex && existing[a] == k);
+}
+
+__global__ void __launch_bounds__(kSortThreads) voxel_count_kernel(const uint32_t *__restrict__ hi,
+                                                                   const uint32_t *__restrict__ lo,
+                                                                   const uint32_t *__restrict__ n_ptr,
+                                                                   const unsigned long long *__restrict__ existing,
+                                                                   long long n_ex, uint32_t *__restrict__ block_sums,
+                                                                   const gs_status *st)
+{
+    if (has_error(st)) return;
+    const uint32_t n = *n_ptr;
+    uint32_t t0, t1;
+    block_tiles(n, blockIdx.x, gridDim.x, &t0, &t1);
+    uint32_t c = 0;
+    unsigned long long k;
+    for (uint32_t i = t0 * kSortTile + threadIdx.x; i < min(n, t1 * kSortTile); i += kSortThreads)
+        c += voxel_is_new(i, hi, lo, existing, n_ex, &k);
+    __shared__ uint32_t s_warp[32];
+    uint32_t tot;
+    scan256(c, s_warp, &tot);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kSortThreads) voxel_write_kernel(const uint32_t *__restrict__ hi,
+                                                                   const uint32_t *__restrict__ lo,
+                                                                   const uint32_t *__restrict__ n_ptr,
+                                                                   const unsigned long long *__restrict__ existing,
+                                                                   long long n_ex,
+                                                                   const uint32_t *__restrict__ block_off, float eps,
+                                                                   unsigned long long *__restrict__ keys_out,
+                                                                   float *__restrict__ centers_out, long long cap,
+                                                                   const gs_status *st)
+{
+    if (has_error(st)) return;
+    const uint32_t n = *n_ptr;
+    uint32_t t0, t1;
+    block_tiles(n, blockIdx.x, gridDim.x, &t0, &t1);
+    __shared__ uint32_t s_warp[32];
+    uint32_t base = block_off[blockIdx.x];
+    for (uint32_t t = t0; t < t1; ++t) {
+        const uint32_t i0 = t * kSortTile + threadIdx.x * kSortItems;
+        bool nw[kSortItems];
+        unsigned long long key[kSortItems];
+        uint32_t c = 0;
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            nw[j] = i0 + j < n && voxel_is_new(i0 + j, hi, lo, existing, n_ex, &key[j]);
+            c += nw[j];
+        }
+        uint32_t tot;
+        uint32_t off = base + scan256(c, s_warp, &tot);
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            if (!nw[j]) continue;
+            if (idx_ok(st, (long long)off, cap, 82)) {
+                keys_out[off] = key[j];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const int v = (int)((key[j] >> (42 - 21 * a)) & 0x1FFFFFull) - kVoxBias;
+                    centers_out[3 * (size_t)off + a] = __fmul_rn((float)v, eps);
+                }
+            }
+            ++off;
+        }
+        base += tot;
+    }
+}
+
+struct VoxLayout {
+    size_t lo, hi, ka, kb, va, vb, hist, totals, sums, counts, total;
+    int nb;
+};
+
+static VoxLayout vox_layout(long long P)
+{
+    VoxLayout L;
+    L.nb = sort_blocks();
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes, 256); return at; };
+    const size_t n = sizeof(uint32_t) * (size_t)std::max<long long>(P, 1);
+    L.lo = take(n); L.hi = take(n); L.ka = take(n); L.kb = take(n); L.va = take(n); L.vb = take(n);
+    L.hist = take(sizeof(uint32_t) * 256 * 1024);
+    L.totals = take(sizeof(uint32_t) * 256);
+    L.sums = take(sizeof(uint32_t) * 1024);
+    L.counts = take(sizeof(uint32_t) * 4);
+    L.total = o;
+    return L;
+}
+
+size_t voxelize_workspace_bytes(long long P) { return vox_layout(P).total; }
+
+int launch_voxelize(const float *pts, long long P, float eps, const unsigned long long *existing, long long n_ex,
+                    unsigned long long *keys_out, float *centers_out, long long cap, uint32_t *n_out, void *ws,
+                    gs_status *st, cudaStream_t s)
+{
+    const VoxLayout L = vox_layout(P);
+    char *w = reinterpret_cast<char *>(ws);
+    uint32_t *lo = (uint32_t *)(w + L.lo), *hi = (uint32_t *)(w + L.hi);
+    uint32_t *ka = (uint32_t *)(w + L.ka), *kb = (uint32_t *)(w + L.kb);
+    uint32_t *va = (uint32_t *)(w + L.va), *vb = (uint32_t *)(w + L.vb);
+    uint32_t *hist = (uint32_t *)(w + L.hist), *totals = (uint32_t *)(w + L.totals);
+    uint32_t *sums = (uint32_t *)(w + L.sums), *count = (uint32_t *)(w + L.counts);
+    const int g = (int)std::max<long long>(1, std::min<long long>((P + 255) / 256, (long long)sm_count() * 8));
+    voxel_keys_kernel<<<g, 256, 0, s>>>(pts, (uint32_t)P, eps, lo, hi, ka, va, count, st);
+    count_launches(1);
+    uint32_t *k1, *v1;   // sorted by the low word
+    radix_sort(ka, va, kb, vb, count, 32, hist, totals, L.nb, st, s, &k1, &v1);
+    uint32_t *kf = (k1 == ka) ? kb : ka, *vf = (v1 == va) ? vb : va;   // the free pair
+    gather_u32_kernel<<<g, 256, 0, s>>>(hi, v1, kf, count, st);
+    count_launches(1);
+    uint32_t *k2, *v2;   // then stably by the high word (31 bits)
+    radix_sort(kf, v1, k1, vf, count, 31, hist, totals, L.nb, st, s, &k2, &v2);
+    uint32_t *lo2 = (k2 == kf) ? k1 : kf;   // the key buffer not holding the result
+    gather_u32_kernel<<<g, 256, 0, s>>>(lo, v2, lo2, count, st);
+    count_launches(1);
+    voxel_count_kernel<<<L.nb, kSortThreads, 0, s>>>(k2, lo2, count, existing, n_ex, sums, st);
+    scan_block_sums<<<1, 1024, 0, s>>>(sums, L.nb, n_out, cap, st, 8);
+    voxel_write_kernel<<<L.nb, kSortThreads, 0, s>>>(k2, lo2, count, existing, n_ex, sums, eps, keys_out, centers_out,
+                                                     cap, st);
+    count_launches(3);
+    return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
 }  // namespace gs

@@ -251,6 +251,29 @@ int gs_densify_masks(int64_t N, int32_t k, const float *grad_accum, const int32_
                                 min_count, grow, prune, (cudaStream_t)stream);
 }
 
+size_t gs_voxelize_workspace(int64_t P) { return P < 0 ? 0 : voxelize_workspace_bytes(P); }
+
+int gs_voxelize(const float *points, int64_t P, float eps, const uint64_t *existing, int64_t n_existing,
+                uint64_t *keys_out, float *centers_out, int64_t cap_out, uint32_t *n_out, void *ws, size_t ws_bytes,
+                gs_status *status, void *stream)
+{
+    if (P < 0 || P >= (1ll << 31) || (P > 0 && !points) || !(eps > 0.f) || n_existing < 0 ||
+        (n_existing > 0 && !existing) || cap_out < 0 || !keys_out || !centers_out || !n_out || !status || !ws ||
+        (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < voxelize_workspace_bytes(P))
+        return GS_ERR_INVALID_ARG;
+    return launch_voxelize(points, P, eps, reinterpret_cast<const unsigned long long *>(existing), n_existing,
+                           reinterpret_cast<unsigned long long *>(keys_out), centers_out, cap_out, n_out, ws, status,
+                           (cudaStream_t)stream);
+}
+
+int gs_loop_closure(float *xyz, int32_t N, const gs_camera *old_cams, const gs_camera *new_cams, const int32_t *wh,
+                    int32_t K, float z_far, int32_t *assigned, void *stream)
+{
+    if (N < 0 || (N > 0 && !xyz) || K < 1 || !old_cams || !new_cams || !wh || !(z_far > 0.f))
+        return GS_ERR_INVALID_ARG;
+    return launch_loop_closure(xyz, N, old_cams, new_cams, wh, K, z_far, assigned, (cudaStream_t)stream);
+}
+
 int gs_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *sp, const gs_bins *bins,
                   const gs_view *views, int32_t V, const float *bg, int32_t chunk, void *ws, size_t ws_bytes,
                   const float *d_image, const float *T_final, const int32_t *last, gs_splat_grad *sgrad,

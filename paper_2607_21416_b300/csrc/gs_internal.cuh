@@ -50,6 +50,12 @@ int launch_render_fwd(const gs_splats *sp, const gs_bins *bins, const ViewTable 
 int launch_l1(const float *image, const float *target, const ViewTable &vt, float *loss, float *d_image,
               cudaStream_t s);
 size_t photometric_workspace_bytes(const ViewTable &vt);
+size_t voxelize_workspace_bytes(long long P);
+int launch_voxelize(const float *pts, long long P, float eps, const unsigned long long *existing, long long n_ex,
+                    unsigned long long *keys_out, float *centers_out, long long cap, uint32_t *n_out, void *ws,
+                    gs_status *st, cudaStream_t s);
+int launch_loop_closure(float *xyz, int N, const gs_camera *old_cams, const gs_camera *new_cams, const int32_t *wh,
+                        int K, float z_far, int32_t *assigned, cudaStream_t s);
 int launch_adam(const gs_adam_group *groups, int ng, long long step, double b1, double b2, double eps, cudaStream_t s);
 int launch_densify_stats(const gs_gauss3d *g, int V, const int32_t *tiles, const float *sgrad, int N,
                          float *grad_accum, int32_t *offset_denom, float *opacity_accum, int32_t *anchor_denom,
