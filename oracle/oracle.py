@@ -350,6 +350,56 @@ def loop_closure(xyz, cams_old, cams_new, wh, z_far, band=BAND):
     return out, assigned, flag
 
 
+def _proj_matrix(cam):
+    """P = K [R | t] of a camera record (fx, fy, cx, cy, R, t), zero skew."""
+    c = _f64(cam).reshape(-1)
+    K = np.array([[c[0], 0, c[2]], [0, c[1], c[3]], [0, 0, 1.0]])
+    return K @ np.hstack([c[4:13].reshape(3, 3), c[13:16, None]])
+
+
+def _skew(v):
+    return np.array([[0, -v[2], v[1]], [v[2], 0, -v[0]], [-v[1], v[0], 0]])
+
+
+def fundamental(cam1, cam2):
+    """Eq. 5: F = [e2]x P2 P1^+ with e2 = P2 C1, C1 the centre of camera 1
+    (the right null space of P1, here -R1^T t1 in homogeneous form)."""
+    P1, P2 = _proj_matrix(cam1), _proj_matrix(cam2)
+    c = _f64(cam1).reshape(-1)
+    C1 = np.append(-c[4:13].reshape(3, 3).T @ c[13:16], 1.0)
+    e2 = P2 @ C1
+    return _skew(e2) @ P2 @ np.linalg.pinv(P1)
+
+
+def flow_triangulate(cam1, cam2, wh, flow, samples, tau, band=1e-9):
+    """Correspondence filtering (Eq. 5) and linear triangulation (Sec. III,
+    Flow Densification), FP64.  For each sampled pixel x = (px, py, 1) of
+    keyframe 1 and x' = x + flow: residual = |x'^T F x|, kept iff < tau.
+    Kept pairs are triangulated by linear least squares on the four DLT rows
+    (x P1[2] - P1[0], y P1[2] - P1[1], x' P2[2] - P2[0], y' P2[2] - P2[1]) with
+    the homogeneous coordinate fixed to 1.  Returns (residual [N], keep [N],
+    flag [N]: |residual - tau| within band of the terms' scale, points [M, 3]
+    of the kept samples in sample order)."""
+    W, H = int(wh[0]), int(wh[1])
+    F = fundamental(cam1, cam2)
+    q = np.asarray(samples, np.int64)
+    fl = _f64(flow).reshape(H * W, 2)[q]
+    x = np.stack([q % W, q // W, np.ones(len(q))], 1).astype(np.float64)
+    xp = x.copy()
+    xp[:, :2] += fl
+    r = np.abs(np.einsum("ni,ij,nj->n", xp, F, x))
+    scale = np.einsum("ni,ij,nj->n", np.abs(xp), np.abs(F), np.abs(x))
+    keep = r < tau
+    flag = np.abs(r - tau) <= band * (tau + scale)
+    P1, P2 = _proj_matrix(cam1), _proj_matrix(cam2)
+    pts = []
+    for i in np.nonzero(keep)[0]:
+        A = np.stack([x[i, 0] * P1[2] - P1[0], x[i, 1] * P1[2] - P1[1],
+                      xp[i, 0] * P2[2] - P2[0], xp[i, 1] * P2[2] - P2[1]])
+        pts.append(np.linalg.lstsq(A[:, :3], -A[:, 3], rcond=None)[0])
+    return r, keep, flag, np.array(pts).reshape(-1, 3)
+
+
 def render_bwd(wh, mean2d, conic, opacity, colour, ranges, vals, dimage, bg=(0.0, 0.0, 0.0)):
     wh = _i32(wh).reshape(-1, 2)
     C_ = np.asarray(opacity).shape[0]

@@ -1,8 +1,11 @@
 """Seeded synthetic inputs for the anchor-Gaussian rendering path.
 
 This module only *draws* inputs; it holds none of the method's arithmetic
-(no decoding, projection, sorting or compositing).  Both the CUDA path and the
-FP64 CPU oracle are fed from here, so the two always see byte-identical inputs.
+(no decoding, projection of Gaussians, sorting, compositing, fundamental
+matrix or triangulation).  Both the CUDA path and the FP64 CPU oracle are fed
+from here, so the two always see byte-identical inputs.  The one pinhole
+reprojection here (`flow_pair`) synthesises what the optical-flow network of
+Sec. III would deliver: the input of the flow densification, not its method.
 
 Every generator uses NumPy's PCG64 (`np.random.default_rng`), draws in the
 fixed order written in its docstring, draws in FP64 and casts to FP32.
@@ -349,3 +352,48 @@ def loop_road(seed=0, n_anchors=2_000_000, circumference=5000.0, relief=1.0,
                  feat=feat, log_scaling=log_scaling, offsets=offsets, part=part, mlp=mlp,
                  F=F, k=k, hidden=hidden, M=n_parts, cams=np.stack(cams), wh=wh,
                  targets=targets)
+
+
+@dataclass
+class FlowPair:
+    cams: np.ndarray       # [2, 16] float32, keyframes 1 and 2
+    wh: tuple              # (width, height)
+    flow: np.ndarray       # [H, W, 2] float32, keyframe 1 -> keyframe 2 (pixels)
+    depth: np.ndarray      # [H, W] float32, depth of each keyframe-1 pixel (its true 3D point)
+    outlier: np.ndarray    # [H, W] bool, pixels whose flow was replaced by a random vector
+    samples: np.ndarray    # [n_samples] int32 pixel indices y W + x, drawn without replacement
+
+
+def flow_pair(seed=0, width=1241, height=376, fx=718.0, step=(0.3, 0.0, 1.2), yaw_deg=1.5,
+              outlier_frac=0.2, noise_px=0.0, n_samples=200_000):
+    """Two consecutive keyframes of a forward-moving camera and the dense flow
+    between them, standing in for the flow network's output (Sec. III, Flow
+    Densification).  Draw order: depth-field phases (8 uniform), outlier mask
+    (H W uniform), outlier vectors (2 H W uniform in [-40, 40] px), flow
+    noise (2 H W normal, times noise_px), samples (a permutation prefix).
+    Depth: 4 + 40 (1 + sum of 4 random plane waves / 4) / 2 m, smooth in the
+    image.  Flow of an inlier pixel: its depth-scaled ray, moved into
+    keyframe 2 and reprojected (pixels at integer coordinates)."""
+    rng = np.random.default_rng(seed)
+    cx, cy = width / 2.0, height / 2.0
+    c1 = camera(fx, fx, cx, cy, (0.0, 0.0, 0.0))
+    c2 = camera(fx, fx, cx, cy, step, yaw_deg=yaw_deg)
+    ph = rng.uniform(0, 2 * np.pi, 8)
+    yy, xx = np.mgrid[0:height, 0:width].astype(np.float64)
+    wave = sum(np.sin(xx * (0.004 + 0.002 * i) + yy * (0.01 - 0.002 * i) + ph[i]) for i in range(4)) / 4.0
+    depth = 4.0 + 40.0 * (1.0 + wave) / 2.0
+    X1 = np.stack([(xx - cx) / fx * depth, (yy - cy) / fx * depth, depth], -1)     # keyframe-1 camera frame
+    R1, t1 = c1[4:13].astype(np.float64).reshape(3, 3), c1[13:16].astype(np.float64)
+    R2, t2 = c2[4:13].astype(np.float64).reshape(3, 3), c2[13:16].astype(np.float64)
+    Xw = (X1 - t1) @ R1                                                              # R1^T (X1 - t1)
+    X2 = Xw @ R2.T + t2
+    u2 = fx * X2[..., 0] / X2[..., 2] + cx
+    v2 = fx * X2[..., 1] / X2[..., 2] + cy
+    flow = np.stack([u2 - xx, v2 - yy], -1)
+    out = rng.uniform(size=(height, width)) < outlier_frac
+    rnd = rng.uniform(-40, 40, (height, width, 2))
+    flow[out] = rnd[out]
+    flow += noise_px * rng.normal(size=(height, width, 2))
+    samples = rng.permutation(width * height)[:n_samples].astype(np.int32)
+    return FlowPair(np.stack([c1, c2]), (width, height), flow.astype(np.float32), depth.astype(np.float32),
+                    out, samples)
