@@ -20,6 +20,7 @@
  *   gs_adam_step, gs_densify_stats, gs_densify_masks  optimizer step and
  *                  growth / pruning statistics after the reverse pass
  *   gs_voxelize, gs_loop_closure  map maintenance (Eq. 4, Eq. 7)
+ *   gs_flow_triangulate  epipolar filtering (Eq. 5) and triangulation of flow
  *
  * Conventions shared by every call
  * --------------------------------
@@ -374,6 +375,30 @@ int gs_voxelize(const float *points, int64_t P, float eps, const uint64_t *exist
  * NULL.  Offsets, features and scalings are left as they are. */
 int gs_loop_closure(float *xyz, int32_t N, const gs_camera *old_cams, const gs_camera *new_cams,
                     const int32_t *wh, int32_t K, float z_far, int32_t *assigned, void *stream);
+
+/* ---- Flow densification geometry (Sec. III, Flow Densification; Eq. 5).
+ * For keyframes 1 and 2 with known poses, F = [e2]x P2 P1^+ with P_i =
+ * K_i [R_i | t_i], e2 = P2 C1 and C1 the centre of keyframe 1.  Each sampled
+ * pixel x = (px, py, 1) of keyframe 1 and its flow correspondence x' = x +
+ * flow(x) is kept iff |x'^T F x| < tau (F and the residual in double
+ * precision); kept pairs are triangulated by linear least squares on the four
+ * DLT rows with the homogeneous coordinate fixed to 1 (double precision).
+ * The paper states neither tau nor N: they are the caller's, and so is the
+ * random choice of the N samples (passed in).
+ * cam1, cam2: device gs_camera (one each); flow: device float [H][W][2]
+ * (x, y displacement in pixels, pixels at integer coordinates); samples:
+ * device int32 [N] pixel indices py W + px; residual: device float [N] or
+ * NULL; kept: device int32 [cap] sample positions of the kept pairs in sample
+ * order; points: device float [cap][3] their world points; n_kept: device
+ * uint32.  ws: gs_flow_workspace(N) bytes, 256-byte aligned.  Errors in
+ * status: GS_ERR_INVALID_ARG (site 90) for a sample outside the image;
+ * GS_ERR_CAPACITY with the needed count when the kept pairs exceed cap
+ * (nothing written, *n_kept = 0). */
+size_t gs_flow_workspace(int32_t N);
+int gs_flow_triangulate(const gs_camera *cam1, const gs_camera *cam2, int32_t width, int32_t height,
+                        const float *flow, const int32_t *samples, int32_t N, double tau, float *residual,
+                        int32_t *kept, float *points, int64_t cap, uint32_t *n_kept, void *ws, size_t ws_bytes,
+                        gs_status *status, void *stream);
 
 /* Reverse of Eq. 1 and of the projection.  Per pixel, from the back: with
  * w_i = alpha_i T_i and B_i the colour composited behind splat i (plus

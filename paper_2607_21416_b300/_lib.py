@@ -96,6 +96,9 @@ EXPORTS = {
     "gs_voxelize_workspace": (sz, [i64]),
     "gs_voxelize": (C.c_int, [vp, i64, C.c_float, vp, i64, vp, vp, i64, vp, vp, sz, vp, vp]),
     "gs_loop_closure": (C.c_int, [vp, i32, vp, vp, vp, i32, C.c_float, vp, vp]),
+    "gs_flow_workspace": (sz, [i32]),
+    "gs_flow_triangulate": (C.c_int, [vp, vp, i32, i32, vp, vp, i32, C.c_double, vp, vp, vp, i64, vp, vp, sz,
+                                      vp, vp]),
     "gs_photometric_loss": (C.c_int, [vp, vp, P(gs_view), i32, C.c_float, vp, sz, vp, vp, vp]),
     "gs_render_bwd": (C.c_int, [P(gs_gauss3d), vp, P(gs_splats), P(gs_bins), P(gs_view), i32,
                                 P(C.c_float), i32, vp, sz, vp, vp, vp, P(gs_splat_grad),

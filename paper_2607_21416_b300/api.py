@@ -338,6 +338,23 @@ def loop_closure(xyz, old_cams, new_cams, wh, z_far, assigned=None, stream=None)
                                                    _ptr(assigned), _stream(stream)))
 
 
+def flow_workspace(N):
+    return int(L.load().gs_flow_workspace(int(N)))
+
+
+def flow_triangulate(cams, wh, flow, samples, tau, kept, points, n_kept, ws, status, residual=None, stream=None):
+    """Eq. 5 filtering and triangulation: cams device [2, 16] float32
+    (keyframes 1, 2), flow device [H, W, 2], samples device int32 [N]."""
+    lib = L.load()
+    c1 = C.c_void_p(cams.data_ptr())
+    c2 = C.c_void_p(cams.data_ptr() + 64)
+    L.check("gs_flow_triangulate", lib.gs_flow_triangulate(c1, c2, int(wh[0]), int(wh[1]), _ptr(flow), _ptr(samples),
+                                                           int(samples.numel()), float(tau), _ptr(residual),
+                                                           _ptr(kept), _ptr(points), int(kept.numel()),
+                                                           _ptr(n_kept), _ptr(ws), ws.numel(), _ptr(status),
+                                                           _stream(stream)))
+
+
 def render_bwd(g: Gauss3D, sp: Splats, bins: Bins, views: Views, bg, d_image, sgrad, out: Gauss3DGrad,
                status, ws, chunk=0, T_final=None, last=None, stream=None):
     lib = L.load()

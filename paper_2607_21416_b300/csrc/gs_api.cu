@@ -274,6 +274,20 @@ int gs_loop_closure(float *xyz, int32_t N, const gs_camera *old_cams, const gs_c
     return launch_loop_closure(xyz, N, old_cams, new_cams, wh, K, z_far, assigned, (cudaStream_t)stream);
 }
 
+size_t gs_flow_workspace(int32_t N) { return N < 0 ? 0 : flow_workspace_bytes(N); }
+
+int gs_flow_triangulate(const gs_camera *cam1, const gs_camera *cam2, int32_t width, int32_t height, const float *flow,
+                        const int32_t *samples, int32_t N, double tau, float *residual, int32_t *kept, float *points,
+                        int64_t cap, uint32_t *n_kept, void *ws, size_t ws_bytes, gs_status *status, void *stream)
+{
+    if (!cam1 || !cam2 || width < 1 || height < 1 || (long long)width * height >= (1ll << 31) || !flow || N < 0 ||
+        (N > 0 && !samples) || !(tau >= 0.0) || cap < 0 || !kept || !points || !n_kept || !status || !ws ||
+        (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < flow_workspace_bytes(N))
+        return GS_ERR_INVALID_ARG;
+    return launch_flow_triangulate(cam1, cam2, width, height, flow, samples, N, tau, residual, kept, points, cap,
+                                   n_kept, ws, status, (cudaStream_t)stream);
+}
+
 int gs_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *sp, const gs_bins *bins,
                   const gs_view *views, int32_t V, const float *bg, int32_t chunk, void *ws, size_t ws_bytes,
                   const float *d_image, const float *T_final, const int32_t *last, gs_splat_grad *sgrad,

@@ -51,6 +51,10 @@ int launch_l1(const float *image, const float *target, const ViewTable &vt, floa
               cudaStream_t s);
 size_t photometric_workspace_bytes(const ViewTable &vt);
 size_t voxelize_workspace_bytes(long long P);
+size_t flow_workspace_bytes(int N);
+int launch_flow_triangulate(const gs_camera *c1, const gs_camera *c2, int W, int H, const float *flow,
+                            const int32_t *samples, int N, double tau, float *residual, int32_t *kept, float *points,
+                            long long cap, uint32_t *n_kept, void *ws, gs_status *st, cudaStream_t s);
 int launch_voxelize(const float *pts, long long P, float eps, const unsigned long long *existing, long long n_ex,
                     unsigned long long *keys_out, float *centers_out, long long cap, uint32_t *n_out, void *ws,
                     gs_status *st, cudaStream_t s);
