@@ -358,9 +358,21 @@ def run_ours(args, rank, world, dist):
             api.loop_closure(xyz_w, old, new, whd, 100.0, assigned)
 
         lc_ms = timed_m(lc)
+        # flow densification geometry (Eq. 5): 200k sampled correspondences of a 1241x376 flow pair
+        fp = scenes.flow_pair(seed=5, outlier_frac=0.3, noise_px=0.05, n_samples=200_000)
+        fcams = torch.as_tensor(np.ascontiguousarray(fp.cams, np.float32), device=dev)
+        fflow = torch.as_tensor(fp.flow, device=dev)
+        fsmp = torch.as_tensor(fp.samples, device=dev)
+        fkept = torch.zeros(len(fp.samples), dtype=torch.int32, device=dev)
+        fpts = torch.zeros(len(fp.samples), 3, device=dev)
+        fn = torch.zeros(1, dtype=torch.int32, device=dev)
+        fws = api.workspace(api.flow_workspace(len(fp.samples)), dev)
+        flow_ms = timed_m(lambda: api.flow_triangulate(fcams, fp.wh, fflow, fsmp, 200.0, fkept, fpts, fn, fws, vst))
+        assert api.read_status(vst)[0] == 0
         maint = {"voxelize_ms": vox_ms, "points": P, "voxel_size": eps, "existing_voxels": int(n_ex[0]),
                  "new_voxels": int(n_o[0]), "loop_closure_ms": lc_ms, "anchors": int(ax.shape[0]),
                  "keyframes": views.V, "moved_anchors": int((assigned >= 0).sum()),
+                 "flow_triangulate_ms": flow_ms, "flow_samples": len(fp.samples), "flow_kept": int(fn[0]),
                  "note": "loop_closure_ms includes a 2.4 MB copy restoring the anchors before each call"}
         del pts, vws, keys_o, cen_o, xyz_w
 
