@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_upsweep(const uint32_t *__
                                                               uint32_t *__restrict__ hist,
                                                               const gs_status *st)
 {
-    if (has_error(st)) return;
+    if (__syncthreads_or(has_error(st))) return;   // block-uniform exit
     __shared__ uint32_t s_h[kSortWarps * 256];   // per-warp histograms, flat
     for (int i = threadIdx.x; i < kSortWarps * 256; i += kSortThreads) s_h[i] = 0;
     __syncthreads();
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_upsweep(const uint32_t *__
 __global__ void __launch_bounds__(1024) radix_scan_rows(uint32_t *__restrict__ hist, int nb,
                                                         uint32_t *__restrict__ totals, const gs_status *st)
 {
-    if (has_error(st)) return;
+    if (__syncthreads_or(has_error(st))) return;   // block-uniform exit
     __shared__ uint32_t s_warp[32];
     const int d = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t x = threadIdx.x < nb ? hist[d * nb + threadIdx.x] : 0;
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep(
     uint32_t *__restrict__ vout, const uint32_t *__restrict__ n_ptr, int shift,
     const uint32_t *__restrict__ hist, const uint32_t *__restrict__ totals, const gs_status *st)
 {
-    if (has_error(st)) return;
+    if (__syncthreads_or(has_error(st))) return;   // block-uniform exit
     __shared__ uint32_t s_keys[kSortTile];
     __shared__ uint32_t s_vals[kSortTile];
     // per-warp digit counts (then per-warp exclusive prefixes), flat
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(kSortThreads) count_valid_kernel(
     const int32_t *__restrict__ tiles, const int32_t *__restrict__ view_start, int V, int k,
     long long cap_cand, uint32_t *__restrict__ block_sums, const gs_status *st)
 {
-    if (has_error(st)) return;
+    if (__syncthreads_or(has_error(st))) return;   // block-uniform exit
     const uint32_t C = (uint32_t)min((long long)__ldg(view_start + V) * k, cap_cand);
     uint32_t t0, t1;
     block_tiles(C, blockIdx.x, gridDim.x, &t0, &t1);
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(1024) scan_block_sums(uint32_t *__restrict__ s
                                                         uint32_t *__restrict__ out_n, long long cap,
                                                         gs_status *st, int where)
 {
-    if (has_error(st)) return;
+    if (__syncthreads_or(has_error(st))) return;   // block-uniform exit
     __shared__ unsigned long long s_warp[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long x = threadIdx.x < nb ? sums[threadIdx.x] : 0ull;
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(kSortThreads) compact_valid_kernel(
     const uint32_t *__restrict__ block_off, uint32_t *__restrict__ ids, uint32_t *__restrict__ dkeys,
     const gs_status *st)
 {
-    if (has_error(st)) return;
+    if (__syncthreads_or(has_error(st))) return;   // block-uniform exit
     const uint32_t C = (uint32_t)min((long long)__ldg(view_start + V) * k, cap_cand);
     uint32_t t0, t1;
     block_tiles(C, blockIdx.x, gridDim.x, &t0, &t1);
@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(kSortThreads) count_pairs_kernel(
     const uint32_t *__restrict__ ids, const uint32_t *__restrict__ n_ptr, const int32_t *__restrict__ tiles,
     uint32_t *__restrict__ block_sums, long long cap_cand, const gs_status *st)
 {
-    if (has_error(st)) return;
+    if (__syncthreads_or(has_error(st))) return;   // block-uniform exit
     const uint32_t S = *n_ptr;
     uint32_t t0, t1;
     block_tiles(S, blockIdx.x, gridDim.x, &t0, &t1);
@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(kSortThreads) pair_offsets_kernel(
     const uint32_t *__restrict__ block_off, uint32_t *__restrict__ offs, uint32_t *__restrict__ round_first,
     long long max_rounds, long long cap_cand, const gs_status *st)
 {
-    if (has_error(st)) return;
+    if (__syncthreads_or(has_error(st))) return;   // block-uniform exit
     const uint32_t S = *n_ptr;
     uint32_t t0, t1;
     block_tiles(S, blockIdx.x, gridDim.x, &t0, &t1);
@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(kSortThreads) emit_pairs_kernel(
     const int32_t *__restrict__ view_start, int k, uint32_t *__restrict__ tkeys, uint32_t *__restrict__ tvals,
     ViewTable vt, long long cap_cand, const gs_status *st)
 {
-    if (has_error(st)) return;
+    if (__syncthreads_or(has_error(st))) return;   // block-uniform exit
     constexpr int kPer = kEmitPairs / kSortThreads;   // staged splats / pairs per thread and round
     const uint32_t S = *n_ptr, P = *np_ptr;
     __shared__ uint32_t s_off[kEmitPairs], s_t00[kEmitPairs], s_id[kEmitPairs];
@@ -720,7 +720,7 @@ __global__ void __launch_bounds__(kSortThreads) voxel_count_kernel(const uint32_
                                                                    long long n_ex, uint32_t *__restrict__ block_sums,
                                                                    const gs_status *st)
 {
-    if (has_error(st)) return;
+    if (__syncthreads_or(has_error(st))) return;   // block-uniform exit
     const uint32_t n = *n_ptr;
     uint32_t t0, t1;
     block_tiles(n, blockIdx.x, gridDim.x, &t0, &t1);
@@ -744,7 +744,7 @@ __global__ void __launch_bounds__(kSortThreads) voxel_write_kernel(const uint32_
                                                                    float *__restrict__ centers_out, long long cap,
                                                                    const gs_status *st)
 {
-    if (has_error(st)) return;
+    if (__syncthreads_or(has_error(st))) return;   // block-uniform exit
     const uint32_t n = *n_ptr;
     uint32_t t0, t1;
     block_tiles(n, blockIdx.x, gridDim.x, &t0, &t1);

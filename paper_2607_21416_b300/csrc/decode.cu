@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kVisThreads) vis_count_kernel(
     const float *__restrict__ xyz, int N, const gs_camera *__restrict__ cams, ViewTable vt,
     int *__restrict__ counts, int nchunks, const gs_status *st)
 {
-    if (has_error(st)) return;
+    if (__syncthreads_or(has_error(st))) return;   // block-uniform exit
     const int v = blockIdx.y, b = blockIdx.x;
     const Cam c = load_cam(cams, v);
     int n = 0;
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(1024) vis_scan_kernel(int *__restrict__ counts
                                                         int V, int32_t *__restrict__ view_start,
                                                         long long cap_rows, gs_status *st)
 {
-    if (has_error(st)) return;
+    if (__syncthreads_or(has_error(st))) return;   // block-uniform exit
     __shared__ int s_warp[32];
     __shared__ long long s_carry;
     if (threadIdx.x == 0) s_carry = 0;
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(kVisThreads) vis_write_kernel(
     const int *__restrict__ offsets, int nchunks, int32_t *__restrict__ row_anchor,
     long long cap_rows, const gs_status *st)
 {
-    if (has_error(st)) return;
+    if (__syncthreads_or(has_error(st))) return;   // block-uniform exit
     const int v = blockIdx.y, b = blockIdx.x;
     const Cam c = load_cam(cams, v);
     __shared__ int s_warp[32];
@@ -226,7 +226,7 @@ __device__ __forceinline__ float out_unit(const HeadPtr &h, int H, int o, const 
 
 __global__ void __launch_bounds__(128) decode_fp32_kernel(DecodeArgs a)
 {
-    if (has_error(a.st)) return;
+    if (__syncthreads_or(has_error(a.st))) return;   // block-uniform exit
     extern __shared__ float smem[];
     const int nt = blockDim.x;
     const int din = a.F + 4;

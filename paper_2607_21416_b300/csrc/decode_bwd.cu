@@ -30,7 +30,7 @@ __device__ __forceinline__ void head_layout(int F, int k, int H, int h, int *off
 
 __global__ void __launch_bounds__(kDbRows) decode_bwd_fp32_kernel(DecodeBwdArgsB a)
 {
-    if (has_error(a.f.st)) return;
+    if (__syncthreads_or(has_error(a.f.st))) return;   // block-uniform exit
     extern __shared__ float sm[];
     const int F = a.f.F, k = a.f.k, H = a.f.H, din = F + 4;
     const long long P = a.f.mlp_floats;

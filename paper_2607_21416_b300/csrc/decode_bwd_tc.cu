@@ -232,7 +232,7 @@ __device__ __forceinline__ bool tb_mma_step(uint64_t *bar, uint32_t &phase, F is
 __global__ void __launch_bounds__(kBThreads) decode_bwd_tc_kernel(DecodeBwdArgsB a, TbShape s)
 {
     const DecodeArgs &f = a.f;
-    if (has_error(f.st)) return;
+    if (__syncthreads_or(has_error(f.st))) return;   // block-uniform exit
     extern __shared__ __align__(1024) char sm[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t tslot;

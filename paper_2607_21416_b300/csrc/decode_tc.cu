@@ -135,7 +135,7 @@ __device__ __forceinline__ void stage_out(const float *stage, float *dst, int n,
 // vec: bit 0 = the five output arrays are 16-byte aligned, bit 1 = feature rows are.
 __global__ void __launch_bounds__(kTThreads) decode_tc_kernel(DecodeArgs a, TcShape s, int vec)
 {
-    if (has_error(a.st)) return;
+    if (__syncthreads_or(has_error(a.st))) return;   // block-uniform exit
     extern __shared__ __align__(1024) char sm[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t tslot;

@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(const uint32_t *__restrict__
     if (threadIdx.x == 0) s_carry = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const bool err = has_error(st);
+    const bool err = __syncthreads_or(has_error(st));   // one decision for the block
     for (int base = 0; base < T; base += 1024) {
         const int t = base + threadIdx.x;
         int x = 0;
