@@ -142,15 +142,14 @@ __device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const u
     if (!item_of(b, plan.item_base, vt.total_tiles, ranges, plan.L, &it)) return;
     const int lane = threadIdx.x & 31, tid = warp * 32 + lane;
     const TileCoord tc = tile_coord(vt, it.t, tid);
-    // lane l of warp w owns pixels (x0 + c, y) and (x0 + c + 8, y) with c = l & 7 and y = y0 + 4 w +
-    // (l >> 3): a splat narrower than 9 pixels is composited by at most one pixel of each lane, so
-    // one composite pass per staged splat suffices (a second one only where a lane needs both)
-    const int col = lane & 7, row = 4 * warp + (lane >> 3);
+    // one composite pass per staged splat suffices where a lane composites it at one of its two
+    // pixels (lane_pixels); a second one runs only where a lane needs both
     const int v = tc.v;
     const long long W = vt.W[v], H = vt.H[v];
-    const int px0 = tc.x0 + col, py = tc.y0 + row;
-    const bool in0 = px0 < W && py < H, in1 = px0 + 8 < W && py < H;
-    const int pid0 = row * kTile + col, pid1 = pid0 + 8;
+    const LanePix lpx = lane_pixels(tc, warp, lane, (int)W, (int)H);
+    const int px0 = lpx.px0, py = lpx.py;
+    const bool in0 = lpx.in0, in1 = lpx.in1;
+    const int pid0 = lpx.pid0, pid1 = pid0 + 8;
     const float fx0 = (float)px0, fx1 = (float)(px0 + 8), fy = (float)py;
     const float bx0 = (float)tc.x0, bx1 = bx0 + (float)(kTile - 1);
     const float by0 = (float)(tc.y0 + 4 * warp), by1 = by0 + 3.f;

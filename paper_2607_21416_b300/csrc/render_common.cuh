@@ -80,6 +80,26 @@ __device__ __forceinline__ TileCoord tile_coord(const ViewTable &vt, int t, int 
     return c;
 }
 
+// The two pixels a lane composites in its warp's 16x4 block: (x0 + c, y) and
+// (x0 + c + 8, y) with c = lane & 7 and y = y0 + 4 w + (lane >> 3).  A splat
+// narrower than 9 pixels is composited by at most one pixel of each lane, so
+// the two per-pixel steps rarely both run their compositing branch.
+struct LanePix {
+    int px0, py, pid0;     // first pixel (image coordinates) and its tile-local id; the second is +8
+    bool in0, in1;         // inside the image
+};
+__device__ __forceinline__ LanePix lane_pixels(const TileCoord &tc, int warp, int lane, int W, int H)
+{
+    LanePix lp;
+    const int col = lane & 7, row = 4 * warp + (lane >> 3);
+    lp.px0 = tc.x0 + col;
+    lp.py = tc.y0 + row;
+    lp.pid0 = row * kTile + col;
+    lp.in0 = lp.px0 < W && lp.py < H;
+    lp.in1 = lp.px0 + 8 < W && lp.py < H;
+    return lp;
+}
+
 struct Item {
     int t;            // tile
     int k, nk;        // chunk index, chunks of the tile

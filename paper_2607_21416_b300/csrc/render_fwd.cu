@@ -163,7 +163,8 @@ __device__ __forceinline__ void chunk_unit(const float4 *__restrict__ rec, const
     if (!item_of(b, plan.item_base, vt.total_tiles, ranges, plan.L, &it)) return;
     const int lane = threadIdx.x & 31, tid = warp * 32 + lane;
     const TileCoord tc = tile_coord(vt, it.t, tid);
-    const float fpx = (float)tc.px, fy0 = (float)tc.py, fy1 = (float)(tc.py + 1);
+    const LanePix lp = lane_pixels(tc, warp, lane, vt.W[tc.v], vt.H[tc.v]);
+    const float fx0 = (float)lp.px0, fx1 = (float)(lp.px0 + 8), fy = (float)lp.py;
     const float bx0 = (float)tc.x0, bx1 = bx0 + (float)(kTile - 1);
     const float by0 = (float)(tc.y0 + 4 * warp), by1 = by0 + 3.f;
     const bool multi = it.nk > 1;
@@ -173,15 +174,15 @@ __device__ __forceinline__ void chunk_unit(const float4 *__restrict__ rec, const
     p0.T = p1.T = 1.f;
     p0.C0 = p0.C1 = p0.C2 = p1.C0 = p1.C1 = p1.C2 = 0.f;
     p0.last = p1.last = p0.stop = p1.stop = p0.ncomp = p1.ncomp = 0;
-    p0.done = !tc.in0;
-    p1.done = !tc.in1;
+    p0.done = !lp.in0;
+    p1.done = !lp.in1;
     if (FIX) {   // the marked pixels start from their entering transmittance
-        const int *lp = reinterpret_cast<const int *>(state_plane(plan.state, item, 5));
+        const int *lst = reinterpret_cast<const int *>(state_plane(plan.state, item, 5));
         const float *tp = state_plane(plan.state, item, 1);
-        p0.done = p0.done || lp[tc.pid0] != -1;
-        p1.done = p1.done || lp[tc.pid0 + kTile] != -1;
-        if (!p0.done) p0.T = tp[tc.pid0];
-        if (!p1.done) p1.T = tp[tc.pid0 + kTile];
+        p0.done = p0.done || lst[lp.pid0] != -1;
+        p1.done = p1.done || lst[lp.pid0 + 8] != -1;
+        if (!p0.done) p0.T = tp[lp.pid0];
+        if (!p1.done) p1.T = tp[lp.pid0 + 8];
     }
     const bool act0 = !p0.done, act1 = !p1.done;
     // the warp walks the item's list on its own, 32 positions at a time
@@ -196,8 +197,8 @@ __device__ __forceinline__ void chunk_unit(const float4 *__restrict__ rec, const
                 const float4 bb = W.b[e];
                 const float cb = W.c[e];
                 const int q = W.pos[e] + 1;
-                if (!p0.done) fwd_step<true>(p0, a, bb, cb, fpx, fy0, q);
-                if (!p1.done) fwd_step<true>(p1, a, bb, cb, fpx, fy1, q);
+                if (!p0.done) fwd_step<true>(p0, a, bb, cb, fx0, fy, q);
+                if (!p1.done) fwd_step<true>(p1, a, bb, cb, fx1, fy, q);
             }
         } else {
             for (int e = 0; e < cnt; ++e) {
@@ -205,8 +206,8 @@ __device__ __forceinline__ void chunk_unit(const float4 *__restrict__ rec, const
                 const float4 bb = W.b[e];
                 const float cb = W.c[e];
                 const int q = W.pos[e] + 1;
-                if (!p0.done) fwd_step<false>(p0, a, bb, cb, fpx, fy0, q);
-                if (!p1.done) fwd_step<false>(p1, a, bb, cb, fpx, fy1, q);
+                if (!p0.done) fwd_step<false>(p0, a, bb, cb, fx0, fy, q);
+                if (!p1.done) fwd_step<false>(p1, a, bb, cb, fx1, fy, q);
             }
         }
         __syncwarp();
@@ -223,11 +224,11 @@ __device__ __forceinline__ void chunk_unit(const float4 *__restrict__ rec, const
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
         const PixFwd &ps = half ? p1 : p0;
-        const int pix = tc.pid0 + half * kTile;
-        const int py = tc.py + half;
+        const int pix = lp.pid0 + 8 * half;
+        const int px = lp.px0 + 8 * half, py = lp.py;
         if (!multi) {
-            if (half ? tc.in1 : tc.in0)
-                write_image(vt, tc.v, tc.px, py, ps.C0, ps.C1, ps.C2, ps.T, ps.last, bg0, bg1, bg2, image, T_final,
+            if (half ? lp.in1 : lp.in0)
+                write_image(vt, tc.v, px, py, ps.C0, ps.C1, ps.C2, ps.T, ps.last, bg0, bg1, bg2, image, T_final,
                             last);
             continue;
         }
@@ -244,7 +245,7 @@ __device__ __forceinline__ void chunk_unit(const float4 *__restrict__ rec, const
             state_plane(plan.state, it.base, 7)[pix] = fmaf(ps.T, bg0, f0);
             state_plane(plan.state, it.base, 8)[pix] = fmaf(ps.T, bg1, f1);
             state_plane(plan.state, it.base, 9)[pix] = fmaf(ps.T, bg2, f2);
-            write_image(vt, tc.v, tc.px, py, f0, f1, f2, ps.T, ps.last > 0 ? it.k * plan.L + ps.last : -1, bg0, bg1,
+            write_image(vt, tc.v, px, py, f0, f1, f2, ps.T, ps.last > 0 ? it.k * plan.L + ps.last : -1, bg0, bg1,
                         bg2, image, T_final, last);
             continue;
         }
