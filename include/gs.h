@@ -243,7 +243,7 @@ int gs_bin_sort(const gs_splats *sp, int32_t k, const int32_t *view_start, int64
  * stop before a splat whose T(1 - alpha) < 1e-4; C += c alpha T; T *= 1 -
  * alpha.  image = C + T bg.  bg: HOST float[3].
  * Work items: each tile's list is cut into chunks of `chunk` splats (0 selects
- * 512; otherwise 256 .. 2^24), and every 16x4 pixel block of every chunk is a
+ * 384; otherwise 256 .. 2^24), and every 16x4 pixel block of every chunk is a
  * work unit that persistent warps take from a device counter, so that a few
  * very long tiles do not serialise the launch.  Later chunks of a tile are
  * composited on their own transmittance and scaled by the transmittance in

@@ -68,6 +68,7 @@ class gs_adam_group(C.Structure):
 
 
 GS_ADAM_MAX_GROUPS = 16
+DEFAULT_CHUNK = 384   # splats per compositing work item when gs_render_fwd gets chunk = 0
 
 P = C.POINTER
 

@@ -165,7 +165,7 @@ int gs_bin_sort(const gs_splats *sp, int32_t k, const int32_t *view_start, int64
     return launch_bin_sort(sp, k, view_start, cap_rows, vt, bins, ws, ws_bytes, status, (cudaStream_t)stream);
 }
 
-static int chunk_len(int32_t chunk) { return chunk == 0 ? 512 : chunk; }
+static int chunk_len(int32_t chunk) { return chunk == 0 ? 384 : chunk; }
 
 size_t gs_render_workspace(const gs_view *views, int32_t V, int64_t cap_pairs, int32_t chunk)
 {

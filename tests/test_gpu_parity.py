@@ -164,7 +164,7 @@ def _render_fwd_case(s, view_start, k, prj, opacity, colour, keys, vals, ranges,
     assert 0 < int(nev[1].item()) <= int(nev[0].item())
     # the same counts over the tiles whose list is a single work item
     lens = ranges[:, 1].astype(np.int64) - ranges[:, 0]
-    L_ = chunk if chunk else 512
+    L_ = chunk if chunk else L.DEFAULT_CHUNK
     assert 0 <= int(nev[2].item()) <= int(nev[0].item()) and 0 <= int(nev[3].item()) <= int(nev[1].item())
     if (lens <= L_).all():
         assert int(nev[2].item()) == int(nev[0].item()) and int(nev[3].item()) == int(nev[1].item())
