@@ -68,11 +68,6 @@ static bool check_gauss(const gs_gauss3d *g)
            g->colour && g->cap_rows * (long long)g->k < (1ll << 31);
 }
 
-static int launch_status()
-{
-    return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
-}
-
 extern "C" {
 
 uint64_t gs_kernel_launches(void) { return (uint64_t)g_launches.load(std::memory_order_relaxed); }
