@@ -1,11 +1,12 @@
 // render_common.cuh -- shared pieces of the tile compositing kernels.
 //
 // Work decomposition.  Each 16x16 tile's sorted splat list [start, end) is
-// cut into chunks of at most L splats; chunk k of tile t is one work item and
-// one CTA of 128 threads (two pixels each).  item_base[t] (exclusive scan of
-// the per-tile chunk counts, built on the device) numbers the items; the item
-// of block b is found by binary search.  A tile with one chunk is composited
-// directly.  Chunk 0 of a multi-chunk tile is composited exactly (it starts
+// cut into chunks of at most L splats; chunk k of tile t is one work item,
+// and each of its four 16x4 pixel blocks is a work unit that one warp of a
+// persistent kernel takes from a device counter (two pixels per lane,
+// lane_pixels).  item_base[t] (exclusive scan of the per-tile chunk counts,
+// built on the device) numbers the items; the item of unit u is found by
+// binary search.  A tile with one chunk is composited directly.  Chunk 0 of a multi-chunk tile is composited exactly (it starts
 // at T = 1); every later chunk is composited with its own transmittance
 // starting at 1 and no stop rule, and the combine step scales it by the
 // transmittance in front of it.  That is Eq. 1 exactly unless a pixel's stop
@@ -28,7 +29,7 @@
 namespace gs {
 
 constexpr int kRT = kTilePix;      // pixels per tile / work item
-constexpr int kRThreads = 128;     // threads per work item: two pixels each (rows y and y + 8)
+constexpr int kRThreads = 128;     // threads per CTA of the compositing kernels (4 warps, one 16x4 block each)
 constexpr int kStateWords = 10;    // T0 (Tprod during the forward), Tend, P0..2 (C during the forward), last,
                                    // composited count, F0..2 (first item only)  (x 256 pixels)
 
@@ -54,12 +55,12 @@ __device__ __forceinline__ float splat_q(float4 a, float C, float px, float py, 
 // Unclamped alpha o exp(power) = 2^(q + L).
 __device__ __forceinline__ float splat_alpha(float q, float L) { return ex2_approx(__fadd_rn(q, L)); }
 
-// Tile thread `tid` (0..127) owns pixels (px, py) and (px, py + 1), with px =
-// x0 + (tid & 15), py = y0 + 2 (tid >> 4): tile-local pixel ids pid0 = (py -
-// y0) * 16 + (px - x0) and pid0 + 16.  Tile warp w = tid >> 5 covers the 16x4
-// block of rows 4w..4w+3.  The compositing kernels are persistent: each warp
-// takes work units (item, block w) from a device counter and plays tile warp
-// w of that item.
+// Tile coordinates of tile t (view, origin), and for the combine step, where
+// tile thread `tid` (0..127) owns pixels (px, py) and (px, py + 1): px = x0 +
+// (tid & 15), py = y0 + 2 (tid >> 4), tile-local pixel ids pid0 = (py - y0)
+// 16 + (px - x0) and pid0 + 16.  The persistent compositing kernels use only
+// the view and origin: their warp w plays the 16x4 block of rows 4w..4w+3 of
+// its work unit's item, its lanes taking pixels as lane_pixels says.
 struct TileCoord {
     int v, x0, y0, px, py, pid0;
     bool in0, in1;
