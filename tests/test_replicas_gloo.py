@@ -34,7 +34,7 @@ def _rank(rank, world, port, out):
 def test_whole_job_takes_the_slowest_rank_and_sums_the_pixels():
     world = 2
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:   # no fork of a threaded process
         out = m.dict()
         mp.start_processes(_rank, args=(world, port, out), nprocs=world, start_method="spawn", join=True)
         res = dict(out)
