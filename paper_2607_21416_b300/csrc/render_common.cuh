@@ -147,6 +147,7 @@ struct WarpStage {
     float io[32];      // 1 / opacity (backward)
     uint32_t id[32];   // candidate id
     int pos[32];       // list position within the item (0-based)
+    int half[32];      // forward: bit 0 / 1 = the alpha box meets the left / right 8 columns of the block
 };
 
 // Whether the alpha >= 1/255 region of a splat record meets the pixel block
@@ -200,6 +201,13 @@ __device__ __forceinline__ int warp_stage(WarpStage &W, const float4 *__restrict
         if (backward) W.io[slot] = exp2f(-b.y);
         W.id[slot] = id;
         W.pos[slot] = (int)(pos - s0);
+        // forward: which 8-column half of the block the box meets.  A lane's first pixel lies in the
+        // left half and its second in the right one (lane_pixels), so a pixel of a half the box
+        // misses fails the alpha test as the kernels evaluate it and is skipped (same test as
+        // above).  The reverse pass does not use it: there the extra tests cost more than they save.
+        if (!backward)
+            W.half[slot] = (meets_block(a, b, bx0, bx0 + 7.f, by0, by1) ? 1 : 0) |
+                           (meets_block(a, b, bx0 + 8.f, bx1, by0, by1) ? 2 : 0);
     }
     __syncwarp();
     (void)lane;

@@ -196,18 +196,18 @@ __device__ __forceinline__ void chunk_unit(const float4 *__restrict__ rec, const
                 const float4 a = W.a[e];
                 const float4 bb = W.b[e];
                 const float cb = W.c[e];
-                const int q = W.pos[e] + 1;
-                if (!p0.done) fwd_step<true>(p0, a, bb, cb, fx0, fy, q);
-                if (!p1.done) fwd_step<true>(p1, a, bb, cb, fx1, fy, q);
+                const int q = W.pos[e] + 1, hm = W.half[e];
+                if ((hm & 1) && !p0.done) fwd_step<true>(p0, a, bb, cb, fx0, fy, q);
+                if ((hm & 2) && !p1.done) fwd_step<true>(p1, a, bb, cb, fx1, fy, q);
             }
         } else {
             for (int e = 0; e < cnt; ++e) {
                 const float4 a = W.a[e];
                 const float4 bb = W.b[e];
                 const float cb = W.c[e];
-                const int q = W.pos[e] + 1;
-                if (!p0.done) fwd_step<false>(p0, a, bb, cb, fx0, fy, q);
-                if (!p1.done) fwd_step<false>(p1, a, bb, cb, fx1, fy, q);
+                const int q = W.pos[e] + 1, hm = W.half[e];
+                if ((hm & 1) && !p0.done) fwd_step<false>(p0, a, bb, cb, fx0, fy, q);
+                if ((hm & 2) && !p1.done) fwd_step<false>(p1, a, bb, cb, fx1, fy, q);
             }
         }
         __syncwarp();
