@@ -390,8 +390,11 @@ int gs_loop_closure(float *xyz, int32_t N, const gs_camera *old_cams, const gs_c
  * device int32 [N] pixel indices py W + px; residual: device float [N] or
  * NULL; kept: device int32 [cap] sample positions of the kept pairs in sample
  * order; points: device float [cap][3] their world points; n_kept: device
- * uint32.  ws: gs_flow_workspace(N) bytes, 256-byte aligned.  Errors in
- * status: GS_ERR_INVALID_ARG (site 90) for a sample outside the image;
+ * uint32.  A kept pair without parallax (its two rays parallel, e.g. a pixel
+ * at the epipole with zero flow) has a singular system and a non-finite
+ * point; callers drop such points.  ws: gs_flow_workspace(N) bytes, 256-byte
+ * aligned.  Errors in status: GS_ERR_INVALID_ARG (site 90) for a sample
+ * outside the image;
  * GS_ERR_CAPACITY with the needed count when the kept pairs exceed cap
  * (nothing written, *n_kept = 0). */
 size_t gs_flow_workspace(int32_t N);
