@@ -538,7 +538,7 @@ __global__ void __launch_bounds__(256) keys_kernel(const uint32_t *__restrict__ 
     }
 }
 
-// ------------------------------------------------------------------ driver
+// ------------------------------------------------------------- host launch
 struct SortLayout {
     size_t ids_a, ids_b, dk_a, dk_b, offs, rfirst, tk_a, tk_b, tv_b, hist, totals, sums, counts, total;
     long long max_rounds;
