@@ -39,6 +39,18 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "keyframe_batch_200k_anchors_8x1241x376"
 METRIC = "mapping fwd+bwd Mpix/s (8-keyframe batch)"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def measured_peaks():
+    """The measured peaks of this machine's GPUs (empty when the file is absent)."""
+    return json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+
+
+def hbm_peak():
+    """(HBM GB/s, "measured" | "fallback"): the measured copy bandwidth, else 6.4 TB/s."""
+    pk = measured_peaks()
+    return (pk["hbm_gbs"], "measured") if "hbm_gbs" in pk else (6400.0, "fallback")
 
 
 def parse():
@@ -258,15 +270,12 @@ def run_ours(args, rank, world, dist):
                 pts.append(pe0.elapsed_time(pe1))
         pms = statistics.mean(pts)
         alg = 36 * npix   # image and target read, dL/dimage written: 3 channels x 4 B each
-        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6400.0) \
-            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6400.0
+        hbm, hbm_of = hbm_peak()
         gbs = alg / (pms * 1e-3) / 1e9
         photo = {"ms": pms, "lambda": 0.8, "loss": [float(x) for x in ploss.tolist()],
                  "launches": 2,
                  "roofline": {"kernel": "ssim_kernel + photometric_finalize",
-                              "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
-                              "peak_of": "measured" if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json"))
-                              else "fallback",
+                              "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "peak_of": hbm_of,
                               "frac": gbs / hbm, "traffic": None,
                               "work_per_launch": f"{alg} B (36 B per pixel: image, target, gradient)"}}
         del pws, pd
@@ -297,14 +306,11 @@ def run_ours(args, rank, world, dist):
 
         adam_ms = timed(opt.step)
         stats_ms = timed(lambda: stats.accumulate(rp))
-        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6400.0) \
-            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6400.0
+        hbm, hbm_of = hbm_peak()
         gbs = 28 * n_par / (adam_ms * 1e-3) / 1e9
         optim = {"adam_ms": adam_ms, "parameters": n_par, "densify_stats_ms": stats_ms,
                  "roofline": {"kernel": "adam_kernel", "bound": "hbm", "achieved": gbs, "peak": hbm,
-                              "unit": "GB/s", "frac": gbs / hbm, "traffic": None,
-                              "peak_of": "measured" if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json"))
-                              else "fallback",
+                              "unit": "GB/s", "frac": gbs / hbm, "traffic": None, "peak_of": hbm_of,
                               "work_per_launch": f"{28 * n_par} B (28 B per parameter)"}}
         del opt, stats, work
 
@@ -416,11 +422,7 @@ def run_ours(args, rank, world, dist):
 
     stages = {n: statistics.mean(v) for n, v in stage_ms.items()}
     dom = max(("render_fwd", "render_bwd", "bin_sort", "decode", "decode_bwd"), key=lambda n: stages[n])
-    peaks = {}
-    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk):
-        peaks = json.load(open(pk))
-    roof = roofline(dom, stages[dom], counts, n_pairs, n_rows, rp, scene, peaks)
+    roof = roofline(dom, stages[dom], counts, n_pairs, n_rows, rp, scene, measured_peaks())
     if roof.get("bound") == "alu":
         roof["peak_measured"] = api.probe_peak(0) / 1e12   # FP32 FMA issue rate of this device
         roof["sfu_ex2_peak_measured"] = api.probe_peak(1) / 1e12
