@@ -189,8 +189,8 @@ def run_ours(args, rank, world, dist):
         ev[5].record()
         if rp.ggrad is None:
             rp.ggrad = api.Gauss3DGrad.like(rp.g)
-        api.render_bwd(rp.g, rp.splats, rp.bins, views, rp.bg, rp.d_image, rp.sgrad, rp.ggrad, rp.status,
-                       rp.render_ws, rp.chunk, rp.T_final, rp.last)
+        api.render_bwd(rp.g, rp.splats, rp.bins, views, rp.image, rp.d_image, rp.sgrad, rp.ggrad, rp.status,
+                       rp.render_ws, rp.chunk, rp.last)
         ev[6].record()
         api.decode_bwd(anchors, views, rp.g, rp.ggrad, rp.agrad, rp.dbwd_ws, rp.status, prec)
         ev[7].record()

@@ -187,6 +187,34 @@ const char *gs_status_string(int32_t code);
 /* Number of kernels this library has enqueued since it was loaded (host
  * counter, all devices and threads); a diagnostic for launch accounting. */
 uint64_t gs_kernel_launches(void);
+/* Failure-detection hook (no counterpart in the paper).  Sets the limit, in
+ * nanoseconds, of the waits of the tensor-core kernels (GS_PREC_BF16
+ * gs_decode / gs_decode_noalloc / gs_decode_bwd) for their MMAs to complete,
+ * for the calls enqueued after it (the value is read on the host at launch):
+ * a wait that runs out records GS_ERR_TIMEOUT in the status word, and the
+ * kernel then waits (with the default limit) for its MMAs still in flight,
+ * frees its tensor memory and returns, leaving the context usable.  0 makes
+ * the first completion wait give up at once (how a test drives that path);
+ * ns < 0 restores the default of 1 s.  Process-wide; returns GS_OK. */
+int gs_set_wait_limit(int64_t ns);
+/* Launch shapes (no counterpart in the paper; set by the autotuner of the
+ * Python layer): CTAs per SM of the persistent forward and reverse
+ * compositing kernels, of the one-sweep radix-sort passes and of the pair
+ * emission.  0 keeps the library's choice (as many as fit on an SM for the
+ * persistent kernels, 4 for the emission); larger values than fit are
+ * clamped to what fits.  None of them changes a result bit except through
+ * the order of the reverse pass's floating-point atomics.  Process-wide and
+ * read when a call enqueues its kernels (a captured CUDA graph keeps the
+ * shapes of its capture).  gs_set_tuning(NULL) restores the defaults;
+ * negative values are GS_ERR_INVALID_ARG. */
+typedef struct gs_tuning {
+    int32_t fwd_ctas_per_sm;
+    int32_t bwd_ctas_per_sm;
+    int32_t sort_ctas_per_sm;
+    int32_t emit_ctas_per_sm;
+} gs_tuning;
+int gs_set_tuning(const gs_tuning *t);
+int gs_get_tuning(gs_tuning *t);
 
 /* --- the pass ---------------------------------------------------------- */
 
@@ -209,11 +237,15 @@ int gs_decode(const gs_anchors *A, const gs_camera *cams, const gs_view *views, 
  * argument.  The scratch lives in a static device array of 512 KiB that every
  * GPU loading this library keeps until the process exits; calls needing more
  * than ceil(N / 2048) * V <= 131072 counts return GS_ERR_CAPACITY at once and
- * enqueue nothing.  The first call on each device looks the array's device
- * address up (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  All calls on a device share the array, so
- * calls that overlap on the GPU race on it.  Nothing is allocated.  The paper
- * has no counterpart of this entry point. */
+ * enqueue nothing.  The array used is the one of the CURRENT device
+ * (cudaGetDevice): `stream` must belong to that device.  The first call on
+ * each device looks the array's device address up (cudaGetSymbolAddress) with
+ * that device current and keeps it for the life of the process; make that
+ * first call before any stream capture, and do not use this entry point on a
+ * device after cudaDeviceReset of that device in the same process (the kept
+ * address then refers to the old context).  All calls on a device share the
+ * array, so calls that overlap on the GPU race on it.  Nothing is allocated.
+ * The paper has no counterpart of this entry point. */
 int gs_decode_noalloc(const gs_anchors *A, const gs_camera *cams, const gs_view *views, int32_t V,
                       int32_t precision, gs_gauss3d *out, gs_status *status, void *stream);
 
@@ -228,7 +260,10 @@ int gs_decode_noalloc(const gs_anchors *A, const gs_camera *cams, const gs_view 
 int gs_project(const gs_gauss3d *g, const gs_camera *cams, const gs_view *views, int32_t V,
                gs_splats *out, gs_status *status, void *stream);
 
-/* Tile binning and sort: one pair per (covered tile, splat), ordered by
+/* Tile binning and sort of the tile-based differentiable rasterizer the
+ * paper renders with (Sec. II, the 3DGS rasterizer it builds on; Sec. III-A,
+ * Eq. 1 composites each pixel's splats front to back, so every tile needs
+ * its splats in depth order): one pair per (covered tile, splat), ordered by
  * (global tile, float bits of depth, splat id) -- exactly the order of a sort
  * on the 64-bit key (tile << 32 | depth bits) with ties broken by id.  Also
  * writes [start, end) per tile (empty tiles [0, 0)).  k and view_start as in
@@ -403,23 +438,28 @@ int gs_flow_triangulate(const gs_camera *cam1, const gs_camera *cam2, int32_t wi
                         int32_t *kept, float *points, int64_t cap, uint32_t *n_kept, void *ws, size_t ws_bytes,
                         gs_status *status, void *stream);
 
-/* Reverse of Eq. 1 and of the projection.  Per pixel, from the back: with
- * w_i = alpha_i T_i and B_i the colour composited behind splat i (plus
- * T_final bg), dL/dc_i = w_i g, dL/dalpha_i = g.(c_i T_i - B_i/(1 - alpha_i)),
- * then through alpha = o exp(power) (no gradient where the 0.99 clamp is
- * active) to mean and conic; per-splat sums are reduced across each warp
- * before global atomics.  Then the projection chain rule gives d mu, d scale,
- * d quat; d opacity, d colour pass through.  T_final/last: the forward's
- * optional outputs, or NULL to recompute them (tiles cut into several chunks
- * always use the per-chunk state the forward left in ws; chunk and ws must be
- * those of the forward).  sgrad: per-splat view-space
- * gradients (workspace-like output, overwritten).  out: overwritten for every
- * candidate (zeros for culled ones). */
+/* Reverse of Eq. 1 and of the projection.  With w_i = alpha_i T_i and B_i
+ * the colour composited behind splat i (plus T_final bg), dL/dc_i = w_i g and
+ * dL/dalpha_i = g.(c_i T_i - B_i/(1 - alpha_i)), then through alpha = o
+ * exp(power) (no gradient where the 0.99 clamp is active) to mean and conic;
+ * per-splat sums are reduced across each warp before global atomics.  Then
+ * the projection chain rule gives d mu, d scale, d quat; d opacity, d colour
+ * pass through.  Each pixel's list is walked front to back again: T_i and the
+ * colour composited up to splat i are recomputed with the forward's
+ * arithmetic (the forward's skip and stop decisions), and B_i is the pixel's
+ * final colour minus that prefix, so the forward stores nothing per pixel.
+ * image: the forward's output (device, same layout as d_image).  last: the
+ * forward's optional per-pixel output (1-based position of the last
+ * composited splat), or NULL to decide the stop rule again.  chunk and ws
+ * must be those of the forward, ws untouched since: tiles cut into several
+ * chunks start each chunk from the transmittance and colour prefix the
+ * forward left there.  sgrad: per-splat view-space gradients (workspace-like
+ * output, overwritten).  out: overwritten for every candidate (zeros for
+ * culled ones). */
 int gs_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *sp,
-                  const gs_bins *bins, const gs_view *views, int32_t V, const float *bg,
-                  int32_t chunk, void *ws, size_t ws_bytes, const float *d_image,
-                  const float *T_final, const int32_t *last, gs_splat_grad *sgrad,
-                  gs_gauss3d_grad *out, gs_status *status, void *stream);
+                  const gs_bins *bins, const gs_view *views, int32_t V, int32_t chunk, void *ws,
+                  size_t ws_bytes, const float *image, const float *d_image, const int32_t *last,
+                  gs_splat_grad *sgrad, gs_gauss3d_grad *out, gs_status *status, void *stream);
 
 /* Reverse of gs_decode, summed over views: through the activations (only for
  * candidates with opacity > 0), both MLP layers (hidden activations

@@ -67,6 +67,11 @@ class gs_adam_group(C.Structure):
     _fields_ = [("param", vp), ("grad", vp), ("m", vp), ("v", vp), ("n", i64), ("lr", C.c_float)]
 
 
+class gs_tuning(C.Structure):
+    _fields_ = [("fwd_ctas_per_sm", i32), ("bwd_ctas_per_sm", i32), ("sort_ctas_per_sm", i32),
+                ("emit_ctas_per_sm", i32)]
+
+
 GS_ADAM_MAX_GROUPS = 16
 DEFAULT_CHUNK = 384   # splats per compositing work item when gs_render_fwd gets chunk = 0
 
@@ -81,6 +86,9 @@ EXPORTS = {
     "gs_decode_bwd_workspace": (sz, [i32, i32, i32, i64]),
     "gs_status_string": (C.c_char_p, [i32]),
     "gs_kernel_launches": (C.c_uint64, []),
+    "gs_set_wait_limit": (i32, [i64]),
+    "gs_set_tuning": (i32, [P(gs_tuning)]),
+    "gs_get_tuning": (i32, [P(gs_tuning)]),
     "gs_probe_peak": (i32, [i32, i32, i32, vp, C.POINTER(C.c_int64), vp]),
     "gs_decode": (C.c_int, [P(gs_anchors), vp, P(gs_view), i32, i32, P(gs_gauss3d), vp, sz, vp, vp]),
     "gs_decode_noalloc": (C.c_int, [P(gs_anchors), vp, P(gs_view), i32, i32, P(gs_gauss3d), vp, vp]),
@@ -102,8 +110,7 @@ EXPORTS = {
                                       vp, vp]),
     "gs_photometric_loss": (C.c_int, [vp, vp, P(gs_view), i32, C.c_float, vp, sz, vp, vp, vp]),
     "gs_render_bwd": (C.c_int, [P(gs_gauss3d), vp, P(gs_splats), P(gs_bins), P(gs_view), i32,
-                                P(C.c_float), i32, vp, sz, vp, vp, vp, P(gs_splat_grad),
-                                P(gs_gauss3d_grad), vp, vp]),
+                                i32, vp, sz, vp, vp, vp, P(gs_splat_grad), P(gs_gauss3d_grad), vp, vp]),
     "gs_decode_bwd": (C.c_int, [P(gs_anchors), vp, P(gs_view), i32, i32, P(gs_gauss3d),
                                 P(gs_gauss3d_grad), P(gs_anchor_grad), vp, sz, vp, vp]),
 }

@@ -194,6 +194,35 @@ def new_status(device="cuda"):
     return torch.zeros(2, dtype=torch.int64, device=device)
 
 
+TUNING_FIELDS = ("fwd_ctas_per_sm", "bwd_ctas_per_sm", "sort_ctas_per_sm", "emit_ctas_per_sm")
+
+
+def set_tuning(tuning: dict | None):
+    """Launch shapes for later calls (gs_set_tuning); None or {} restores the
+    library's defaults, missing keys are 0 (the library's choice)."""
+    lib = L.load()
+    if not tuning:
+        L.check("gs_set_tuning", lib.gs_set_tuning(None))
+        return
+    unknown = set(tuning) - set(TUNING_FIELDS)
+    if unknown:
+        raise ValueError(f"unknown tuning keys {sorted(unknown)}")
+    t = L.gs_tuning(*(int(tuning.get(k, 0)) for k in TUNING_FIELDS))
+    L.check("gs_set_tuning", lib.gs_set_tuning(C.byref(t)))
+
+
+def get_tuning() -> dict:
+    t = L.gs_tuning()
+    L.check("gs_get_tuning", L.load().gs_get_tuning(C.byref(t)))
+    return {k: int(getattr(t, k)) for k in TUNING_FIELDS}
+
+
+def set_wait_limit(ns: int | None):
+    """Limit (ns) of the tensor-core kernels' MMA completion waits for later
+    calls; None restores the default (1 s), 0 gives up at the first wait."""
+    L.check("gs_set_wait_limit", L.load().gs_set_wait_limit(-1 if ns is None else int(ns)))
+
+
 def read_status(status):
     s = status.cpu().numpy()
     code = int(np.int32(s[0] & 0xFFFFFFFF))
@@ -355,16 +384,18 @@ def flow_triangulate(cams, wh, flow, samples, tau, kept, points, n_kept, ws, sta
                                                            _stream(stream)))
 
 
-def render_bwd(g: Gauss3D, sp: Splats, bins: Bins, views: Views, bg, d_image, sgrad, out: Gauss3DGrad,
-               status, ws, chunk=0, T_final=None, last=None, stream=None):
+def render_bwd(g: Gauss3D, sp: Splats, bins: Bins, views: Views, image, d_image, sgrad, out: Gauss3DGrad,
+               status, ws, chunk=0, last=None, stream=None):
+    """Reverse of the compositing and the projection.  image: the forward's
+    output; last: its optional per-pixel last composited position."""
     lib = L.load()
     gs_, s, b = g.struct(), sp.struct(), bins.struct()
     sg = L.gs_splat_grad(sgrad.data_ptr())
     o = out.struct()
     L.check("gs_render_bwd", lib.gs_render_bwd(C.byref(gs_), _ptr(views.cams), C.byref(s), C.byref(b),
-                                               views.ptr, views.V, _bg(bg), chunk, _ptr(ws), ws.numel(),
-                                               _ptr(d_image), _ptr(T_final), _ptr(last), C.byref(sg),
-                                               C.byref(o), _ptr(status), _stream(stream)))
+                                               views.ptr, views.V, chunk, _ptr(ws), ws.numel(), _ptr(image),
+                                               _ptr(d_image), _ptr(last), C.byref(sg), C.byref(o),
+                                               _ptr(status), _stream(stream)))
 
 
 def decode_bwd_workspace(anchors: Anchors, views: Views, cap_rows):

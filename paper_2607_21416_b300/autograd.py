@@ -105,6 +105,7 @@ class GsRender(torch.autograd.Function):
         sp = api.Splats.alloc(C_, dev)
         st = api.new_status(dev)
         api.project(g, views, sp, st)
+        _check(st, "gs_project")   # before the retries below reset the status word
         cap = max(renderer.cap_pairs, int(renderer.ppc * C_), 1024)
         for _ in range(4):
             bins = api.Bins.alloc(cap, views.total_tiles, dev)
@@ -123,17 +124,17 @@ class GsRender(torch.autograd.Function):
         ws = api.workspace(api.render_workspace(views, cap, renderer.chunk), dev)
         api.render_fwd(sp, bins, views, bg, image, st, ws, renderer.chunk, T_final, last)
         _check(st, "gs_render_fwd")
-        ctx.state = (g, sp, bins, ws, T_final, last, views, bg, renderer.chunk)
+        ctx.state = (g, sp, bins, ws, image, last, views, renderer.chunk)
         return image
 
     @staticmethod
     def backward(ctx, d_image):
-        g, sp, bins, ws, T_final, last, views, bg, chunk = ctx.state
+        g, sp, bins, ws, image, last, views, chunk = ctx.state
         dev = g.mu.device
         sgrad = torch.zeros(max(g.mu.shape[0], 1), 9, device=dev)
         out = api.Gauss3DGrad.like(g)
         st = api.new_status(dev)
-        api.render_bwd(g, sp, bins, views, bg, d_image.contiguous(), sgrad, out, st, ws, chunk, T_final, last)
+        api.render_bwd(g, sp, bins, views, image, d_image.contiguous(), sgrad, out, st, ws, chunk, last)
         _check(st, "gs_render_bwd")
         return out.dmu, out.dscale, out.dquat, out.dopacity, out.dcolour, None, None, None, None, None, None
 

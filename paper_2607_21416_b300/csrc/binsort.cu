@@ -545,7 +545,12 @@ struct SortLayout {
     int nb;
 };
 
-static int sort_blocks() { return std::min(1024, sm_count() * 4); }
+// CTAs of the sort and scan kernels: 4 per SM unless tuned (gs_set_tuning), at most 1024.
+static int sort_blocks()
+{
+    const int per_sm = tuning().sort_ctas_per_sm > 0 ? tuning().sort_ctas_per_sm : 4;
+    return std::max(1, std::min(1024, sm_count() * per_sm));
+}
 
 static SortLayout layout(long long cap_cand, long long cap_pairs)
 {
@@ -632,7 +637,8 @@ int launch_bin_sort(const gs_splats *sp, int k, const int32_t *view_start, long 
     uint32_t *ok = tk_b, *ov = (passes % 2 == 0) ? tv_b : bins->vals;
     pair_offsets_kernel<<<nb, kSortThreads, 0, s>>>(ids_s, n_splats, sp->tiles, sums, offs, rfirst, L.max_rounds,
                                                     cap_cand, st);
-    emit_pairs_kernel<<<sm_count() * 4, kSortThreads, 0, s>>>(ids_s, n_splats, n_pairs, offs, rfirst, rec,
+    const int emit_per_sm = tuning().emit_ctas_per_sm > 0 ? std::min(tuning().emit_ctas_per_sm, 8) : 4;
+    emit_pairs_kernel<<<sm_count() * emit_per_sm, kSortThreads, 0, s>>>(ids_s, n_splats, n_pairs, offs, rfirst, rec,
                                                               view_start, k, ek, ev, vt, cap_cand, st);
     count_launches(4);
     // 4. stable sort on the tile id

@@ -310,7 +310,7 @@ int launch_decode(const gs_anchors *A, const gs_camera *cams, const ViewTable &v
     a.N = N; a.F = A->F; a.k = A->k; a.H = A->hidden; a.M = A->M; a.V = V;
     a.cams = cams; a.view_start = out->view_start; a.row_anchor = out->row_anchor;
     a.mu = out->mu; a.scale = out->scale; a.quat = out->quat; a.opacity = out->opacity;
-    a.colour = out->colour; a.st = st; a.cap_rows = out->cap_rows;
+    a.colour = out->colour; a.st = st; a.cap_rows = out->cap_rows; a.wait_ns = wait_limit_ns();
     if (precision == GS_PREC_BF16) return launch_decode_bf16(a, s);
     const int nt = 128;
     const size_t smem = (size_t)(A->F + 4 + A->hidden) * nt * sizeof(float);

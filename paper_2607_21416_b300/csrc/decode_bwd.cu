@@ -278,7 +278,7 @@ int launch_decode_bwd(const gs_anchors *A, const gs_camera *cams, const ViewTabl
     f.part = A->part; f.mlp = A->mlp; f.mlp_floats = P; f.N = A->N; f.F = A->F; f.k = A->k; f.H = A->hidden;
     f.M = A->M; f.V = vt.V; f.cams = cams; f.view_start = g->view_start; f.row_anchor = g->row_anchor;
     f.mu = g->mu; f.scale = g->scale; f.quat = g->quat; f.opacity = g->opacity; f.colour = g->colour;
-    f.st = st; f.cap_rows = g->cap_rows;
+    f.st = st; f.cap_rows = g->cap_rows; f.wait_ns = wait_limit_ns();
     a.dmu = dg->dmu; a.dscale = dg->dscale; a.dquat = dg->dquat; a.dopacity = dg->dopacity; a.dcolour = dg->dcolour;
     a.dxyz = out->dxyz; a.dfeat = out->dfeat; a.dls = out->dlog_scaling; a.doff = out->doffsets; a.dmlp = out->dmlp;
     if (precision == GS_PREC_BF16) return launch_decode_bwd_bf16(a, s);

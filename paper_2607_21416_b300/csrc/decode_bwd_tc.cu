@@ -212,7 +212,7 @@ __device__ void tb_flush(const TbShape &s, uint32_t tmem, float *__restrict__ g)
 // Issues the MMAs of one step from thread 0 and waits for them (bounded);
 // false (uniformly over the CTA) if the wait ran out.
 template <typename F>
-__device__ __forceinline__ bool tb_mma_step(uint64_t *bar, uint32_t &phase, F issue)
+__device__ __forceinline__ bool tb_mma_step(uint64_t *bar, uint32_t &phase, unsigned long long wait_ns, F issue)
 {
     tc::fence_async_smem();
     tc::fence_before_sync();
@@ -222,7 +222,7 @@ __device__ __forceinline__ bool tb_mma_step(uint64_t *bar, uint32_t &phase, F is
         issue();
         tc::mma_commit(bar);
     }
-    const bool ok = tc::mbar_wait(bar, phase);
+    const bool ok = tc::mbar_wait(bar, phase, wait_ns);
     if (__syncthreads_or(!ok)) return false;
     phase ^= 1u;
     tc::fence_after_sync();
@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(kBThreads) decode_bwd_tc_kernel(DecodeBwdArgsB
             const bool mine = !done && pm == p;
 
             // ---- 1. PRE (split BF16)
-            if (!tb_mma_step(&bar, phase, [&] {
+            if (!tb_mma_step(&bar, phase, f.wait_ns, [&] {
                     const uint32_t id = tc::idesc_bf16(kBRows, s.N1);
                     const uint32_t sbo = s.KP * 16;
                     for (int ks = 0; ks < s.KP / 16; ++ks) {
@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(kBThreads) decode_bwd_tc_kernel(DecodeBwdArgsB
                 put8_bf16(sm + s.o_HX, tc::kmajor_offset(tid, s.N1 + 8, s.NH1), zero);
             }
             // ---- Z_oc = HID[:, 0:2H] W2oc^T
-            if (!tb_mma_step(&bar, phase, [&] {
+            if (!tb_mma_step(&bar, phase, f.wait_ns, [&] {
                     const uint32_t id = tc::idesc_bf16(kBRows, s.Noc), sbo = s.NH1 * 16;
                     for (int ks = 0; ks < 2 * H / 16; ++ks)
                         tc::mma_bf16(tmem, tc::sdesc(sHX + 256 * ks, 128, sbo),
@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(kBThreads) decode_bwd_tc_kernel(DecodeBwdArgsB
                 put8_bf16(sm + s.o_A, tc::kmajor_offset(tid, 16 * cc + 8, s.NZ), dz + 8);
             }
             {
-                const bool ok = tc::mbar_wait(&bar, phase);
+                const bool ok = tc::mbar_wait(&bar, phase, f.wait_ns);
                 if (__syncthreads_or(!ok)) { failed = true; break; }
                 phase ^= 1u;
                 tc::fence_after_sync();
@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(kBThreads) decode_bwd_tc_kernel(DecodeBwdArgsB
             }
             // ---- 4. dHID = dZ W2 (W2 read MN-major); dW2 += dZ^T [HID | 1]
             const uint32_t acc = fresh ? 0u : 1u;
-            if (!tb_mma_step(&bar, phase, [&] {
+            if (!tb_mma_step(&bar, phase, f.wait_ns, [&] {
                     const uint32_t ioc = tc::idesc_bf16(kBRows, 2 * H, 0, 1), icov = tc::idesc_bf16(kBRows, H, 0, 1);
                     const uint32_t zsbo = s.NZ * 16;
                     for (int ks = 0; ks < s.Noc / 16; ++ks)
@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(kBThreads) decode_bwd_tc_kernel(DecodeBwdArgsB
                 put8_bf16(sm + s.o_A, tc::kmajor_offset(tid, c + 8, s.N1), v + 8);
             }
             // dU = dPRE W1 (W1 read MN-major); dW1 += dPRE^T [U | 1]
-            if (!tb_mma_step(&bar, phase, [&] {
+            if (!tb_mma_step(&bar, phase, f.wait_ns, [&] {
                     const uint32_t iu = tc::idesc_bf16(kBRows, s.KP, 0, 1), psbo = s.N1 * 16, usbo = s.KP * 16;
                     for (int ks = 0; ks < s.N1 / 16; ++ks)
                         tc::mma_bf16(tmem, tc::sdesc(sA + 256 * ks, 128, psbo), tc::sdesc(sW1h + 2 * ks * usbo, usbo, 128),
@@ -541,7 +541,7 @@ __global__ void __launch_bounds__(kBThreads) decode_bwd_tc_kernel(DecodeBwdArgsB
     }
     if (failed) {
         if (tid == 0) set_error(f.st, GS_ERR_TIMEOUT, 65);
-        tc::mbar_wait(&bar, phase);   // MMAs still in flight (bounded)
+        tc::mbar_wait(&bar, phase);   // MMAs still in flight (bounded by the default limit)
     } else {
         tc::fence_before_sync();
         __syncthreads();

@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(kTThreads) decode_tc_kernel(DecodeArgs a, TcSh
                                  id, ks > 0);
                 tc::mma_commit(&bar);
             }
-            bool ok = tc::mbar_wait(&bar, phase);
+            bool ok = tc::mbar_wait(&bar, phase, a.wait_ns);
             if (__syncthreads_or(!ok)) { failed = true; break; }
             phase ^= 1u;
             tc::fence_after_sync();
@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(kTThreads) decode_tc_kernel(DecodeArgs a, TcSh
                                  tc::sdesc(sW2cov + 256 * ks, 128, H * 16), icov, ks > 0);
                 tc::mma_commit(&bar);
             }
-            ok = tc::mbar_wait(&bar, phase);
+            ok = tc::mbar_wait(&bar, phase, a.wait_ns);
             if (__syncthreads_or(!ok)) { failed = true; break; }
             phase ^= 1u;
             tc::fence_after_sync();
@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(kTThreads) decode_tc_kernel(DecodeArgs a, TcSh
     }
     if (failed) {
         if (tid == 0) set_error(a.st, GS_ERR_TIMEOUT, 15);
-        tc::mbar_wait(&bar, phase);   // MMAs still in flight (bounded)
+        tc::mbar_wait(&bar, phase);   // MMAs still in flight (bounded by the default limit)
     }
     tc::fence_before_sync();
     __syncthreads();

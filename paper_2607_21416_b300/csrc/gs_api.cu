@@ -2,6 +2,7 @@
 // tables and dispatch to the kernels.  Nothing here allocates or syncs.
 #include <atomic>
 #include <cstring>
+#include <mutex>
 
 #include "gs_internal.cuh"
 
@@ -34,6 +35,17 @@ bool make_view_table(const gs_view *views, int V, ViewTable *vt)
 
 static std::atomic<unsigned long long> g_launches{0};
 void count_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+
+static std::atomic<unsigned long long> g_wait_ns{kDefaultWaitNs};
+unsigned long long wait_limit_ns() { return g_wait_ns.load(std::memory_order_relaxed); }
+
+static std::mutex g_tuning_mu;
+static gs_tuning g_tuning{0, 0, 0, 0};
+gs_tuning tuning()
+{
+    std::lock_guard<std::mutex> lock(g_tuning_mu);
+    return g_tuning;
+}
 
 int sm_count()
 {
@@ -71,6 +83,28 @@ static bool check_gauss(const gs_gauss3d *g)
 extern "C" {
 
 uint64_t gs_kernel_launches(void) { return (uint64_t)g_launches.load(std::memory_order_relaxed); }
+
+int gs_set_tuning(const gs_tuning *t)
+{
+    if (t && (t->fwd_ctas_per_sm < 0 || t->bwd_ctas_per_sm < 0 || t->sort_ctas_per_sm < 0 || t->emit_ctas_per_sm < 0))
+        return GS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_tuning_mu);
+    g_tuning = t ? *t : gs_tuning{0, 0, 0, 0};
+    return GS_OK;
+}
+
+int gs_get_tuning(gs_tuning *t)
+{
+    if (!t) return GS_ERR_INVALID_ARG;
+    *t = tuning();
+    return GS_OK;
+}
+
+int gs_set_wait_limit(int64_t ns)
+{
+    g_wait_ns.store(ns < 0 ? kDefaultWaitNs : (unsigned long long)ns, std::memory_order_relaxed);
+    return GS_OK;
+}
 
 int64_t gs_mlp_floats(int32_t F, int32_t k, int32_t hidden)
 {
@@ -284,22 +318,22 @@ int gs_flow_triangulate(const gs_camera *cam1, const gs_camera *cam2, int32_t wi
 }
 
 int gs_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *sp, const gs_bins *bins,
-                  const gs_view *views, int32_t V, const float *bg, int32_t chunk, void *ws, size_t ws_bytes,
-                  const float *d_image, const float *T_final, const int32_t *last, gs_splat_grad *sgrad,
-                  gs_gauss3d_grad *out, gs_status *status, void *stream)
+                  const gs_view *views, int32_t V, int32_t chunk, void *ws, size_t ws_bytes, const float *image,
+                  const float *d_image, const int32_t *last, gs_splat_grad *sgrad, gs_gauss3d_grad *out,
+                  gs_status *status, void *stream)
 {
     ViewTable vt;
     if (!check_gauss(g) || !cams || !sp || !sp->rec || !sp->tiles || !bins || !bins->vals || !bins->ranges ||
-        !bins->n_pairs || !bg || !d_image || !sgrad || !sgrad->g || !out || !out->dmu || !out->dscale ||
+        !bins->n_pairs || !image || !d_image || !sgrad || !sgrad->g || !out || !out->dmu || !out->dscale ||
         !out->dquat || !out->dopacity || !out->dcolour || !status || !make_view_table(views, V, &vt) ||
-        (T_final == nullptr) != (last == nullptr) || sp->cap < g->cap_rows * (long long)g->k)
+        sp->cap < g->cap_rows * (long long)g->k)
         return GS_ERR_INVALID_ARG;
     if ((chunk != 0 && (chunk < 256 || chunk > (1 << 24))) || !ws ||
         (reinterpret_cast<uintptr_t>(ws) & 255) != 0 ||
         ws_bytes < render_workspace_bytes(vt, bins->cap_pairs, chunk_len(chunk)))
         return GS_ERR_INVALID_ARG;
-    return launch_render_bwd(g, cams, sp, bins, vt, bg, chunk_len(chunk), ws, d_image, T_final, last, sgrad, out,
-                             status, (cudaStream_t)stream);
+    return launch_render_bwd(g, cams, sp, bins, vt, chunk_len(chunk), ws, image, d_image, last, sgrad, out, status,
+                             (cudaStream_t)stream);
 }
 
 int gs_decode_bwd(const gs_anchors *A, const gs_camera *cams, const gs_view *views, int32_t V, int32_t precision,

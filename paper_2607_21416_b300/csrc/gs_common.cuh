@@ -121,4 +121,12 @@ int sm_count();
 // Host-side count of kernels this library has launched (gs_kernel_launches).
 void count_launches(int n);
 
+// Limit in nanoseconds of the tensor-core kernels' waits for their MMAs
+// (gs_set_wait_limit; 1 s unless changed).
+constexpr unsigned long long kDefaultWaitNs = 1000000000ull;
+unsigned long long wait_limit_ns();
+
+// Launch shapes of gs_set_tuning (0: the library's choice).
+gs_tuning tuning();
+
 }  // namespace gs

@@ -19,6 +19,7 @@ struct DecodeArgs {
     float *mu, *scale, *quat, *opacity, *colour;
     gs_status *st;
     long long cap_rows;
+    unsigned long long wait_ns;   // limit of the tensor-core kernels' MMA completion waits
 };
 
 struct DecodeBwdArgsB {
@@ -70,9 +71,9 @@ int launch_densify_masks(long long N, int k, const float *grad_accum, const int3
 int launch_photometric(const float *image, const float *target, const ViewTable &vt, float lam, void *ws,
                        float *loss, float *d_image, cudaStream_t s);
 int launch_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *sp, const gs_bins *bins,
-                      const ViewTable &vt, const float bg[3], int L, void *ws, const float *d_image,
-                      const float *T_final, const int32_t *last, gs_splat_grad *sgrad, gs_gauss3d_grad *out,
-                      gs_status *st, cudaStream_t s);
+                      const ViewTable &vt, int L, void *ws, const float *image, const float *d_image,
+                      const int32_t *last, gs_splat_grad *sgrad, gs_gauss3d_grad *out, gs_status *st,
+                      cudaStream_t s);
 
 size_t decode_bwd_workspace_bytes(int N, int V, int M, long long cap_rows);
 int launch_decode_bwd(const gs_anchors *A, const gs_camera *cams, const ViewTable &vt, int precision,

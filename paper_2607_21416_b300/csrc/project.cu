@@ -3,9 +3,13 @@
 // One thread per candidate (grid-stride over the device-side candidate count).
 // Each writes a 48-byte record (mean, conic, opacity, colour, depth, tile
 // rectangle) and its tile count; culled candidates get an empty rectangle.
-// The determinant and conic of near-degenerate splats (det < 1e-3 a c) are
-// taken in FP64; everything else is FP32.
-#include "gs_internal.cuh"
+// Near-degenerate splats (det < 1e-3 a c from the FP32 covariance) have
+// their covariance formed again in compensated single precision
+// (cov2d_f2.cuh) and its determinant and conic taken in FP64; everything
+// else is FP32.
+#include <cfloat>
+
+#include "cov2d_f2.cuh"
 
 namespace gs {
 
@@ -84,12 +88,17 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a, ViewTable v
             float det = ca * cc - cb * cb;
             float ka, kb, kc;
             if (det < 1e-3f * ca * cc) {
-                const double dd = (double)ca * (double)cc - (double)cb * (double)cb;
+                double da, db, dc;
+                cov2d_compensated(cm, mx_, my_, mz_, __ldg(a.quat + 4 * c), __ldg(a.quat + 4 * c + 1),
+                                  __ldg(a.quat + 4 * c + 2), __ldg(a.quat + 4 * c + 3), s0, s1, s2,
+                                  kTanClamp * (W / (2.f * cm.fx)), kTanClamp * (H / (2.f * cm.fy)), &da, &db, &dc);
+                const double dd = da * dc - db * db;
                 det = (float)dd;
                 if (dd > 0.0) {
-                    ka = (float)((double)cc / dd);
-                    kb = (float)(-(double)cb / dd);
-                    kc = (float)((double)ca / dd);
+                    ka = (float)(dc / dd);
+                    kb = (float)(-db / dd);
+                    kc = (float)(da / dd);
+                    if (!(det > 0.f)) det = FLT_MIN;   // positive, below FP32's normal range
                 }
                 if (!(dd > 0.0)) det = 0.f;
             } else {

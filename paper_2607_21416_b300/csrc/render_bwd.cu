@@ -1,13 +1,16 @@
 // render_bwd.cu -- reverse of the tile compositing (Eq. 1) over chunked work
 // items, and the chain rule of the projection.
 //
-// Per item and pixel the reverse traversal starts from the transmittance after
-// the item's last composited splat and the colour composited behind it, and
-// walks the chunk's list back to front.  Single-chunk tiles take those from the
-// forward's optional per-pixel output or recompute them (one extra front-to-back
-// pass over the tile); multi-chunk tiles read them from the per-chunk state the
-// forward left in the render workspace.  Per-splat sums are reduced across the
-// warp (shuffles) before one global atomicAdd per warp and quantity.
+// Per item and pixel the reverse traversal runs front to back, like the
+// forward: it recomputes the transmittance in front of each splat and the
+// colour composited so far with the forward's own arithmetic (so it takes the
+// forward's skip and stop decisions), and gets the colour behind a splat as
+// the pixel's final colour (the forward's image) minus that prefix.  Single-
+// chunk tiles need no per-pixel state from the forward; a later chunk of a
+// multi-chunk tile starts from the per-chunk state the forward left in the
+// render workspace.  Per-splat sums are reduced across the warp (shuffles)
+// before one global atomicAdd per warp and quantity.
+#include "cov2d_f2.cuh"
 #include "render_common.cuh"
 
 namespace gs {
@@ -46,16 +49,21 @@ __device__ __forceinline__ float warp_sum8(const float v[8])
     return r;
 }
 
-// Reverse state of one pixel: transmittance, S = g . (colour composited
-// behind the current splat, background included) with g = dL/dC of the pixel.
+// Reverse state of one pixel, carried front to back: T the transmittance in
+// front of the current splat, Sp = g . (colour composited up to and including
+// it), GC = g . (the pixel's final colour, background included) with g =
+// dL/dC of the pixel, so that g . B_i = GC - Sp_i is the colour behind splat i.
+// lim: last list position (1-based, in the item) the pixel may composite;
+// done: nothing left for the pixel in this item.
 struct PixBwd {
-    float T, S, g0, g1, g2;
-    int last;
+    float T, Sp, GC, g0, g1, g2;
+    int lim;
+    bool done;
 };
 
 // The alpha decision of Eq. 1 for one pixel (the forward's, operation for
-// operation): true iff the splat is composited at (px, py), with the offset
-// and the unclamped alpha o exp(power).
+// operation): true iff the splat passes the skip tests at (px, py), with the
+// offset and the unclamped alpha o exp(power).
 __device__ __forceinline__ bool alpha_test(const float4 a, const float4 bb, float px, float py, float *dx, float *dy,
                                            float *ag)
 {
@@ -65,29 +73,29 @@ __device__ __forceinline__ bool alpha_test(const float4 a, const float4 bb, floa
     return fminf(kAlphaMax, *ag) >= kAlphaMin;
 }
 
-// Gradient terms of one pixel for a staged splat it composites, added to the
+// Gradient terms of one pixel for a splat it composites, added to the
 // per-splat sums acc[9] = (m_x, m_y, m_xx, m_xy, m_yy, sum dal exp(power),
 // d r, d g, d b) with dp = dL/dpower and the moments m_x = sum dp dx, m_y =
 // sum dp dy, m_xx = sum dp dx^2, m_xy = sum dp dx dy, m_yy = sum dp dy^2 over
 // the pixels; after the warp reduction they become d mean2d and d conic
 // (conic_grads) and the opacity sum is divided by the opacity.  Eq. 1 gives,
 // for splat i with transmittance T_i in front of it, dC/dalpha_i = T_i c_i -
-// B_i / (1 - alpha_i) (B_i: colour behind i), so only the scalar S = g . B_i
-// is carried.  T and S are the pixel's reverse state, updated in place.
-__device__ __forceinline__ void bwd_composite(float &T, float &S, float g0, float g1, float g2, const float4 bb,
-                                              float cb, float dx, float dy, float ag, float acc[9])
+// B_i / (1 - alpha_i) (B_i: colour behind i, background included), and g . B_i
+// = GC - Sp_i.  T and Sp advance past the splat.
+__device__ __forceinline__ void bwd_composite(float &T, float &Sp, float Tn, float GC, float g0, float g1, float g2,
+                                              const float4 bb, float cb, float dx, float dy, float ag, float acc[9])
 {
     const float alpha = fminf(kAlphaMax, ag);
     float inv;                             // 1 / (1 - alpha) on the SFU (relative error ~2^-23; the
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(1.f - alpha));   // operand lies in [0.01, 1))
-    T = T * inv;                           // transmittance in front of this splat
     const float w = alpha * T;
     acc[6] = fmaf(w, g0, acc[6]);
     acc[7] = fmaf(w, g1, acc[7]);
     acc[8] = fmaf(w, g2, acc[8]);
     const float gc = fmaf(g0, bb.z, fmaf(g1, bb.w, g2 * cb));
-    const float dal = fmaf(gc, T, -S * inv);
-    S = fmaf(gc, w, S);
+    Sp = fmaf(gc, w, Sp);
+    const float dal = fmaf(gc, T, -(GC - Sp) * inv);
+    T = Tn;
     if (ag < kAlphaMax) {                  // the clamped branch passes no gradient to o exp(power)
         acc[5] = fmaf(dal, ag, acc[5]);
         const float dp = dal * alpha;      // d power (alpha = o exp(power))
@@ -131,137 +139,113 @@ __device__ __forceinline__ float conic_grads(const LaneRole &r, float total, flo
     return fmaf(cs, total, co * other);
 }
 
+// Reverse pass of one work unit (block `warp` of item b), front to back.  Per
+// pixel the traversal recomputes, splat by splat, the transmittance in front
+// of it and the colour composited so far -- the forward's own arithmetic, so
+// every skip / stop decision is the forward's -- and takes the colour behind
+// a splat as the pixel's final colour (the forward's image) minus that
+// prefix.  Nothing per pixel is stored by the forward for single-chunk tiles;
+// a later chunk of a multi-chunk tile starts from the transmittance in front
+// of it and the colour prefix of the chunk before (the per-chunk state) and
+// composites up to its last composited position.
 __device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const uint32_t *__restrict__ vals,
                                          const uint32_t *__restrict__ ranges, const ViewTable &vt,
-                                         const RenderPlan &plan, float bg0, float bg1, float bg2,
-                                         const float *__restrict__ d_image, const float *__restrict__ T_final_in,
-                                         const int32_t *__restrict__ last_in, float *__restrict__ sgrad,
-                                         long long cap_cand, const gs_status *st, int b, int warp, WarpStage &WSw)
+                                         const RenderPlan &plan, const float *__restrict__ image,
+                                         const float *__restrict__ d_image, const int32_t *__restrict__ last_in,
+                                         float *__restrict__ sgrad, long long cap_cand, const gs_status *st, int b,
+                                         int warp, WarpStage &WSw)
 {
     Item it;
     if (!item_of(b, plan.item_base, vt.total_tiles, ranges, plan.L, &it)) return;
     const int lane = threadIdx.x & 31, tid = warp * 32 + lane;
     const TileCoord tc = tile_coord(vt, it.t, tid);
-    // one composite pass per staged splat suffices where a lane composites it at one of its two
-    // pixels (lane_pixels); a second one runs only where a lane needs both
     const int v = tc.v;
     const long long W = vt.W[v], H = vt.H[v];
     const LanePix lpx = lane_pixels(tc, warp, lane, (int)W, (int)H);
     const int px0 = lpx.px0, py = lpx.py;
-    const bool in0 = lpx.in0, in1 = lpx.in1;
-    const int pid0 = lpx.pid0, pid1 = pid0 + 8;
+    const int pid0 = lpx.pid0;
     const float fx0 = (float)px0, fx1 = (float)(px0 + 8), fy = (float)py;
     const float bx0 = (float)tc.x0, bx1 = bx0 + (float)(kTile - 1);
     const float by0 = (float)(tc.y0 + 4 * warp), by1 = by0 + 3.f;
-    const long long pix0 = (long long)py * W + px0, pix1 = pix0 + 8;
+    const long long pix0 = (long long)py * W + px0;
     const int n_items = (int)(it.s1 - it.s0);
+    const bool multi = it.nk > 1;
     PixBwd p0, p1;
-    p0.T = p1.T = 1.f;
-    p0.S = p1.S = 0.f;
-    p0.last = p1.last = 0;
-    p0.g0 = p0.g1 = p0.g2 = p1.g0 = p1.g1 = p1.g2 = 0.f;
-    {
-        const float *dimg = d_image + 3 * vt.pix_base[v];
-        if (in0) { p0.g0 = dimg[pix0]; p0.g1 = dimg[W * H + pix0]; p0.g2 = dimg[2 * W * H + pix0]; }
-        if (in1) { p1.g0 = dimg[pix1]; p1.g1 = dimg[W * H + pix1]; p1.g2 = dimg[2 * W * H + pix1]; }
-    }
-    if (it.nk > 1) {
-        // forward state of the chunk: entering transmittance (activity), end
-        // transmittance, last position, colour composited behind it
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            PixBwd &ps = half ? p1 : p0;
-            const int pix = half ? pid1 : pid0;
+    for (int h = 0; h < 2; ++h) {
+        PixBwd &ps = h ? p1 : p0;
+        const bool in = h ? lpx.in1 : lpx.in0;
+        const long long pix = pix0 + 8 * h;
+        const int pid = pid0 + 8 * h;
+        ps.T = 1.f;
+        ps.Sp = ps.GC = ps.g0 = ps.g1 = ps.g2 = 0.f;
+        ps.lim = 0;
+        ps.done = true;
+        if (!in) continue;
+        const float *dimg = d_image + 3 * vt.pix_base[v];
+        const float *img = image + 3 * vt.pix_base[v];
+        ps.g0 = dimg[pix];
+        ps.g1 = dimg[W * H + pix];
+        ps.g2 = dimg[2 * W * H + pix];
+        ps.GC = fmaf(ps.g0, img[pix], fmaf(ps.g1, img[W * H + pix], ps.g2 * img[2 * W * H + pix]));
+        if (multi) {
             const int item = it.base + it.k;
-            const float T0 = state_plane(plan.state, item, 0)[pix];
-            if (T0 >= kTMin && (half ? in1 : in0)) {
-                ps.T = state_plane(plan.state, item, 1)[pix];
-                ps.last = reinterpret_cast<const int *>(state_plane(plan.state, item, 5))[pix];
-                // colour behind the chunk: final colour - prefix up to the chunk
-                const float B0 = state_plane(plan.state, it.base, 7)[pix] - state_plane(plan.state, item, 2)[pix];
-                const float B1 = state_plane(plan.state, it.base, 8)[pix] - state_plane(plan.state, item, 3)[pix];
-                const float B2 = state_plane(plan.state, it.base, 9)[pix] - state_plane(plan.state, item, 4)[pix];
-                ps.S = fmaf(ps.g0, B0, fmaf(ps.g1, B1, ps.g2 * B2));
-            } else {
-                ps.last = 0;
+            const float T0 = state_plane(plan.state, item, 0)[pid];
+            if (T0 >= kTMin) {   // active chunk: enter with its transmittance and the prefix in front of it
+                ps.T = T0;
+                ps.lim = min(reinterpret_cast<const int *>(state_plane(plan.state, item, 5))[pid], n_items);
+                if (it.k > 0)
+                    ps.Sp = fmaf(ps.g0, state_plane(plan.state, item - 1, 2)[pid],
+                                 fmaf(ps.g1, state_plane(plan.state, item - 1, 3)[pid],
+                                      ps.g2 * state_plane(plan.state, item - 1, 4)[pid]));
             }
+        } else {
+            ps.lim = last_in ? min(last_in[vt.pix_base[v] + pix], n_items) : n_items;
         }
-    } else if (T_final_in) {
-        if (in0) { p0.T = T_final_in[vt.pix_base[v] + pix0]; p0.last = min(last_in[vt.pix_base[v] + pix0], n_items); }
-        if (in1) { p1.T = T_final_in[vt.pix_base[v] + pix1]; p1.last = min(last_in[vt.pix_base[v] + pix1], n_items); }
-        p0.S = p0.T * fmaf(p0.g0, bg0, fmaf(p0.g1, bg1, p0.g2 * bg2));
-        p1.S = p1.T * fmaf(p1.g0, bg0, fmaf(p1.g1, bg1, p1.g2 * bg2));
-    } else {
-        // recompute the forward transmittance and the last composited position (per warp)
-        bool d0 = !in0, d1 = !in1;
-        for (uint32_t b0 = it.s0; b0 < it.s1; b0 += 32) {
-            if (__all_sync(0xffffffffu, d0 && d1)) break;
-            const uint32_t pos = b0 + lane;
-            const int cnt = warp_stage(WSw, rec, vals, pos, it.s0, pos < it.s1, cap_cand, st, 52, false, bx0, bx1,
-                                       by0, by1);
-            for (int e = 0; e < cnt; ++e) {
-                const float4 a = WSw.a[e];
-                const float4 bb = WSw.b[e];
-                const int q1 = WSw.pos[e] + 1;
-                float dx, dy;
-                if (!d0) {
-                    const float q = splat_q(a, bb.x, fx0, fy, &dx, &dy);
-                    if (q <= 0.f) {
-                        const float alpha = fminf(kAlphaMax, splat_alpha(q, bb.y));
-                        if (alpha >= kAlphaMin) {
-                            const float Tn = __fmul_rn(p0.T, 1.f - alpha);
-                            if (Tn < kTMin) d0 = true;
-                            else { p0.T = Tn; p0.last = q1; }
-                        }
-                    }
-                }
-                if (!d1) {
-                    const float q = splat_q(a, bb.x, fx1, fy, &dx, &dy);
-                    if (q <= 0.f) {
-                        const float alpha = fminf(kAlphaMax, splat_alpha(q, bb.y));
-                        if (alpha >= kAlphaMin) {
-                            const float Tn = __fmul_rn(p1.T, 1.f - alpha);
-                            if (Tn < kTMin) d1 = true;
-                            else { p1.T = Tn; p1.last = q1; }
-                        }
-                    }
-                }
-            }
-            __syncwarp();
-        }
-        p0.S = p0.T * fmaf(p0.g0, bg0, fmaf(p0.g1, bg1, p0.g2 * bg2));
-        p1.S = p1.T * fmaf(p1.g0, bg0, fmaf(p1.g1, bg1, p1.g2 * bg2));
+        ps.done = ps.lim <= 0;
     }
-    // back to front over the warp's chunk positions [0, maxlast), 32 at a time
     const int vi = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
     const LaneRole role = lane_role(vi);
-    const int maxlast = min(__reduce_max_sync(0xffffffffu, max(p0.last, p1.last)), n_items);
-    for (int hi = maxlast; hi > 0; hi -= 32) {
-        const int pl = hi - 1 - lane;   // lane l <-> position hi - 1 - l: hits come back to front
-        const int cnt = warp_stage(WSw, rec, vals, it.s0 + (uint32_t)max(pl, 0), it.s0, pl >= 0, cap_cand, st, 53,
-                                   true, bx0, bx1, by0, by1);
+    const int maxlim = __reduce_max_sync(0xffffffffu, max(p0.done ? 0 : p0.lim, p1.done ? 0 : p1.lim));
+    // the forward's stop rule is decided again here for single-chunk tiles (unless `last` is given);
+    // chunks of longer lists composite up to their recorded last position
+    const bool stop_rule = !multi && !last_in;
+    for (int b0 = 0; b0 < maxlim; b0 += 32) {
+        if (__all_sync(0xffffffffu, p0.done && p1.done)) break;
+        const int pl = b0 + lane;
+        const int cnt = warp_stage<true, true>(WSw, rec, vals, it.s0 + (uint32_t)pl, it.s0, pl < maxlim, cap_cand,
+                                               st, 53, bx0, bx1, by0, by1);
         for (int e = 0; e < cnt; ++e) {
-            const int p = WSw.pos[e];
+            const int q1 = WSw.pos[e] + 1;
             const float4 a = WSw.a[e];
             const float4 bb = WSw.b[e];
+            const int hm = WSw.half[e];
             float dx0 = 0.f, dy0 = 0.f, ag0 = 0.f, dx1 = 0.f, dy1 = 0.f, ag1 = 0.f;
-            const bool c0 = p < p0.last && alpha_test(a, bb, fx0, fy, &dx0, &dy0, &ag0);
-            const bool c1 = p < p1.last && alpha_test(a, bb, fx1, fy, &dx1, &dy1, &ag1);
+            bool c0 = (hm & 1) && !p0.done && q1 <= p0.lim && alpha_test(a, bb, fx0, fy, &dx0, &dy0, &ag0);
+            bool c1 = (hm & 2) && !p1.done && q1 <= p1.lim && alpha_test(a, bb, fx1, fy, &dx1, &dy1, &ag1);
+            // transmittance behind the splat, rounded as the forward rounds it
+            const float Tn0 = __fmul_rn(p0.T, 1.f - fminf(kAlphaMax, ag0));
+            const float Tn1 = __fmul_rn(p1.T, 1.f - fminf(kAlphaMax, ag1));
+            if (stop_rule) {
+                if (c0 && Tn0 < kTMin) { p0.done = true; c0 = false; }
+                if (c1 && Tn1 < kTMin) { p1.done = true; c1 = false; }
+            }
             const bool contrib = c0 || c1;
             if (!__any_sync(0xffffffffu, contrib)) continue;
             float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             const float cb = WSw.c[e];
             {   // pixel 0 where it composites the splat, else pixel 1
                 const bool u1 = !c0;
-                float T = u1 ? p1.T : p0.T, S = u1 ? p1.S : p0.S;
+                float T = u1 ? p1.T : p0.T, Sp = u1 ? p1.Sp : p0.Sp;
                 if (contrib) {
-                    bwd_composite(T, S, u1 ? p1.g0 : p0.g0, u1 ? p1.g1 : p0.g1, u1 ? p1.g2 : p0.g2, bb, cb,
-                                  u1 ? dx1 : dx0, u1 ? dy1 : dy0, u1 ? ag1 : ag0, acc);
-                    if (u1) { p1.T = T; p1.S = S; } else { p0.T = T; p0.S = S; }
+                    bwd_composite(T, Sp, u1 ? Tn1 : Tn0, u1 ? p1.GC : p0.GC, u1 ? p1.g0 : p0.g0,
+                                  u1 ? p1.g1 : p0.g1, u1 ? p1.g2 : p0.g2, bb, cb, u1 ? dx1 : dx0, u1 ? dy1 : dy0,
+                                  u1 ? ag1 : ag0, acc);
+                    if (u1) { p1.T = T; p1.Sp = Sp; } else { p0.T = T; p0.Sp = Sp; }
                 }
             }
             if (__any_sync(0xffffffffu, c0 && c1) && c0 && c1)   // a lane that composites it at both pixels
-                bwd_composite(p1.T, p1.S, p1.g0, p1.g1, p1.g2, bb, cb, dx1, dy1, ag1, acc);
+                bwd_composite(p1.T, p1.Sp, Tn1, p1.GC, p1.g0, p1.g1, p1.g2, bb, cb, dx1, dy1, ag1, acc);
             {
                 const float t8 = warp_sum8(acc);
                 const float t9 = warp_sum(acc[8]);
@@ -273,6 +257,9 @@ __device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const u
             }
         }
         __syncwarp();
+        // pixels whose last position lies in this batch are finished
+        if (p0.lim <= b0 + 32) p0.done = true;
+        if (p1.lim <= b0 + 32) p1.done = true;
     }
 }
 
@@ -280,9 +267,8 @@ __device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const u
 // counter and runs block w of item i.
 __global__ void __launch_bounds__(kRThreads) render_bwd_kernel(
     const float4 *__restrict__ rec, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
-    ViewTable vt, RenderPlan plan, float bg0, float bg1, float bg2, const float *__restrict__ d_image,
-    const float *__restrict__ T_final_in, const int32_t *__restrict__ last_in, float *__restrict__ sgrad,
-    long long cap_cand, const gs_status *st)
+    ViewTable vt, RenderPlan plan, const float *__restrict__ image, const float *__restrict__ d_image,
+    const int32_t *__restrict__ last_in, float *__restrict__ sgrad, long long cap_cand, const gs_status *st)
 {
     if (has_error(st)) return;
     __shared__ WarpStage WS[kRThreads / 32];
@@ -290,8 +276,7 @@ __global__ void __launch_bounds__(kRThreads) render_bwd_kernel(
     const int n_units = 4 * __ldg(plan.item_base + vt.total_tiles);
     int32_t *counter = plan.counters + 2;
     for (int u = next_unit(counter); u < n_units; u = next_unit(counter))
-        bwd_unit(rec, vals, ranges, vt, plan, bg0, bg1, bg2, d_image, T_final_in, last_in, sgrad, cap_cand, st, u >> 2,
-                 u & 3, W);
+        bwd_unit(rec, vals, ranges, vt, plan, image, d_image, last_in, sgrad, cap_cand, st, u >> 2, u & 3, W);
 }
 
 // Projection chain rule, one thread per candidate.
@@ -368,8 +353,9 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(ProjBwdArgs a, ViewTab
             const float cc = TS[3] * T[3] + TS[4] * T[4] + TS[5] * T[5] + kLowpass;
             float da, db, dcv;
             const float det = ca * cc - cb * cb;
-            if (det < 1e-3f * ca * cc) {
-                const double A = ca, Bv = cb, Cv = cc;
+            if (det < 1e-3f * ca * cc) {   // near-degenerate: the forward's compensated covariance, FP64 inverse
+                double A, Bv, Cv;
+                cov2d_compensated(cm, m0, m1, m2, qw, qx, qy, qz, s[0], s[1], s[2], limx, limy, &A, &Bv, &Cv);
                 const double dd = A * Cv - Bv * Bv, d2 = dd * dd;
                 da = (float)((gka * (-Cv * Cv) + gkb * (Bv * Cv) + gkc * (-Bv * Bv)) / d2);
                 db = (float)((gka * (2 * Bv * Cv) + gkb * (-(A * Cv + Bv * Bv)) + gkc * (2 * A * Bv)) / d2);
@@ -448,9 +434,9 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(ProjBwdArgs a, ViewTab
 
 // ------------------------------------------------------------ launcher
 int launch_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *sp, const gs_bins *bins,
-                      const ViewTable &vt, const float bg[3], int L, void *ws, const float *d_image,
-                      const float *T_final, const int32_t *last, gs_splat_grad *sgrad, gs_gauss3d_grad *out,
-                      gs_status *st, cudaStream_t s)
+                      const ViewTable &vt, int L, void *ws, const float *image, const float *d_image,
+                      const int32_t *last, gs_splat_grad *sgrad, gs_gauss3d_grad *out, gs_status *st,
+                      cudaStream_t s)
 {
     const long long cap_cand = g->cap_rows * (long long)g->k;
     cudaMemsetAsync(sgrad->g, 0, sizeof(float) * 9 * (size_t)cap_cand, s);
@@ -458,9 +444,9 @@ int launch_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splat
     if (vt.total_tiles > 0) {
         const RenderPlan plan = render_plan(vt, bins->cap_pairs, L, ws);
         cudaMemsetAsync(plan.counters + 2, 0, sizeof(int32_t), s);
-        render_bwd_kernel<<<persistent_grid((const void *)render_bwd_kernel), kRThreads, 0, s>>>(rec, bins->vals, bins->ranges, vt, plan, bg[0], bg[1],
-                                                          bg[2], d_image, T_final, last, sgrad->g,
-                                                          std::min<long long>(sp->cap, cap_cand), st);
+        render_bwd_kernel<<<persistent_grid((const void *)render_bwd_kernel, tuning().bwd_ctas_per_sm), kRThreads, 0, s>>>(
+            rec, bins->vals, bins->ranges, vt, plan, image, d_image, last, sgrad->g,
+            std::min<long long>(sp->cap, cap_cand), st);
         count_launches(1);
     }
     ProjBwdArgs a;

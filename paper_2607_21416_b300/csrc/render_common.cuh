@@ -174,9 +174,12 @@ __device__ __forceinline__ bool meets_block(float4 a, float4 b, float bx0, float
 // Reads list position `pos` of the item (when valid) and tests it against the
 // warp's block; the hits are compacted into the warp's stage in list order
 // (lane order).  Returns the number of hits.
+// IO: also stage 1 / opacity (the reverse pass); HALF: also stage which 8-column
+// halves of the block the splat's alpha box meets.
+template <bool IO, bool HALF>
 __device__ __forceinline__ int warp_stage(WarpStage &W, const float4 *__restrict__ rec,
                                           const uint32_t *__restrict__ vals, uint32_t pos, uint32_t s0, bool valid,
-                                          long long cap_cand, const gs_status *st, int site, bool backward,
+                                          long long cap_cand, const gs_status *st, int site,
                                           float bx0, float bx1, float by0, float by1)
 {
     const int lane = threadIdx.x & 31;
@@ -198,14 +201,13 @@ __device__ __forceinline__ int warp_stage(WarpStage &W, const float4 *__restrict
         W.a[slot] = a;
         W.b[slot] = b;
         W.c[slot] = __ldg(reinterpret_cast<const float *>(&rec[3 * (size_t)id + 2]));
-        if (backward) W.io[slot] = exp2f(-b.y);
+        if (IO) W.io[slot] = exp2f(-b.y);
         W.id[slot] = id;
         W.pos[slot] = (int)(pos - s0);
-        // forward: which 8-column half of the block the box meets.  A lane's first pixel lies in the
-        // left half and its second in the right one (lane_pixels), so a pixel of a half the box
-        // misses fails the alpha test as the kernels evaluate it and is skipped (same test as
-        // above).  The reverse pass does not use it: there the extra tests cost more than they save.
-        if (!backward)
+        // which 8-column half of the block the box meets.  A lane's first pixel lies in the left
+        // half and its second in the right one (lane_pixels), so a pixel of a half the box misses
+        // fails the alpha test as the kernels evaluate it and is skipped (same test as above).
+        if (HALF)
             W.half[slot] = (meets_block(a, b, bx0, bx0 + 7.f, by0, by1) ? 1 : 0) |
                            (meets_block(a, b, bx0 + 8.f, bx1, by0, by1) ? 2 : 0);
     }
@@ -235,7 +237,8 @@ struct RenderPlan {
 RenderPlan render_plan(const ViewTable &vt, long long cap_pairs, int L, void *ws);
 
 // CTAs of 128 threads of a persistent compositing kernel that fit on the
-// device at once (registers, shared memory, warps), times the SM count.
-int persistent_grid(const void *kernel);
+// device at once (registers, shared memory, warps), at most cap_per_sm per
+// SM when cap_per_sm > 0, times the SM count.
+int persistent_grid(const void *kernel, int cap_per_sm = 0);
 
 }  // namespace gs

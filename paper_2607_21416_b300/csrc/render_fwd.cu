@@ -189,8 +189,8 @@ __device__ __forceinline__ void chunk_unit(const float4 *__restrict__ rec, const
     for (uint32_t b0 = it.s0; b0 < it.s1; b0 += 32) {
         if (__all_sync(0xffffffffu, p0.done && p1.done)) break;
         const uint32_t pos = b0 + lane;
-        const int cnt = warp_stage(W, rec, vals, pos, it.s0, pos < it.s1, cap_cand, st, 42, false, bx0, bx1, by0,
-                                   by1);
+        const int cnt = warp_stage<false, true>(W, rec, vals, pos, it.s0, pos < it.s1, cap_cand, st, 42, bx0, bx1,
+                                                 by0, by1);
         if (exact) {
             for (int e = 0; e < cnt; ++e) {
                 const float4 a = W.a[e];
@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(2 * kRThreads) combine_kernel(const uint32_t *
     if (COUNT) count_add(n_eval, nev, ncomp);
 }
 
-int persistent_grid(const void *kernel)
+int persistent_grid(const void *kernel, int cap_per_sm)
 {
     static int dev_smem = 0, dev_reserve = 0;
     if (dev_smem == 0) {
@@ -421,6 +421,7 @@ int persistent_grid(const void *kernel)
     int occ = 64 / (kRThreads / 32);                                             // warps per SM
     occ = std::min(occ, 65536 / std::max(1, fa.numRegs * kRThreads));           // registers
     occ = std::min(occ, dev_smem / std::max(1, (int)fa.sharedSizeBytes + dev_reserve));
+    if (cap_per_sm > 0) occ = std::min(occ, cap_per_sm);
     return sm_count() * std::max(1, occ);
 }
 
@@ -480,12 +481,12 @@ static void launch_items(const float4 *rec, const gs_bins *bins, const ViewTable
                          const float bg[3], float *image, float *T_final, int32_t *last, unsigned long long *n_eval,
                          long long cap, gs_status *st, cudaStream_t s)
 {
-    chunk_kernel<COUNT, false><<<persistent_grid((const void *)chunk_kernel<COUNT, false>), kRThreads, 0, s>>>(rec, bins->vals, bins->ranges, vt, plan, bg[0],
+    chunk_kernel<COUNT, false><<<persistent_grid((const void *)chunk_kernel<COUNT, false>, tuning().fwd_ctas_per_sm), kRThreads, 0, s>>>(rec, bins->vals, bins->ranges, vt, plan, bg[0],
                                                                    bg[1], bg[2], image, T_final, last, n_eval, cap,
                                                                    st);
     combine_kernel<COUNT><<<vt.total_tiles, 2 * kRThreads, 0, s>>>(bins->ranges, vt, plan, bg[0], bg[1], bg[2], image,
                                                               T_final, last, n_eval, st);
-    chunk_kernel<COUNT, true><<<persistent_grid((const void *)chunk_kernel<COUNT, true>), kRThreads, 0, s>>>(rec, bins->vals, bins->ranges, vt, plan, bg[0],
+    chunk_kernel<COUNT, true><<<persistent_grid((const void *)chunk_kernel<COUNT, true>, tuning().fwd_ctas_per_sm), kRThreads, 0, s>>>(rec, bins->vals, bins->ranges, vt, plan, bg[0],
                                                                   bg[1], bg[2], image, T_final, last, n_eval, cap,
                                                                   st);
 }

@@ -121,10 +121,8 @@ class RenderPass:
         if self.ggrad is None or self.ggrad.dmu.shape[0] != self.g.mu.shape[0]:
             self.ggrad = api.Gauss3DGrad.like(self.g)
         dimg = self.d_image if d_image is None else d_image
-        api.render_bwd(self.g, self.splats, self.bins, self.views, self.bg, dimg, self.sgrad, self.ggrad,
-                       self.status, self.render_ws, self.chunk,
-                       self.T_final if self.store_state else None,
-                       self.last if self.store_state else None, stream)
+        api.render_bwd(self.g, self.splats, self.bins, self.views, self.image, dimg, self.sgrad, self.ggrad,
+                       self.status, self.render_ws, self.chunk, self.last if self.store_state else None, stream)
         if self.anchors is not None:
             api.decode_bwd(self.anchors, self.views, self.g, self.ggrad, self.agrad, self.dbwd_ws,
                            self.status, self.precision, stream)
@@ -176,7 +174,9 @@ class MappingStep:
     backward, no optimizer step) captured once into a CUDA graph and replayed.
 
     `prepare(target)` sizes the buffers with one host-synchronised eager pass
-    and captures the graph; `run()` replays it on device-resident inputs;
+    and captures the graph (with tune=True it first picks the chunk length
+    and launch shapes with `autotune.tune`, cached in `tune_cache`, and
+    captures with them); `run()` replays it on device-resident inputs;
     `step(target_host, cams_host)` is the end-to-end call: it copies the
     iteration's target images (and optionally cameras) from pinned host memory,
     replays the graph and reads back the loss and the status word (one stream
@@ -186,14 +186,19 @@ class MappingStep:
 
     def __init__(self, views: api.Views, anchors: api.Anchors, precision: int = L.GS_PREC_BF16,
                  cap_rows: int | None = None, store_state: bool = False, chunk: int = 0, device="cuda",
-                 loss: str = "l1", lam: float = 0.8):
+                 loss: str = "l1", lam: float = 0.8, tune: bool = False, tune_cache: str | None = None):
         self.views = views
         self.anchors = anchors
-        self.rp = RenderPass(views, anchors, cap_rows=cap_rows, precision=precision, store_state=store_state,
-                             chunk=chunk, device=device, loss=loss, lam=lam)
+        self._args = dict(cap_rows=cap_rows, precision=precision, store_state=store_state, device=device,
+                          loss=loss, lam=lam)
+        self.rp = RenderPass(views, anchors, chunk=chunk, **self._args)
         self.target = torch.zeros(3 * views.total_pixels, device=device)
         self.stream = torch.cuda.Stream(device=device)
         self.graph = None
+        self.tune = bool(tune)
+        self.tune_cache = tune_cache
+        self.tuned = None      # the autotuner's pick and its measurements (tune=True)
+        self.tuning = None     # launch shapes the graph is captured with (None: the process-wide ones)
         self._loss_host = torch.zeros(1, dtype=torch.float32).pin_memory()
         self._status_host = torch.zeros(2, dtype=torch.int64).pin_memory()
 
@@ -201,19 +206,53 @@ class MappingStep:
     def h2d_bytes(self):
         return self.target.numel() * 4
 
+    def _autotune(self):
+        """Picks the chunk length and launch shapes for this batch (measured
+        with CUDA events on it, or from the cache) and rebuilds the buffers
+        when the chunk length changes."""
+        from . import autotune
+        code = self.rp.ensure_capacity(self.target)   # the batch's sizes, for the candidates' buffers
+        if code != 0:
+            raise L.GsError("capacity handling", code)
+        cfg, info = autotune.tune(self.views, self.anchors, self.target, self._args["precision"],
+                                  self._args["loss"], cache_path=self.tune_cache, cap_rows=self.rp.cap_rows,
+                                  cap_pairs=self.rp.cap_pairs)
+        self.tuned = dict(config=cfg, **info)
+        if int(cfg["chunk"]) != self.rp.chunk:
+            cap_pairs = self.rp.cap_pairs
+            self._args["cap_rows"] = self.rp.cap_rows
+            self.rp = RenderPass(self.views, self.anchors, chunk=int(cfg["chunk"]), **self._args)
+            self.rp.cap_pairs = cap_pairs
+            self.rp._alloc()
+        self.tuning = {k: int(cfg[k]) for k in api.TUNING_FIELDS}
+
     def prepare(self, target=None):
         if target is not None:
             self.target.copy_(target)
+        if self.tune and self.tuned is None:
+            self._autotune()
         code = self.rp.ensure_capacity(self.target)
         if code != 0:
             raise L.GsError("capacity handling", code)
-        with torch.cuda.stream(self.stream):
-            self.rp.step(self.target)   # kernel attributes and workspaces settle outside the capture
-        torch.cuda.synchronize()
-        self.graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(self.graph, stream=self.stream):
-            self.rp.step(self.target)
-        torch.cuda.synchronize()
+        self.recapture()
+
+    def recapture(self):
+        """Captures the iteration into a new CUDA graph with the current
+        buffers (and this step's launch shapes, when tuned)."""
+        prev = api.get_tuning()
+        if self.tuning is not None:
+            api.set_tuning(self.tuning)
+        try:
+            with torch.cuda.stream(self.stream):
+                self.rp.step(self.target)   # kernel attributes and workspaces settle outside the capture
+            torch.cuda.synchronize()
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph, stream=self.stream):
+                self.rp.step(self.target)
+            torch.cuda.synchronize()
+        finally:
+            if self.tuning is not None:
+                api.set_tuning(prev)
 
     def run(self):
         """Replays the captured iteration on the current inputs; returns the device loss."""

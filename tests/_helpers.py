@@ -99,6 +99,8 @@ def assert_grad_close(got, want, name, rel=GRAD_REL, elem=GRAD_ELEM):
         assert np.max(np.abs(got)) <= 1e-6, f"{name}: expected zero gradient"
         return
     err = np.linalg.norm(got - want) / nw
+    worst = float(np.max(np.abs(got - want))) / scale if scale > 0 else 0.0
+    print(f"[grad] {name}: per-tensor {err:.3e} (bar {rel}), worst element {worst:.3e} of max|g*| (bar {elem})")
     assert err <= rel, f"{name}: relative error {err:.3e} > {rel}"
     bad = np.abs(got - want) > elem * scale + 1e-7
     assert not bad.any(), f"{name}: {bad.sum()} elements off (max {np.max(np.abs(got - want)):.3e})"

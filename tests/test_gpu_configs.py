@@ -9,7 +9,10 @@ oracle computes one by one:
       partitions, 32 keyframes drawn by the recent-window rule, 17.1M rows.
 
 Checked: visibility rows exact (near-threshold rows excepted); 1000 sampled
-decoded rows; per view the heaviest tile and random busy tiles composited by
+decoded rows; 20k sampled candidates projected by the oracle from the GPU's
+decoded Gaussians; all pairs (each (splat, covered tile) once, inside the
+splat's rectangle, (depth bits, id) order in every tile, ranges partitioning
+the pairs); per view the heaviest tile and random busy tiles composited by
 the oracle from the GPU's lists (every tile's list ordered by (depth bits, id));
 the render backward of an image gradient confined to those tiles; the decode
 backward of candidate gradients confined to the sampled rows."""
@@ -21,7 +24,7 @@ from _helpers import PIX_TOL, assert_grad_close, f32, image_mask, to_np
 from oracle import oracle as O
 from paper_2607_21416_b300 import _lib as L
 from paper_2607_21416_b300 import api, pipeline, scenes
-from test_gpu_fullsize import _records, _row_subset, _sample_rows, _tile_pixel_mask
+from test_gpu_fullsize import _at, _records, _row_subset, _sample_rows, _tile_pixel_mask, check_pairs, check_projection
 
 pytestmark = pytest.mark.gpu
 
@@ -46,11 +49,6 @@ def run(request):
     yield s, views, A, ms
     del ms
     torch.cuda.empty_cache()
-
-
-def _at(t, idx):
-    """Host copy of t[idx] (indexed on the device: these buffers hold 10^8 rows)."""
-    return to_np(t[torch.as_tensor(np.asarray(idx, np.int64)).to(t.device)])
 
 
 def _tiles_and_lists(ms, views, n_per_view, seed, n_views=6):
@@ -112,6 +110,16 @@ def test_decode_sampled_rows(run):
     assert np.abs(_at(g.opacity, c) - dec.opacity).mean() < 3e-3
 
 
+def test_project_sampled_candidates(run):
+    s, views, A, ms = run
+    check_projection(s, views, ms.rp, 20000, 16)
+
+
+def test_bin_sort_invariants_all_pairs(run):
+    s, views, A, ms = run
+    check_pairs(s, views, ms.rp, 10_000_000)
+
+
 def test_render_sampled_tiles(run):
     s, views, A, ms = run
     rp = ms.rp
@@ -135,7 +143,7 @@ def test_render_sampled_tiles(run):
     sgrad = torch.zeros_like(rp.sgrad)
     out = api.Gauss3DGrad.like(rp.g)
     st = api.new_status()
-    api.render_bwd(rp.g, rp.splats, rp.bins, views, rp.bg, torch.as_tensor(f32(dimg)).cuda(), sgrad, out, st,
+    api.render_bwd(rp.g, rp.splats, rp.bins, views, rp.image, torch.as_tensor(f32(dimg)).cuda(), sgrad, out, st,
                    rp.render_ws, rp.chunk)
     torch.cuda.synchronize()
     assert api.read_status(st)[0] == 0

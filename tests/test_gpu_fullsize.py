@@ -94,19 +94,25 @@ def test_decode_sampled_rows(run):
     assert np.abs(to_np(g.opacity)[c] - dec.opacity).mean() < 3e-3
 
 
-def test_project_sampled_candidates(run):
-    s, views, A, ms = run
-    g = ms.rp.g
+def _at(t, idx):
+    """Host copy of t[idx], gathered on the device (the buffers can hold 10^8 rows)."""
+    return to_np(t[torch.as_tensor(np.asarray(idx, np.int64)).to(t.device)])
+
+
+def check_projection(s, views, rp, n, seed):
+    """Splat records of n sampled candidates against the oracle's projection
+    of the GPU's own decoded Gaussians (3DGS preliminaries of Sec. III-A)."""
+    g = rp.g
     vs_g = to_np(g.view_start).astype(np.int64)
     C_ = int(vs_g[-1]) * s.k
-    cand = _sample_rows(C_, 20000, 2)
-    cand = cand[to_np(g.opacity)[cand] > 0]
+    cand = _sample_rows(C_, n, seed)
+    cand = cand[_at(g.opacity, cand) > 0]
     v = np.searchsorted(vs_g * s.k, cand, side="right") - 1
     vs_sub = np.concatenate([[0], np.cumsum(np.bincount(v, minlength=views.V))]).astype(np.int64)
-    mu, sc, q, op = (to_np(t)[cand].astype(np.float64) for t in (g.mu, g.scale, g.quat, g.opacity))
+    mu, sc, q, op = (_at(t, cand).astype(np.float64) for t in (g.mu, g.scale, g.quat, g.opacity))
     prj = O.project(mu, sc, q, op, s.cams, s.wh, vs_sub, 1)
-    rec = to_np(ms.rp.splats.rec)[cand]
-    tiles = to_np(ms.rp.splats.tiles)[cand]
+    rec = _at(rp.splats.rec, cand)
+    tiles = _at(rp.splats.tiles, cand)
     ok = prj.flag == 0
     assert ok.mean() > 0.95
     assert np.array_equal(tiles[ok], prj.tiles[ok])
@@ -125,45 +131,70 @@ def test_project_sampled_candidates(run):
     assert np.all(np.abs(r["mean2d"] - prj.mean2d)[live] <= tol_px[live])
     scale = np.max(np.abs(prj.conic[live]), axis=1, keepdims=True)
     assert np.all(np.abs(r["conic"][live] - prj.conic[live]) <= (2e-5 + 8 * rel_z[live, None]) * scale)
+    # opacity (log2 in the record) and colour pass through unchanged
+    # (the record keeps log2 of the opacity: two ulps of log2 relative to its magnitude)
+    lg = np.maximum(1.0, np.abs(np.log2(op[live])))
+    assert np.all(np.abs(r["opacity"][live] / op[live] - 1.0) <= 4 * 2.0 ** -24 * lg + 1e-7)
+    assert np.array_equal(rec[live, 6:9], _at(g.colour, cand)[live])
+    # the depth key is the camera-space z
+    assert np.all(np.abs(rec[live, 9] - z[live]) <= (4 * 2.0 ** -24 + rel_z[live]) * z[live])
     # rectangles: equal except where that position error moves a bound across a tile edge
     same = np.all(r["rect"] == prj.rect, axis=1)
     assert same[live].mean() > 0.999
 
 
-def test_bin_sort_invariants_all_pairs(run):
-    s, views, A, ms = run
-    bins, sp = ms.rp.bins, ms.rp.splats
-    P = int(bins.n_pairs.item())
-    vals = u32(bins.vals)[:P].astype(np.int64)
-    ranges = u32(bins.ranges).astype(np.int64)
-    C_ = int(to_np(ms.rp.g.view_start)[-1]) * s.k
-    tiles = to_np(sp.tiles)[:C_].astype(np.int64)
-    assert P == tiles.sum() > 10_000_000
-    # ranges partition [0, P) in tile order
+def check_pairs(s, views, rp, min_pairs):
+    """Invariants of all (tile, splat) pairs, checked on the device: ranges
+    partition the pairs in tile order; every pair lies inside its splat's tile
+    rectangle in the splat's own view; per-splat pair counts equal the tiles
+    the rectangle covers; (depth bits, id) strictly increase inside every tile
+    (so no pair repeats).  Together: each (splat, covered tile) exactly once,
+    in the order of the (tile, depth, id) key."""
+    dev = rp.bins.vals.device
+    P = int(rp.bins.n_pairs.item())
+    assert P > min_pairs
+    i64 = lambda t: t.to(torch.int64) & 0xFFFFFFFF
+    vals = i64(rp.bins.vals[:P])
+    ranges = i64(rp.bins.ranges.view(-1, 2))
+    T = ranges.shape[0]
     lens = ranges[:, 1] - ranges[:, 0]
-    assert (lens >= 0).all() and lens.sum() == P
-    starts = np.concatenate([[0], np.cumsum(lens)[:-1]])
+    assert bool((lens >= 0).all()) and int(lens.sum()) == P
+    starts = torch.cumsum(lens, 0) - lens
     busy = lens > 0
-    assert np.array_equal(ranges[busy, 0], starts[busy])
-    tile = np.repeat(np.arange(len(ranges)), lens)
-    # each pair once, inside its splat's rectangle, per-splat counts equal tiles_touched
-    assert np.unique(tile * C_ + vals).size == P
-    assert np.array_equal(np.bincount(vals, minlength=C_), tiles)
-    rec = to_np(sp.rec)
-    rx, ry = rec[vals, 10].view(np.uint32).astype(np.int64), rec[vals, 11].view(np.uint32).astype(np.int64)
-    tb = np.concatenate([[0], np.cumsum([((w + 15) // 16) * ((h + 15) // 16) for w, h in s.wh])])
-    tv = np.searchsorted(tb, tile, side="right") - 1
-    TX = np.array([(w + 15) // 16 for w, h in s.wh])[tv]
+    assert torch.equal(ranges[busy, 0], starts[busy])
+    tile = torch.repeat_interleave(torch.arange(T, device=dev), lens)
+    vs = rp.g.view_start.to(torch.int64)
+    C_ = int(vs[-1]) * s.k
+    tiles_touched = rp.splats.tiles[:C_].to(torch.int64)
+    assert int(tiles_touched.sum()) == P
+    assert bool((vals < C_).all())
+    assert torch.equal(torch.bincount(vals, minlength=C_), tiles_touched)
+    rec = rp.splats.rec.view(-1, 12)
+    words = rec[:, 9:12].contiguous().view(torch.int32)
+    rx, ry = i64(words[vals, 1]), i64(words[vals, 2])
+    tb = torch.as_tensor(np.concatenate([[0], np.cumsum([((w + 15) // 16) * ((h + 15) // 16)
+                                                         for w, h in views.wh])]), device=dev)
+    tv = torch.searchsorted(tb, tile, right=True) - 1
+    TX = torch.as_tensor(np.array([(w + 15) // 16 for w, h in views.wh]), device=dev)[tv]
     loc = tile - tb[tv]
     tx, ty = loc % TX, loc // TX
-    assert ((tx >= (rx & 0xFFFF)) & (tx < (rx >> 16)) & (ty >= (ry & 0xFFFF)) & (ty < (ry >> 16))).all()
-    v_of_c = np.searchsorted(to_np(ms.rp.g.view_start).astype(np.int64) * s.k, vals, side="right") - 1
-    assert np.array_equal(v_of_c, tv)
-    # (depth bits, id) non-decreasing inside every tile
-    d = rec[vals, 9].view(np.uint32).astype(np.int64)
+    inside = (tx >= (rx & 0xFFFF)) & (tx < (rx >> 16)) & (ty >= (ry & 0xFFFF)) & (ty < (ry >> 16))
+    assert bool(inside.all())
+    v_of_c = torch.searchsorted(vs * s.k, vals, right=True) - 1
+    assert torch.equal(v_of_c, tv)
+    key = i64(words[vals, 0]) * (1 << 32) + vals
     same = tile[1:] == tile[:-1]
-    key = d * (1 << 32) + vals
-    assert (key[1:][same] > key[:-1][same]).all()
+    assert bool((key[1:][same] > key[:-1][same]).all())
+
+
+def test_project_sampled_candidates(run):
+    s, views, A, ms = run
+    check_projection(s, views, ms.rp, 20000, 2)
+
+
+def test_bin_sort_invariants_all_pairs(run):
+    s, views, A, ms = run
+    check_pairs(s, views, ms.rp, 10_000_000)
 
 
 def _sampled_tiles(ms, views, n_per_view=3, seed=3):
@@ -239,7 +270,7 @@ def test_render_sampled_tiles_forward_and_backward(run):
     sgrad = torch.zeros_like(rp.sgrad)
     out = api.Gauss3DGrad.like(rp.g)
     st = api.new_status()
-    api.render_bwd(rp.g, rp.splats, rp.bins, views, rp.bg, torch.as_tensor(f32(dimg)).cuda(), sgrad, out, st,
+    api.render_bwd(rp.g, rp.splats, rp.bins, views, rp.image, torch.as_tensor(f32(dimg)).cuda(), sgrad, out, st,
                    rp.render_ws, rp.chunk)
     torch.cuda.synchronize()
     assert api.read_status(st)[0] == 0

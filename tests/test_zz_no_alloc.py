@@ -2,8 +2,9 @@
 device memory (its scratch is a static device array instead of a caller
 workspace).  Its output must equal that of gs_decode on the same inputs, on
 two calls in a row with different problem sizes (the second call finds the
-first call's counts in the shared scratch).  This file is collected last so
-that a stop at the first failure has already run every other test."""
+first call's counts in the shared scratch), with the FP32 decoder and with
+the BF16 tensor-core decoder.  This file is collected last so that a stop at
+the first failure has already run every other test."""
 import numpy as np
 import pytest
 import torch
@@ -16,18 +17,18 @@ pytestmark = pytest.mark.gpu
 PREC_TOL = 0.0   # same kernels and inputs: outputs match bit for bit
 
 
-def _decode_both(s):
+def _decode_both(s, precision):
     A = api.Anchors.from_scene(s)
     vw = api.Views(s.cams, s.wh)
     cap = s.N * s.V
     ref = api.Gauss3D.alloc(cap, s.k, s.V)
     st = api.new_status()
-    api.decode(A, vw, ref, api.workspace(api.decode_workspace(A, vw, cap)), st)
+    api.decode(A, vw, ref, api.workspace(api.decode_workspace(A, vw, cap)), st, precision)
     got = api.Gauss3D.alloc(cap, s.k, s.V)
     got.row_anchor.fill_(-7)
     got.opacity.fill_(123.0)
     st2 = api.new_status()
-    api.decode_noalloc(A, vw, got, st2)
+    api.decode_noalloc(A, vw, got, st2, precision)
     torch.cuda.synchronize()
     assert api.read_status(st)[0] == 0 and api.read_status(st2)[0] == 0
     rows = int(ref.view_start[-1].item())
@@ -40,11 +41,12 @@ def _decode_both(s):
         assert torch.allclose(a, b, rtol=PREC_TOL, atol=PREC_TOL), name
 
 
-def test_noalloc_decode_matches_decode_on_two_calls_in_a_row():
+@pytest.mark.parametrize("precision", [L.GS_PREC_FP32, L.GS_PREC_BF16])
+def test_noalloc_decode_matches_decode_on_two_calls_in_a_row(precision):
     # two different problems back to back: several anchor chunks and views,
     # then a larger single view
-    _decode_both(scenes.tiny_corridor(seed=2, n_anchors=5000))
-    _decode_both(scenes.anchor_single_view(seed=1))
+    _decode_both(scenes.tiny_corridor(seed=2, n_anchors=5000), precision)
+    _decode_both(scenes.anchor_single_view(seed=1), precision)
 
 
 def test_noalloc_decode_rejects_sizes_beyond_its_scratch():
