@@ -6,7 +6,20 @@ driving corridor, 8 keyframes of 1241x376 (fx = fy = 718) at 1 m spacing with
 +-2 deg yaw jitter, k = 10 Gaussians per anchor, 2-layer decoders of width 32
 on 32-d features.  One step = one mapping iteration without the optimizer:
 decode -> project -> bin/sort -> composite -> L1 -> composite backward ->
-decode backward over all 8 keyframes.
+projection backward -> decode backward over all 8 keyframes.
+
+--workload selects the other workloads of the same loop (each its own line):
+  explicit_2k_128x96              2,000 explicit FP32 Gaussians, one 128x96 view
+                                  (enters at the projection; plain FP32 path)
+  anchor_grid_20k_1241x376        20k anchors, one 1241x376 view, FP32 decoding
+  keyframe_batch_200k_anchors_8x1241x376   the default (batched, BF16 decoding)
+  uneven_partitions_16x           16 lognormal partitions (~650k anchors), 16
+                                  keyframes of mixed resolution, BF16 decoding
+  loop_road_2M_anchors_32x1241x376  2M anchors on a 5 km loop, 32 keyframes
+                                  drawn by the recent-window rule, BF16 decoding
+The batched workloads pick their chunk length and launch shapes with the
+autotuner first (untimed; --no-tune keeps the library defaults) and report
+the pick.
 
 Arms:
   default            the batched path: one CUDA graph per iteration (all views
@@ -39,6 +52,28 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "keyframe_batch_200k_anchors_8x1241x376"
 METRIC = "mapping fwd+bwd Mpix/s (8-keyframe batch)"
+WORKLOADS = ("explicit_2k_128x96", "anchor_grid_20k_1241x376", WORKLOAD, "uneven_partitions_16x",
+             "loop_road_2M_anchors_32x1241x376")
+
+
+def build_workload(name, seed, n_anchors=200000, n_views=8):
+    """(scene, path, default precision, batched) of a workload."""
+    from paper_2607_21416_b300 import scenes
+    if name == "explicit_2k_128x96":
+        return scenes.explicit_frustum(seed=seed, n=2000), "explicit", "fp32", False
+    if name == "anchor_grid_20k_1241x376":
+        return scenes.anchor_single_view(seed=seed), "anchor", "fp32", False
+    if name == WORKLOAD:
+        return scenes.keyframe_batch(seed=seed, n_anchors=n_anchors, n_views=n_views), "anchor", "bf16", True
+    if name == "uneven_partitions_16x":
+        return scenes.uneven_partitions(seed=seed), "anchor", "bf16", True
+    if name == "loop_road_2M_anchors_32x1241x376":
+        return scenes.loop_road(seed=seed), "anchor", "bf16", True
+    raise ValueError(name)
+
+
+def metric_of(name):
+    return METRIC if name == WORKLOAD else f"mapping fwd+bwd Mpix/s ({name})"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
@@ -59,7 +94,10 @@ def parse():
     p.add_argument("--steps", type=int, default=100)
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
+    p.add_argument("--workload", default=WORKLOAD, choices=WORKLOADS)
+    p.add_argument("--precision", default=None, choices=["fp32", "bf16"],
+                   help="decoder arithmetic (default: the workload's)")
+    p.add_argument("--no-tune", action="store_true", help="keep the library's default launch shapes")
     p.add_argument("--no-plain", action="store_true", help="skip timing the plain path")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     p.add_argument("--no-photometric", action="store_true",
@@ -146,37 +184,54 @@ def run_ours(args, rank, world, dist):
     import torch
 
     from paper_2607_21416_b300 import _lib as L
-    from paper_2607_21416_b300 import api, pipeline, scenes
+    from paper_2607_21416_b300 import api, pipeline
 
     dev = torch.device("cuda", torch.cuda.current_device())
-    prec = L.GS_PREC_BF16 if args.precision == "bf16" else L.GS_PREC_FP32
-    scene = scenes.keyframe_batch(seed=rank, n_anchors=args.anchors, n_views=args.views)
+    scene, path, prec_name, batched = build_workload(args.workload, rank, args.anchors, args.views)
+    prec = L.GS_PREC_BF16 if (args.precision or prec_name) == "bf16" else L.GS_PREC_FP32
     views = api.Views(scene.cams, scene.wh)
-    anchors = api.Anchors.from_scene(scene)
+    anchors = api.Anchors.from_scene(scene) if path == "anchor" else None
     target_host = torch.from_numpy(np.concatenate([t.reshape(-1) for t in scene.targets])).pin_memory()
     cams_host = torch.from_numpy(np.ascontiguousarray(scene.cams)).pin_memory()
     target = target_host.to(dev)
     npix = views.total_pixels
 
-    # ---- batched path: capacity first (outside capture), then one CUDA graph
+    # ---- the iteration: capacity first (outside capture), then one CUDA graph
     store = args.state == "store"
     torch.cuda.reset_peak_memory_stats()
-    ms = pipeline.MappingStep(views, anchors, precision=prec, cap_rows=int(1.2 * scene.N * 0.6 * views.V),
-                              store_state=store, chunk=args.chunk)
-    ms.prepare(target)    # sizes the buffers (host-synchronised) and captures the public step's graph
-    rp = ms.rp
+    tuned = None
+    if path == "anchor":
+        # first capacities: the 8-keyframe corridor keeps ~50 % of its (anchor, view) rows; the wider
+        # batches far fewer (the step grows every buffer that turns out too small)
+        cap_rows = (int(1.2 * scene.N * 0.6 * views.V) if views.V <= 8 else scene.N * views.V // 4) if batched else None
+        ms = pipeline.MappingStep(views, anchors, precision=prec, cap_rows=cap_rows, store_state=store,
+                                  chunk=args.chunk, tune=batched and not args.no_tune and args.chunk == 0)
+        if batched and views.V > 8:   # ~0.8 pairs per candidate to start with, not the 4 of the default
+            ms.rp.cap_pairs = 8 * ms.rp.cap_rows
+            ms.rp._alloc()
+        ms.prepare(target)    # sizes the buffers (host-synchronised), tunes, captures the public step's graph
+        rp = ms.rp
+        tuned = ms.tuned
+    else:
+        ms = None
+        rp = pipeline.RenderPass(views, None, cap_rows=scene.mu.shape[0], store_state=store, chunk=args.chunk)
+        rp.set_explicit(api.Gauss3D.explicit(scene.mu, scene.scale, scene.quat, scene.opacity, scene.colour))
+        assert rp.ensure_capacity(target) == 0
     torch.cuda.synchronize()
     n_rows, n_pairs = rp.n_rows(), rp.n_pairs()
     counts = work_counts(rp)      # exact work of one iteration (untimed)
     stream = torch.cuda.Stream()
+    # decode_bwd: the projection's and the decoders' reverse in one call (gs_decode_project_bwd; the
+    # tensor-core path fuses them); explicit Gaussians: the projection's reverse (gs_project_bwd)
     names = ["decode", "project", "bin_sort", "render_fwd", "l1", "render_bwd", "decode_bwd"]
     ev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(len(names) + 1)]
+    shapes = ms.tuning if ms is not None and ms.tuning is not None else None
 
     def step_with_events():
-        s = None
         ev[0].record()
         rp.status.zero_()
-        api.decode(anchors, views, rp.g, rp.dec_ws, rp.status, prec)
+        if anchors is not None:
+            api.decode(anchors, views, rp.g, rp.dec_ws, rp.status, prec)
         ev[1].record()
         api.project(rp.g, views, rp.splats, rp.status)
         ev[2].record()
@@ -187,16 +242,22 @@ def run_ours(args, rank, world, dist):
         ev[4].record()
         api.l1_loss(rp.image, target, views, rp.loss, rp.d_image)
         ev[5].record()
-        if rp.ggrad is None:
-            rp.ggrad = api.Gauss3DGrad.like(rp.g)
-        api.render_bwd(rp.g, rp.splats, rp.bins, views, rp.image, rp.d_image, rp.sgrad, rp.ggrad, rp.status,
+        api.render_bwd(rp.g, rp.splats, rp.bins, views, rp.image, rp.d_image, rp.sgrad, None, rp.status,
                        rp.render_ws, rp.chunk, rp.last)
         ev[6].record()
-        api.decode_bwd(anchors, views, rp.g, rp.ggrad, rp.agrad, rp.dbwd_ws, rp.status, prec)
+        if anchors is not None:
+            api.decode_project_bwd(anchors, views, rp.g, rp.splats, rp.sgrad, rp.agrad, rp.dpbwd_ws, rp.status,
+                                   prec)
+        else:
+            if rp.ggrad is None:
+                rp.ggrad = api.Gauss3DGrad.like(rp.g)
+            api.project_bwd(rp.g, rp.splats, views, rp.sgrad, rp.ggrad, rp.status)
         ev[7].record()
-        return s
 
-    # warm the launch path once eagerly (sets kernel attributes), then capture
+    # warm the launch path once eagerly (sets kernel attributes), then capture, with the tuned shapes
+    prev_shapes = api.get_tuning()
+    if shapes is not None:
+        api.set_tuning(shapes)
     with torch.cuda.stream(stream):
         step_with_events()
     torch.cuda.synchronize()
@@ -209,6 +270,7 @@ def run_ours(args, rank, world, dist):
         step_with_events()     # one eager step only to count this library's launches per step
     torch.cuda.synchronize()
     launches_per_step = int(L.load().gs_kernel_launches()) - launches_before
+    api.set_tuning(prev_shapes)
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     for _ in range(args.warmup):
@@ -234,7 +296,19 @@ def run_ours(args, rank, world, dist):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    # the clock sampler (nvidia-smi, 200 ms period) keeps running over untimed replays of the same
+    # iteration right after the timed loop until 1.2 s have passed, so that it sees the clock under
+    # this load even when the timed loop itself is shorter than its period
+    t_soak = time.perf_counter()
+    soak = 0
+    while time.perf_counter() - t_soak < 1.2 - min(1.2, sum(step_ms) * 1e-3):
+        graph.replay()
+        soak += 1
+        if soak % 20 == 0:
+            torch.cuda.synchronize()
+    torch.cuda.synchronize()
     clk = clocks.stop()
+    clk["soak_replays"] = soak
     total_ms, mpix = whole_job(float(sum(step_ms)), npix, args.steps, world, dist, dev)
     ms_per_step = total_ms / args.steps
 
@@ -242,19 +316,32 @@ def run_ours(args, rank, world, dist):
     # target images and cameras from pinned host memory, replays the iteration and reads the
     # loss and status back (one stream synchronisation); timed on the host clock
     e2e_ms = []
+    h2d = int(target_host.numel() * 4) + int(cams_host.numel() * 4)
+    d2h = 20
     for _ in range(max(3, args.steps // 2)):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ms.step(target_host, cams_host)
+        if ms is not None:
+            ms.step(target_host, cams_host)
+        else:   # explicit Gaussians: the same copies around a replay of the captured iteration
+            with torch.cuda.stream(stream):
+                target.copy_(target_host, non_blocking=True)
+                views.cams.copy_(cams_host, non_blocking=True)
+                graph.replay()
+                lh = rp.loss[:1].to("cpu", non_blocking=True)
+                sh = rp.status.to("cpu", non_blocking=True)
+            stream.synchronize()
+            assert int(np.int32(int(sh[0]) & 0xFFFFFFFF)) == 0
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_mpix = npix * world / (statistics.mean(e2e_ms) * 1e-3) / 1e6
     peak_hbm_gb = torch.cuda.max_memory_allocated() / 1e9
+    default_workload = args.workload == WORKLOAD
 
     # ---- the full objective of Eq. 3 (L1 + SSIM terms, lambda 0.8) on this batch's rendered
     # image, timed on its own (the mapping step above uses its L1 term, as the workload does)
     photo = None
-    if not args.no_photometric:
+    if not args.no_photometric and default_workload:
         pws = api.workspace(api.photometric_workspace(views), dev)
         ploss = torch.zeros(3, device=dev)
         pd = torch.empty_like(rp.d_image)
@@ -283,7 +370,7 @@ def run_ours(args, rank, world, dist):
     # ---- after the reverse pass: Adam over the optimised anchor tensors and the decoder weights
     # (one launch), and the densification statistics of the iteration, each timed on its own
     optim = None
-    if not args.no_optim:
+    if not args.no_optim and default_workload:
         import dataclasses
         work = dataclasses.replace(anchors, feat=anchors.feat.clone(), offsets=anchors.offsets.clone(),
                                    log_scaling=anchors.log_scaling.clone(), mlp=anchors.mlp.clone())
@@ -318,7 +405,7 @@ def run_ours(args, rank, world, dist):
     # 2M points around the map's surfaces against the map's own voxels, and the loop-closure
     # deformation (Eq. 7) of the anchors by perturbed poses of the batch's keyframes
     maint = None
-    if not args.no_maintenance:
+    if not args.no_maintenance and default_workload:
         rng = np.random.default_rng(1234)
         eps = 0.2
         base = np.repeat(scene.xyz.astype(np.float32), 10, axis=0)
@@ -384,7 +471,7 @@ def run_ours(args, rank, world, dist):
 
     # ---- plain FP32 path: views one at a time, state stored, eager launches
     plain = None
-    if not args.no_plain:
+    if not args.no_plain and default_workload:
         passes = []
         for v in range(views.V):
             vv = api.Views(scene.cams[v:v + 1], scene.wh[v:v + 1])
@@ -429,8 +516,8 @@ def run_ours(args, rank, world, dist):
     return dict(value=mpix, ms_per_step=ms_per_step, stages=stages, clocks=clk, e2e_ms=e2e_ms,
                 e2e_mpix=e2e_mpix, plain=plain, roofline=roof, n_rows=n_rows, n_pairs=n_pairs,
                 counts=counts, launches=launches_per_step, npix=npix, peak_hbm_gb=peak_hbm_gb, photo=photo,
-                optim=optim, maint=maint,
-                h2d=ms.h2d_bytes + int(cams_host.numel() * 4), d2h=ms.d2h_bytes)
+                optim=optim, maint=maint, h2d=h2d, d2h=d2h, tuned=tuned, scene=scene, views=views,
+                precision="bf16" if prec == L.GS_PREC_BF16 else "fp32", chunk=rp.chunk)
 
 
 # FP32 operations of the method per (pixel, splat) evaluation, counted from
@@ -479,20 +566,27 @@ def roofline(dom, ms, counts, n_pairs, n_rows, rp, scene, peaks):
                 "unit": "T FP32 ops/s", "frac": a / alu_peak, "traffic": None,
                 "work_per_launch": f"{ex} examined + {comp} composited pixel-splat pairs"}
     if dom == "render_bwd":
-        # the forward is recomputed only for tiles whose list is one work item;
-        # chunks of longer lists start from the state the forward left
-        ops = (ex1 * OPS_EXAMINED + comp1 * OPS_COMPOSITED_FWD        # recomputed forward
-               + rev * OPS_EXAMINED + comp * OPS_COMPOSITED_BWD)      # reverse traversal
+        # the reverse walk examines, per pixel, every list position up to its stop (tiles whose
+        # list is one work item, deciding the stop rule again) or up to its last composited
+        # splat (chunks of longer lists, from the per-chunk state); every composited pair costs
+        # the forward's transmittance step and the reverse terms
+        exf = counts["examined_reverse_walk"]
+        ops = exf * OPS_EXAMINED + comp * OPS_COMPOSITED_BWD
         a = ops / (ms * 1e-3) / 1e12
-        return {"kernel": "render_bwd_kernel (+project_bwd_kernel, same call)", "bound": "alu",
-                "achieved": a, "peak": alu_peak, "unit": "T FP32 ops/s", "frac": a / alu_peak,
+        return {"kernel": "render_bwd_kernel", "bound": "alu", "achieved": a, "peak": alu_peak,
+                "unit": "T FP32 ops/s", "frac": a / alu_peak,
                 "peak_of": "148 SMs x 128 FP32 lanes x 2032 MHz (the measured FMA issue rate is beside it)",
                 "traffic": profiled_traffic("render_bwd_kernel_keyframe_batch_8x1241x376.md",
                                             ("render_bwd.cu", "render_common.cuh")),
-                "work_per_launch": f"{ex1} examined (recomputed, single-item tiles) + {rev} reverse-examined + "
-                                   f"{comp1} + {comp} composited pairs"}
+                "work_per_launch": f"{exf} examined + {comp} composited pixel-splat pairs"}
+    if dom == "project_bwd":
+        C_ = n_rows * scene.k if scene.k else n_rows
+        byts = C_ * (4 + 9 * 4 + 40 + 56)
+        a = byts / (ms * 1e-3) / 1e9
+        return {"kernel": "project_bwd_kernel", "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s",
+                "frac": a / hbm, "traffic": None, "work_per_launch": f"{C_} candidates x 136 B"}
     if dom == "bin_sort":
-        S = n_rows * scene.k
+        S = n_rows * (scene.k or 1)
         byts = S * 4 * 2 + n_pairs * 8 * 2 + n_pairs * 4
         a = byts / (ms * 1e-3) / 1e9
         return {"kernel": "bin_sort", "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s",
@@ -506,20 +600,39 @@ def roofline(dom, ms, counts, n_pairs, n_rows, rp, scene, peaks):
 
 def work_counts(rp):
     """Exact pixel-splat counts of one forward (untimed): pairs examined,
-    pairs composited, and the reverse pass's examined pairs (sum of the last
-    composited list position over pixels)."""
+    pairs composited, the same over the tiles whose list is one work item,
+    the reverse pass's examined pairs up to each pixel's last composited
+    splat, and the pairs the front-to-back reverse walk examines (the
+    forward's examined pairs in single-item tiles, the positions up to the
+    last composited splat in the others)."""
     import torch
 
+    from paper_2607_21416_b300 import _lib as L
     from paper_2607_21416_b300 import api
     T = torch.zeros(rp.views.total_pixels, device="cuda")
     last = torch.zeros(rp.views.total_pixels, device="cuda", dtype=torch.int32)
     api.render_fwd(rp.splats, rp.bins, rp.views, rp.bg, rp.image, rp.status, rp.render_ws, rp.chunk, T, last,
                    rp.n_eval)
     torch.cuda.synchronize()
+    # tile of every pixel, and whether its list is one work item
+    chunk = rp.chunk if rp.chunk else L.DEFAULT_CHUNK
+    ranges = rp.bins.ranges.view(-1, 2).to(torch.int64) & 0xFFFFFFFF
+    multi = (ranges[:, 1] - ranges[:, 0]) > chunk
+    tiles = []
+    tb = 0
+    for w, h in np.asarray(rp.views.wh).reshape(-1, 2):
+        w, h = int(w), int(h)
+        tx = (w + 15) // 16
+        yy, xx = torch.meshgrid(torch.arange(h, device="cuda"), torch.arange(w, device="cuda"), indexing="ij")
+        tiles.append((tb + (yy // 16) * tx + xx // 16).reshape(-1))
+        tb += tx * ((h + 15) // 16)
+    pix_multi = multi[torch.cat(tiles)]
+    last64 = last.to(torch.int64)
     return {"examined": int(rp.n_eval[0].item()), "composited": int(rp.n_eval[1].item()),
             "examined_single_item_tiles": int(rp.n_eval[2].item()),
             "composited_single_item_tiles": int(rp.n_eval[3].item()),
-            "reverse_examined": int(last.to(torch.int64).sum().item())}
+            "reverse_examined": int(last64.sum().item()),
+            "examined_reverse_walk": int(rp.n_eval[2].item()) + int(last64[pix_multi].sum().item())}
 
 
 # -------------------------------------------------------------- CPU oracle
@@ -628,7 +741,7 @@ def main():
         torch.cuda.set_device(0)
     r = run_ours(args, rank, world, dist)
     cpu = None
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and not args.no_cpu and args.workload == WORKLOAD:
         pool = OraclePool(args.anchors, args.views)
         v, wall, npix, cpu_s = pool.keyframe()
         pool.close()
@@ -638,15 +751,28 @@ def main():
                          f"process (spawned), all anchors, forward + L1 + reverse of the FP64 oracle; "
                          f"{wall:.1f} s wall, {cpu_s:.1f} s CPU"}
     if rank == 0:
-        line = {"metric": METRIC, "value": r["value"], "unit": "Mpix/s", "n_gpus": world,
+        sc, vw = r["scene"], r["views"]
+        wh = np.asarray(vw.wh).reshape(-1, 2)
+        res = sorted({f"{int(w)}x{int(h)}" for w, h in wh})
+        cfg = {"workload": args.workload, "keyframes": int(vw.V), "resolution": "/".join(res),
+               "pixels": int(vw.total_pixels)}
+        if sc.xyz is not None:
+            cfg.update({"anchors": int(sc.N), "partitions": int(sc.M), "k": int(sc.k), "feature_dim": int(sc.F),
+                        "hidden": int(sc.hidden)})
+        else:
+            cfg.update({"gaussians": int(sc.mu.shape[0])})
+        cfg.update({"path": ("batched" if args.workload not in WORKLOADS[:2] else "plain") +
+                            ", one CUDA graph per iteration, per-pixel state " +
+                            ("stored" if args.state == "store" else "recomputed"),
+                    "decode": r["precision"], "chunk": r["chunk"] or 384,
+                    "launch_shapes": (r["tuned"] or {}).get("config"),
+                    "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) before each step"})
+        line = {"metric": metric_of(args.workload), "value": r["value"], "unit": "Mpix/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32" if args.precision == "fp32" else "bf16-decode/f32",
+                "dtype": "f32" if r["precision"] == "fp32" else "bf16-decode/f32",
                 "data": "synthetic (seeded driving-corridor scene; no dataset)",
-                "config": {"workload": WORKLOAD, "anchors": args.anchors, "keyframes": args.views,
-                           "resolution": "1241x376", "k": 10, "feature_dim": 32, "hidden": 32,
-                           "path": "batched, one CUDA graph per iteration, per-pixel state " + ("stored" if args.state == "store" else "recomputed"),
-                           "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) before each step"},
+                "config": cfg,
                 "e2e": {"value": r["e2e_mpix"], "unit": "Mpix/s", "h2d_bytes_per_step": r["h2d"],
                         "d2h_bytes_per_step": r["d2h"]},
                 "gpu_launches": r["launches"] * args.steps,
@@ -654,6 +780,7 @@ def main():
                 "stages_ms": r["stages"], "plain_path": r["plain"], "peak_hbm_gb": r["peak_hbm_gb"],
                 "speedup_vs_plain": (r["value"] / r["plain"]["value"]) if r["plain"] else None,
                 "counts": dict(rows=r["n_rows"], pairs=r["n_pairs"], pixels=r["npix"], **r["counts"]),
+                "autotune": r["tuned"],
                 "photometric_loss": r["photo"], "optimizer": r["optim"], "maintenance": r["maint"]}
         print(json.dumps(line), flush=True)
     if dist:

@@ -443,23 +443,34 @@ int gs_flow_triangulate(const gs_camera *cam1, const gs_camera *cam2, int32_t wi
  * dL/dalpha_i = g.(c_i T_i - B_i/(1 - alpha_i)), then through alpha = o
  * exp(power) (no gradient where the 0.99 clamp is active) to mean and conic;
  * per-splat sums are reduced across each warp before global atomics.  Then
- * the projection chain rule gives d mu, d scale, d quat; d opacity, d colour
- * pass through.  Each pixel's list is walked front to back again: T_i and the
- * colour composited up to splat i are recomputed with the forward's
- * arithmetic (the forward's skip and stop decisions), and B_i is the pixel's
- * final colour minus that prefix, so the forward stores nothing per pixel.
- * image: the forward's output (device, same layout as d_image).  last: the
- * forward's optional per-pixel output (1-based position of the last
- * composited splat), or NULL to decide the stop rule again.  chunk and ws
- * must be those of the forward, ws untouched since: tiles cut into several
- * chunks start each chunk from the transmittance and colour prefix the
- * forward left there.  sgrad: per-splat view-space gradients (workspace-like
- * output, overwritten).  out: overwritten for every candidate (zeros for
- * culled ones). */
+ * (unless out is NULL) the projection chain rule of gs_project_bwd.  Each
+ * pixel's list is walked front to back again: T_i and the colour composited
+ * up to splat i are recomputed with the forward's arithmetic (the forward's
+ * skip and stop decisions), and B_i is the pixel's final colour minus that
+ * prefix, so the forward stores nothing per pixel.  image: the forward's
+ * output (device, same layout as d_image).  last: the forward's optional
+ * per-pixel output (1-based position of the last composited splat), or NULL
+ * to decide the stop rule again.  chunk and ws must be those of the forward,
+ * ws untouched since: tiles cut into several chunks start each chunk from
+ * the transmittance and colour prefix the forward left there.  sgrad:
+ * per-splat view-space gradients, overwritten for the candidates that cover
+ * a tile (sp->tiles > 0; the others are neither written nor read).  out:
+ * NULL, or overwritten for every candidate (zeros for culled ones). */
 int gs_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *sp,
                   const gs_bins *bins, const gs_view *views, int32_t V, int32_t chunk, void *ws,
                   size_t ws_bytes, const float *image, const float *d_image, const int32_t *last,
                   gs_splat_grad *sgrad, gs_gauss3d_grad *out, gs_status *status, void *stream);
+
+/* Chain rule of the EWA projection (3DGS preliminaries, Sec. III-A): from the
+ * splat gradients of gs_render_bwd (d mean2d, d conic, d opacity, d colour)
+ * to d mu, d scale, d quat of the 3D Gaussians, with the FP64 inverse
+ * derivative (on the compensated covariance) for near-degenerate splats as in
+ * gs_project; d opacity and d colour pass through.  Candidates with
+ * sp->tiles == 0 get zeros.  out is overwritten for every candidate up to the
+ * row count. */
+int gs_project_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *sp, const gs_view *views,
+                   int32_t V, const gs_splat_grad *sgrad, gs_gauss3d_grad *out, gs_status *status,
+                   void *stream);
 
 /* Reverse of gs_decode, summed over views: through the activations (only for
  * candidates with opacity > 0), both MLP layers (hidden activations
@@ -469,6 +480,24 @@ int gs_decode_bwd(const gs_anchors *A, const gs_camera *cams, const gs_view *vie
                   int32_t precision, const gs_gauss3d *g, const gs_gauss3d_grad *dg,
                   gs_anchor_grad *out, void *ws, size_t ws_bytes, gs_status *status,
                   void *stream);
+
+/* Reverse of the projection and of the decoders in one call, from the splat
+ * gradients of gs_render_bwd (called with out = NULL): the result of
+ * gs_project_bwd followed by gs_decode_bwd, without the 3D-Gaussian
+ * gradients in between.  With GS_PREC_BF16 the tensor-core reverse decoder
+ * applies the projection's chain rule (the near-degenerate branch included)
+ * to each candidate it recomputes -- mean x_a + offset exp(l[0:3]), scale
+ * exp(l[3:6]) sigmoid, unit quaternion, evaluated with the reverse pass's
+ * recomputed decoder activations -- and needs no workspace; with
+ * GS_PREC_FP32 the two steps run one after the other through a workspace of
+ * gs_decode_project_bwd_workspace bytes (256-byte aligned).  sp->tiles marks
+ * the candidates that cover a tile (the others get no gradient).  out is
+ * overwritten. */
+size_t gs_decode_project_bwd_workspace(int32_t k, int64_t cap_rows, int32_t precision);
+int gs_decode_project_bwd(const gs_anchors *A, const gs_camera *cams, const gs_view *views, int32_t V,
+                          int32_t precision, const gs_gauss3d *g, const gs_splats *sp,
+                          const gs_splat_grad *sgrad, gs_anchor_grad *out, void *ws, size_t ws_bytes,
+                          gs_status *status, void *stream);
 
 /* Measurement helper (no counterpart in the paper): launches `blocks` CTAs of
  * 256 threads, each running 8 independent chains of `iters` dependent

@@ -386,16 +386,45 @@ def flow_triangulate(cams, wh, flow, samples, tau, kept, points, n_kept, ws, sta
 
 def render_bwd(g: Gauss3D, sp: Splats, bins: Bins, views: Views, image, d_image, sgrad, out: Gauss3DGrad,
                status, ws, chunk=0, last=None, stream=None):
-    """Reverse of the compositing and the projection.  image: the forward's
-    output; last: its optional per-pixel last composited position."""
+    """Reverse of the compositing and (unless out is None) of the projection.
+    image: the forward's output; last: its optional per-pixel last
+    composited position."""
     lib = L.load()
     gs_, s, b = g.struct(), sp.struct(), bins.struct()
     sg = L.gs_splat_grad(sgrad.data_ptr())
-    o = out.struct()
+    o = C.byref(out.struct()) if out is not None else None
     L.check("gs_render_bwd", lib.gs_render_bwd(C.byref(gs_), _ptr(views.cams), C.byref(s), C.byref(b),
                                                views.ptr, views.V, chunk, _ptr(ws), ws.numel(), _ptr(image),
-                                               _ptr(d_image), _ptr(last), C.byref(sg), C.byref(o),
+                                               _ptr(d_image), _ptr(last), C.byref(sg), o,
                                                _ptr(status), _stream(stream)))
+
+
+def project_bwd(g: Gauss3D, sp: Splats, views: Views, sgrad, out: Gauss3DGrad, status, stream=None):
+    """Chain rule of the projection from the splat gradients of render_bwd."""
+    lib = L.load()
+    gs_, s = g.struct(), sp.struct()
+    sg = L.gs_splat_grad(sgrad.data_ptr())
+    o = out.struct()
+    L.check("gs_project_bwd", lib.gs_project_bwd(C.byref(gs_), _ptr(views.cams), C.byref(s), views.ptr, views.V,
+                                                 C.byref(sg), C.byref(o), _ptr(status), _stream(stream)))
+
+
+def decode_project_bwd_workspace(g: Gauss3D, precision=L.GS_PREC_FP32):
+    return int(L.load().gs_decode_project_bwd_workspace(g.k, g.cap_rows, precision))
+
+
+def decode_project_bwd(anchors: Anchors, views: Views, g: Gauss3D, sp: Splats, sgrad, out: AnchorGrad, ws,
+                       status, precision=L.GS_PREC_FP32, stream=None):
+    """Reverse of the projection and the decoders from render_bwd's splat
+    gradients (tensor-core path fused; FP32 path through ws)."""
+    lib = L.load()
+    a, gs_, s = anchors.struct(), g.struct(), sp.struct()
+    sg = L.gs_splat_grad(sgrad.data_ptr())
+    o = out.struct()
+    L.check("gs_decode_project_bwd", lib.gs_decode_project_bwd(C.byref(a), _ptr(views.cams), views.ptr, views.V,
+                                                               precision, C.byref(gs_), C.byref(s), C.byref(sg),
+                                                               C.byref(o), _ptr(ws), 0 if ws is None else ws.numel(),
+                                                               _ptr(status), _stream(stream)))
 
 
 def decode_bwd_workspace(anchors: Anchors, views: Views, cap_rows):

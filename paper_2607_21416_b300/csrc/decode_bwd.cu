@@ -48,7 +48,10 @@ __global__ void __launch_bounds__(kDbRows) decode_bwd_fp32_kernel(DecodeBwdArgsB
     if (tid < 3) s_accpart[tid] = -1;
     for (long long i = tid; i < P; i += kDbRows) s_acc[i] = 0.f;
     __syncthreads();
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    // contiguous tile ranges per CTA: few partition changes, so few flushes of the accumulators
+    const int per_cta = (ntiles + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int tile_end = min(ntiles, ((int)blockIdx.x + 1) * per_cta);
+    for (int tile = (int)blockIdx.x * per_cta; tile < tile_end; ++tile) {
         const int r = tile * kDbRows + tid;
         const bool live = r < rows;
         int an = 0, v = 0, m = -1;
@@ -261,11 +264,12 @@ static size_t fp32_smem(int F, int k, int H, long long P)
     return sizeof(float) * ((size_t)(din + H + 7 * k + H + din) * kDbStride + (size_t)P);
 }
 
-int launch_decode_bwd(const gs_anchors *A, const gs_camera *cams, const ViewTable &vt, int precision,
-                      const gs_gauss3d *g, const gs_gauss3d_grad *dg, gs_anchor_grad *out, void *ws,
-                      gs_status *st, cudaStream_t s)
+// Reverse of the decoders from the 3D-Gaussian gradients dg, or (dg NULL, BF16)
+// from the splat gradients with the projection's chain rule fused in.
+static int launch_decode_bwd_impl(const gs_anchors *A, const gs_camera *cams, const ViewTable &vt, int precision,
+                                  const gs_gauss3d *g, const gs_gauss3d_grad *dg, const gs_splats *sp,
+                                  const float *sgrad, gs_anchor_grad *out, gs_status *st, cudaStream_t s)
 {
-    (void)ws;
     const long long P = gs_mlp_floats(A->F, A->k, A->hidden);
     cudaMemsetAsync(out->dxyz, 0, sizeof(float) * 3 * (size_t)A->N, s);
     cudaMemsetAsync(out->dfeat, 0, sizeof(float) * (size_t)A->F * A->N, s);
@@ -279,9 +283,19 @@ int launch_decode_bwd(const gs_anchors *A, const gs_camera *cams, const ViewTabl
     f.M = A->M; f.V = vt.V; f.cams = cams; f.view_start = g->view_start; f.row_anchor = g->row_anchor;
     f.mu = g->mu; f.scale = g->scale; f.quat = g->quat; f.opacity = g->opacity; f.colour = g->colour;
     f.st = st; f.cap_rows = g->cap_rows; f.wait_ns = wait_limit_ns();
-    a.dmu = dg->dmu; a.dscale = dg->dscale; a.dquat = dg->dquat; a.dopacity = dg->dopacity; a.dcolour = dg->dcolour;
+    a.dmu = a.dscale = a.dquat = a.dopacity = a.dcolour = nullptr;
+    if (dg) {
+        a.dmu = dg->dmu; a.dscale = dg->dscale; a.dquat = dg->dquat; a.dopacity = dg->dopacity; a.dcolour = dg->dcolour;
+    }
     a.dxyz = out->dxyz; a.dfeat = out->dfeat; a.dls = out->dlog_scaling; a.doff = out->doffsets; a.dmlp = out->dmlp;
+    a.sgrad = dg ? nullptr : sgrad;
+    a.tiles = dg ? nullptr : sp->tiles;
+    for (int v = 0; v < GS_MAX_VIEWS; ++v) {
+        a.W[v] = v < vt.V ? vt.W[v] : 0;
+        a.H[v] = v < vt.V ? vt.H[v] : 0;
+    }
     if (precision == GS_PREC_BF16) return launch_decode_bwd_bf16(a, s);
+    if (!dg) return GS_ERR_UNSUPPORTED;   // the FP32 decoder takes the 3D gradients (see below)
     const size_t smem = fp32_smem(A->F, A->k, A->hidden, P);
     static int configured_smem = 0;
     if ((int)smem > configured_smem) {
@@ -295,6 +309,45 @@ int launch_decode_bwd(const gs_anchors *A, const gs_camera *cams, const ViewTabl
     decode_bwd_fp32_kernel<<<grid, kDbRows, smem, s>>>(a);
     count_launches(1);
     return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+int launch_decode_bwd(const gs_anchors *A, const gs_camera *cams, const ViewTable &vt, int precision,
+                      const gs_gauss3d *g, const gs_gauss3d_grad *dg, gs_anchor_grad *out, void *ws,
+                      gs_status *st, cudaStream_t s)
+{
+    (void)ws;
+    return launch_decode_bwd_impl(A, cams, vt, precision, g, dg, nullptr, nullptr, out, st, s);
+}
+
+// Workspace of the fused reverse: none for the tensor-core path; the FP32 path
+// keeps the candidates' 3D gradients (14 floats each) between its two steps.
+size_t decode_project_bwd_workspace_bytes(int k, long long cap_rows, int precision)
+{
+    if (precision == GS_PREC_BF16) return 0;
+    const size_t C = (size_t)std::max<long long>(cap_rows * k, 1);
+    return align_up(sizeof(float) * 3 * C, 256) * 3 + align_up(sizeof(float) * 4 * C, 256) +
+           align_up(sizeof(float) * C, 256);
+}
+
+int launch_decode_project_bwd(const gs_anchors *A, const gs_camera *cams, const ViewTable &vt, int precision,
+                              const gs_gauss3d *g, const gs_splats *sp, const gs_splat_grad *sgrad,
+                              gs_anchor_grad *out, void *ws, gs_status *st, cudaStream_t s)
+{
+    if (precision == GS_PREC_BF16)
+        return launch_decode_bwd_impl(A, cams, vt, precision, g, nullptr, sp, sgrad->g, out, st, s);
+    // FP32: the projection's chain rule into the workspace, then the decoders' reverse
+    const size_t C = (size_t)std::max<long long>(g->cap_rows * g->k, 1);
+    char *w = reinterpret_cast<char *>(ws);
+    gs_gauss3d_grad dg;
+    size_t o = 0;
+    dg.dmu = reinterpret_cast<float *>(w + o); o += align_up(sizeof(float) * 3 * C, 256);
+    dg.dscale = reinterpret_cast<float *>(w + o); o += align_up(sizeof(float) * 3 * C, 256);
+    dg.dcolour = reinterpret_cast<float *>(w + o); o += align_up(sizeof(float) * 3 * C, 256);
+    dg.dquat = reinterpret_cast<float *>(w + o); o += align_up(sizeof(float) * 4 * C, 256);
+    dg.dopacity = reinterpret_cast<float *>(w + o);
+    const int rc = launch_project_bwd(g, cams, sp, vt, sgrad, &dg, st, s);
+    if (rc != GS_OK) return rc;
+    return launch_decode_bwd_impl(A, cams, vt, precision, g, &dg, nullptr, nullptr, out, st, s);
 }
 
 }  // namespace gs

@@ -30,6 +30,7 @@
 #include <cuda_bf16.h>
 
 #include "gs_internal.cuh"
+#include "proj_bwd.cuh"
 #include "tc05.cuh"
 
 namespace gs {
@@ -263,11 +264,17 @@ __global__ void __launch_bounds__(kBThreads) decode_bwd_tc_kernel(DecodeBwdArgsB
     uint32_t phase = 0;
     bool failed = false, fresh = true;   // fresh: the accumulators hold nothing yet
 
-    for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
+    // each CTA takes a contiguous range of tiles: rows are view-major and partition-sorted inside a
+    // view, so a CTA meets few partitions (the weights are staged, and the weight gradients flushed,
+    // only when the partition changes)
+    const int per_cta = (ntiles + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int tile_end = min(ntiles, ((int)blockIdx.x + 1) * per_cta);
+    for (int tile = (int)blockIdx.x * per_cta; tile < tile_end && !failed; ++tile) {
         // ---- row setup: anchor, partition, (d, |d|) of Eq. 2; U = [f, d/|d|, |d|, 1] as hi + lo
         const int row = tile * kBRows + tid;
-        int an = -1, pm = -1;
+        int an = -1, pm = -1, vw = 0;
         float d0 = 0.f, d1 = 0.f, d2 = 0.f, dl = 1.f;
+        Cam cam;
         if (row < rows) {
             an = __ldg(f.row_anchor + row);
             if (!idx_ok(f.st, an, f.N, 63)) an = -1;
@@ -277,7 +284,9 @@ __global__ void __launch_bounds__(kBThreads) decode_bwd_tc_kernel(DecodeBwdArgsB
             if (!idx_ok(f.st, pm, f.M, 64)) { pm = -1; an = -1; }
         }
         if (an >= 0) {
-            const Cam c = load_cam(f.cams, view_of_row(f.view_start, f.V, row));
+            vw = view_of_row(f.view_start, f.V, row);
+            cam = load_cam(f.cams, vw);
+            const Cam &c = cam;
             float xc[3];
 #pragma unroll
             for (int i = 0; i < 3; ++i) xc[i] = -(c.R[i] * c.t[0] + c.R[3 + i] * c.t[1] + c.R[6 + i] * c.t[2]);
@@ -411,11 +420,25 @@ __global__ void __launch_bounds__(kBThreads) decode_bwd_tc_kernel(DecodeBwdArgsB
                     const float op = tanh_fast(zoc[o] + b2[o]);
                     if (!(op > 0.f)) continue;   // culled by decoding: no gradient
                     live |= 1u << i;
-                    dz[4 * j] = __ldg(a.dopacity + c0 + i) * (1.f - op * op);
+                    // d opacity, d colour: from the candidate's splat gradient (fused with the
+                    // projection's reverse; zero for a splat that covers no tile) or given
+                    float gop, gcol[3];
+                    if (a.sgrad) {
+                        const bool drawn = __ldg(a.tiles + c0 + i) > 0;
+                        const float *sgp = a.sgrad + 9 * (c0 + i);
+                        gop = drawn ? __ldg(sgp + 5) : 0.f;
+#pragma unroll
+                        for (int ch = 0; ch < 3; ++ch) gcol[ch] = drawn ? __ldg(sgp + 6 + ch) : 0.f;
+                    } else {
+                        gop = __ldg(a.dopacity + c0 + i);
+#pragma unroll
+                        for (int ch = 0; ch < 3; ++ch) gcol[ch] = __ldg(a.dcolour + 3 * (c0 + i) + ch);
+                    }
+                    dz[4 * j] = gop * (1.f - op * op);
 #pragma unroll
                     for (int ch = 0; ch < 3; ++ch) {
                         const float sg = sigmoid_fast(zoc[o + 1 + ch] + b2[o + 1 + ch]);
-                        dz[4 * j + 1 + ch] = __ldg(a.dcolour + 3 * (c0 + i) + ch) * sg * (1.f - sg);
+                        dz[4 * j + 1 + ch] = gcol[ch] * sg * (1.f - sg);
                     }
                 }
                 put8_bf16(sm + s.o_A, tc::kmajor_offset(tid, 16 * cc, s.NZ), dz);
@@ -428,9 +451,11 @@ __global__ void __launch_bounds__(kBThreads) decode_bwd_tc_kernel(DecodeBwdArgsB
                 tc::fence_after_sync();
             }
             // ---- 3b. dZ of scale (exp(l) sigmoid) and rotation (normalisation); per-anchor terms
-            float el[6], gls[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, gx[3] = {0.f, 0.f, 0.f};
+            float el[6], gls[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, gx[3] = {0.f, 0.f, 0.f}, xa[3];
 #pragma unroll
             for (int j = 0; j < 6; ++j) el[j] = mine ? expf(__ldg(f.log_scaling + 6 * an + j)) : 0.f;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) xa[j] = mine ? __ldg(f.xyz + 3 * an + j) : 0.f;
             for (int cc = 0; cc < s.Ncov; cc += 16) {
                 float v[16], dz[16];
                 tc::tmem_ld16(tc::tmem_addr(tmem, warp, cc), v);
@@ -441,28 +466,50 @@ __global__ void __launch_bounds__(kBThreads) decode_bwd_tc_kernel(DecodeBwdArgsB
                     for (int e = 0; e < 8; ++e) dz[8 * j + e] = 0.f;
                     if (i >= k || !(live >> i & 1u)) continue;
                     const size_t ci = c0 + i;
+                    const float *off = f.offsets + ((size_t)an * k + i) * 3;
+                    float sgv[3], q[4], dsv[3], dq[4], dmv[3], qd = 0.f;
 #pragma unroll
-                    for (int e = 0; e < 3; ++e) {
-                        const float sg = sigmoid_fast(v[8 * j + e] + b2[o + e]);
-                        const float ds = __ldg(a.dscale + 3 * ci + e);
-                        dz[8 * j + e] = ds * el[3 + e] * sg * (1.f - sg);
-                        gls[3 + e] += ds * el[3 + e] * sg;
-                    }
-                    float q[4], dq[4], qd = 0.f;
+                    for (int e = 0; e < 3; ++e) sgv[e] = sigmoid_fast(v[8 * j + e] + b2[o + e]);
 #pragma unroll
                     for (int e = 0; e < 4; ++e) q[e] = v[8 * j + 3 + e] + b2[o + 3 + e];
                     const float inv = rsqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+                    if (a.sgrad) {
+                        // the projection's reverse on the recomputed Gaussian: mean x_a + offset *
+                        // exp(l[0:3]), scale exp(l[3:6]) sigmoid, unit quaternion
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        dq[e] = __ldg(a.dquat + 4 * ci + e);
-                        qd += q[e] * inv * dq[e];
+                        for (int e = 0; e < 3; ++e) dsv[e] = dmv[e] = 0.f;
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) dq[e] = 0.f;
+                        if (__ldg(a.tiles + ci) > 0) {
+                            const float *sgp = a.sgrad + 9 * ci;
+                            const float sc[3] = {el[3] * sgv[0], el[4] * sgv[1], el[5] * sgv[2]};
+                            const float qu[4] = {q[0] * inv, q[1] * inv, q[2] * inv, q[3] * inv};
+                            proj_bwd_one(cam, (float)a.W[vw], (float)a.H[vw], xa[0] + __ldg(off) * el[0],
+                                         xa[1] + __ldg(off + 1) * el[1], xa[2] + __ldg(off + 2) * el[2], sc, qu,
+                                         __ldg(sgp), __ldg(sgp + 1), __ldg(sgp + 2), __ldg(sgp + 3), __ldg(sgp + 4),
+                                         dmv, dsv, dq);
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 3; ++e) {
+                            dsv[e] = __ldg(a.dscale + 3 * ci + e);
+                            dmv[e] = __ldg(a.dmu + 3 * ci + e);
+                        }
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) dq[e] = __ldg(a.dquat + 4 * ci + e);
                     }
 #pragma unroll
+                    for (int e = 0; e < 3; ++e) {
+                        dz[8 * j + e] = dsv[e] * el[3 + e] * sgv[e] * (1.f - sgv[e]);
+                        gls[3 + e] += dsv[e] * el[3 + e] * sgv[e];
+                    }
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) qd += q[e] * inv * dq[e];
+#pragma unroll
                     for (int e = 0; e < 4; ++e) dz[8 * j + 3 + e] = (dq[e] - q[e] * inv * qd) * inv;
-                    const float *off = f.offsets + ((size_t)an * k + i) * 3;
 #pragma unroll
                     for (int e = 0; e < 3; ++e) {
-                        const float gm = __ldg(a.dmu + 3 * ci + e);
+                        const float gm = dmv[e];
                         gx[e] += gm;
                         atomicAdd(a.doff + ((size_t)an * k + i) * 3 + e, gm * el[e]);
                         gls[e] += gm * __ldg(off + e) * el[e];

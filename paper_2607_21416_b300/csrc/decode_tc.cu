@@ -166,7 +166,12 @@ __global__ void __launch_bounds__(kTThreads) decode_tc_kernel(DecodeArgs a, TcSh
     uint32_t phase = 0;
     bool failed = false;   // an MMA completion wait ran out; `phase` is then the parity it waited for
 
-    for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
+    // each CTA takes a contiguous range of tiles: rows are view-major and partition-sorted inside a
+    // view, so a CTA meets few partitions (the weights are staged, and the weight gradients flushed,
+    // only when the partition changes)
+    const int per_cta = (ntiles + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int tile_end = min(ntiles, ((int)blockIdx.x + 1) * per_cta);
+    for (int tile = (int)blockIdx.x * per_cta; tile < tile_end && !failed; ++tile) {
         // ---- this thread's row: anchor, partition, view inputs of Eq. 2, U row
         const int row = tile * kTRows + tid;
         int an = -1, pm = -1;

@@ -324,9 +324,9 @@ int gs_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *s
 {
     ViewTable vt;
     if (!check_gauss(g) || !cams || !sp || !sp->rec || !sp->tiles || !bins || !bins->vals || !bins->ranges ||
-        !bins->n_pairs || !image || !d_image || !sgrad || !sgrad->g || !out || !out->dmu || !out->dscale ||
-        !out->dquat || !out->dopacity || !out->dcolour || !status || !make_view_table(views, V, &vt) ||
-        sp->cap < g->cap_rows * (long long)g->k)
+        !bins->n_pairs || !image || !d_image || !sgrad || !sgrad->g ||
+        (out && (!out->dmu || !out->dscale || !out->dquat || !out->dopacity || !out->dcolour)) || !status ||
+        !make_view_table(views, V, &vt) || sp->cap < g->cap_rows * (long long)g->k)
         return GS_ERR_INVALID_ARG;
     if ((chunk != 0 && (chunk < 256 || chunk > (1 << 24))) || !ws ||
         (reinterpret_cast<uintptr_t>(ws) & 255) != 0 ||
@@ -334,6 +334,38 @@ int gs_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *s
         return GS_ERR_INVALID_ARG;
     return launch_render_bwd(g, cams, sp, bins, vt, chunk_len(chunk), ws, image, d_image, last, sgrad, out, status,
                              (cudaStream_t)stream);
+}
+
+int gs_project_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *sp, const gs_view *views,
+                   int32_t V, const gs_splat_grad *sgrad, gs_gauss3d_grad *out, gs_status *status, void *stream)
+{
+    ViewTable vt;
+    if (!check_gauss(g) || !cams || !sp || !sp->tiles || !sgrad || !sgrad->g || !out || !out->dmu || !out->dscale ||
+        !out->dquat || !out->dopacity || !out->dcolour || !status || !make_view_table(views, V, &vt) ||
+        sp->cap < g->cap_rows * (long long)g->k)
+        return GS_ERR_INVALID_ARG;
+    return launch_project_bwd(g, cams, sp, vt, sgrad, out, status, (cudaStream_t)stream);
+}
+
+size_t gs_decode_project_bwd_workspace(int32_t k, int64_t cap_rows, int32_t precision)
+{
+    return decode_project_bwd_workspace_bytes(k, cap_rows, precision);
+}
+
+int gs_decode_project_bwd(const gs_anchors *A, const gs_camera *cams, const gs_view *views, int32_t V,
+                          int32_t precision, const gs_gauss3d *g, const gs_splats *sp, const gs_splat_grad *sgrad,
+                          gs_anchor_grad *out, void *ws, size_t ws_bytes, gs_status *status, void *stream)
+{
+    ViewTable vt;
+    if (!check_anchors(A) || !cams || !check_gauss(g) || !g->row_anchor || !sp || !sp->tiles || !sgrad ||
+        !sgrad->g || !out || !out->dxyz || !out->dfeat || !out->dlog_scaling || !out->doffsets || !out->dmlp ||
+        !status || !make_view_table(views, V, &vt) || g->k != A->k || sp->cap < g->cap_rows * (long long)g->k)
+        return GS_ERR_INVALID_ARG;
+    if (precision != GS_PREC_FP32 && precision != GS_PREC_BF16) return GS_ERR_INVALID_ARG;
+    if (ws_bytes < decode_project_bwd_workspace_bytes(g->k, g->cap_rows, precision) ||
+        (ws_bytes > 0 && (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0)))
+        return GS_ERR_INVALID_ARG;
+    return launch_decode_project_bwd(A, cams, vt, precision, g, sp, sgrad, out, ws, status, (cudaStream_t)stream);
 }
 
 int gs_decode_bwd(const gs_anchors *A, const gs_camera *cams, const gs_view *views, int32_t V, int32_t precision,

@@ -26,6 +26,11 @@ struct DecodeBwdArgsB {
     DecodeArgs f;   // forward inputs (the candidate outputs are not read)
     const float *dmu, *dscale, *dquat, *dopacity, *dcolour;
     float *dxyz, *dfeat, *dls, *doff, *dmlp;
+    // fused with the projection's reverse (tcgen05 path): the splat gradients
+    // [C][9] and tile counts replace the five gradients above (NULL: not fused)
+    const float *sgrad;
+    const int32_t *tiles;
+    int W[GS_MAX_VIEWS], H[GS_MAX_VIEWS];
 };
 int launch_decode_bwd_bf16(const DecodeBwdArgsB &a, cudaStream_t s);
 
@@ -74,8 +79,14 @@ int launch_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splat
                       const ViewTable &vt, int L, void *ws, const float *image, const float *d_image,
                       const int32_t *last, gs_splat_grad *sgrad, gs_gauss3d_grad *out, gs_status *st,
                       cudaStream_t s);
+int launch_project_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *sp, const ViewTable &vt,
+                       const gs_splat_grad *sgrad, gs_gauss3d_grad *out, gs_status *st, cudaStream_t s);
 
 size_t decode_bwd_workspace_bytes(int N, int V, int M, long long cap_rows);
+size_t decode_project_bwd_workspace_bytes(int k, long long cap_rows, int precision);
+int launch_decode_project_bwd(const gs_anchors *A, const gs_camera *cams, const ViewTable &vt, int precision,
+                              const gs_gauss3d *g, const gs_splats *sp, const gs_splat_grad *sgrad,
+                              gs_anchor_grad *out, void *ws, gs_status *st, cudaStream_t s);
 int launch_decode_bwd(const gs_anchors *A, const gs_camera *cams, const ViewTable &vt, int precision,
                       const gs_gauss3d *g, const gs_gauss3d_grad *dg, gs_anchor_grad *out, void *ws,
                       gs_status *st, cudaStream_t s);

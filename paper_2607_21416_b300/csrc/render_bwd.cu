@@ -10,7 +10,7 @@
 // multi-chunk tile starts from the per-chunk state the forward left in the
 // render workspace.  Per-splat sums are reduced across the warp (shuffles)
 // before one global atomicAdd per warp and quantity.
-#include "cov2d_f2.cuh"
+#include "proj_bwd.cuh"
 #include "render_common.cuh"
 
 namespace gs {
@@ -308,120 +308,10 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(ProjBwdArgs a, ViewTab
             const int v = view_of_row(a.view_start, a.V, (int)(c / a.k));
             const Cam cm = load_cam(a.cams, v);
             const float m0 = __ldg(a.mu + 3 * c), m1 = __ldg(a.mu + 3 * c + 1), m2 = __ldg(a.mu + 3 * c + 2);
-            const float px = cm.R[0] * m0 + cm.R[1] * m1 + cm.R[2] * m2 + cm.t[0];
-            const float py = cm.R[3] * m0 + cm.R[4] * m1 + cm.R[5] * m2 + cm.t[1];
-            const float pz = cm.R[6] * m0 + cm.R[7] * m1 + cm.R[8] * m2 + cm.t[2];
-            const float qw = __ldg(a.quat + 4 * c), qx = __ldg(a.quat + 4 * c + 1),
-                        qy = __ldg(a.quat + 4 * c + 2), qz = __ldg(a.quat + 4 * c + 3);
-            float Rq[9];
-            Rq[0] = 1.f - 2.f * (qy * qy + qz * qz); Rq[1] = 2.f * (qx * qy - qw * qz); Rq[2] = 2.f * (qx * qz + qw * qy);
-            Rq[3] = 2.f * (qx * qy + qw * qz); Rq[4] = 1.f - 2.f * (qx * qx + qz * qz); Rq[5] = 2.f * (qy * qz - qw * qx);
-            Rq[6] = 2.f * (qx * qz - qw * qy); Rq[7] = 2.f * (qy * qz + qw * qx); Rq[8] = 1.f - 2.f * (qx * qx + qy * qy);
             const float s[3] = {__ldg(a.scale + 3 * c), __ldg(a.scale + 3 * c + 1), __ldg(a.scale + 3 * c + 2)};
-            float M[9];   // Rq diag(s)
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-                for (int j = 0; j < 3; ++j) M[3 * i + j] = Rq[3 * i + j] * s[j];
-            float S3[9];
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-                for (int j = 0; j < 3; ++j)
-                    S3[3 * i + j] = M[3 * i] * M[3 * j] + M[3 * i + 1] * M[3 * j + 1] + M[3 * i + 2] * M[3 * j + 2];
-            const float W = (float)vt.W[v], H = (float)vt.H[v];
-            const float limx = kTanClamp * (W / (2.f * cm.fx)), limy = kTanClamp * (H / (2.f * cm.fy));
-            const float ux = px / pz, uy = py / pz;
-            const bool inx = ux >= -limx && ux <= limx, iny = uy >= -limy && uy <= limy;
-            const float txz = fminf(fmaxf(ux, -limx), limx), tyz = fminf(fmaxf(uy, -limy), limy);
-            const float fx = cm.fx, fy = cm.fy, z = pz;
-            const float J[6] = {fx / z, 0.f, -fx * txz / z, 0.f, fy / z, -fy * tyz / z};
-            float T[6];
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 3; ++j)
-                    T[3 * i + j] = J[3 * i] * cm.R[j] + J[3 * i + 1] * cm.R[3 + j] + J[3 * i + 2] * cm.R[6 + j];
-            float TS[6];   // T S3
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 3; ++j)
-                    TS[3 * i + j] = T[3 * i] * S3[j] + T[3 * i + 1] * S3[3 + j] + T[3 * i + 2] * S3[6 + j];
-            const float ca = TS[0] * T[0] + TS[1] * T[1] + TS[2] * T[2] + kLowpass;
-            const float cb = TS[0] * T[3] + TS[1] * T[4] + TS[2] * T[5];
-            const float cc = TS[3] * T[3] + TS[4] * T[4] + TS[5] * T[5] + kLowpass;
-            float da, db, dcv;
-            const float det = ca * cc - cb * cb;
-            if (det < 1e-3f * ca * cc) {   // near-degenerate: the forward's compensated covariance, FP64 inverse
-                double A, Bv, Cv;
-                cov2d_compensated(cm, m0, m1, m2, qw, qx, qy, qz, s[0], s[1], s[2], limx, limy, &A, &Bv, &Cv);
-                const double dd = A * Cv - Bv * Bv, d2 = dd * dd;
-                da = (float)((gka * (-Cv * Cv) + gkb * (Bv * Cv) + gkc * (-Bv * Bv)) / d2);
-                db = (float)((gka * (2 * Bv * Cv) + gkb * (-(A * Cv + Bv * Bv)) + gkc * (2 * A * Bv)) / d2);
-                dcv = (float)((gka * (-Bv * Bv) + gkb * (A * Bv) + gkc * (-A * A)) / d2);
-            } else {
-                const float i2 = 1.f / (det * det);
-                da = (gka * (-cc * cc) + gkb * (cb * cc) + gkc * (-cb * cb)) * i2;
-                db = (gka * (2.f * cb * cc) + gkb * (-(ca * cc + cb * cb)) + gkc * (2.f * ca * cb)) * i2;
-                dcv = (gka * (-cb * cb) + gkb * (ca * cb) + gkc * (-ca * ca)) * i2;
-            }
-            const float G2[4] = {da, 0.5f * db, 0.5f * db, dcv};
-            // dS3 = T^T G2 T ; dT = 2 G2 T S3
-            float GT[6];   // G2 T
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 3; ++j) GT[3 * i + j] = G2[2 * i] * T[j] + G2[2 * i + 1] * T[3 + j];
-            float dS3[9];
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-                for (int j = 0; j < 3; ++j) dS3[3 * i + j] = T[i] * GT[j] + T[3 + i] * GT[3 + j];
-            float dT[6];
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 3; ++j)
-                    dT[3 * i + j] = 2.f * (G2[2 * i] * TS[j] + G2[2 * i + 1] * TS[3 + j]);
-            float dJ[6];
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 3; ++j)
-                    dJ[3 * i + j] = dT[3 * i] * cm.R[3 * j] + dT[3 * i + 1] * cm.R[3 * j + 1] + dT[3 * i + 2] * cm.R[3 * j + 2];
-            const float iz2 = 1.f / (z * z);
-            float dp0 = 0.f, dp1 = 0.f, dp2 = 0.f;
-            dp2 += dJ[0] * (-fx * iz2) + dJ[4] * (-fy * iz2);
-            dp2 += dJ[2] * (fx * txz * iz2);
-            if (inx) { dp0 += dJ[2] * (-fx * iz2); dp2 += dJ[2] * (fx * px * iz2 / z); }
-            dp2 += dJ[5] * (fy * tyz * iz2);
-            if (iny) { dp1 += dJ[5] * (-fy * iz2); dp2 += dJ[5] * (fy * py * iz2 / z); }
-            dp0 += gmx * fx / z;
-            dp1 += gmy * fy / z;
-            dp2 += gmx * (-fx * px * iz2) + gmy * (-fy * py * iz2);
-#pragma unroll
-            for (int j = 0; j < 3; ++j) dmu[j] = cm.R[j] * dp0 + cm.R[3 + j] * dp1 + cm.R[6 + j] * dp2;
-            // dM = 2 dS3 M ; dscale_j = sum_i dM_ij Rq_ij ; dRq_ij = dM_ij s_j
-            float dRq[9];
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                float acc = 0.f;
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    const float dM = 2.f * (dS3[3 * i] * M[j] + dS3[3 * i + 1] * M[3 + j] + dS3[3 * i + 2] * M[6 + j]);
-                    acc += dM * Rq[3 * i + j];
-                    dRq[3 * i + j] = dM * s[j];
-                }
-                ds[j] = acc;
-            }
-            dq[0] = 2.f * (-qz * dRq[1] + qy * dRq[2] + qz * dRq[3] - qx * dRq[5] - qy * dRq[6] + qx * dRq[7]);
-            dq[1] = 2.f * (qy * dRq[1] + qz * dRq[2] + qy * dRq[3] - 2.f * qx * dRq[4] - qw * dRq[5] +
-                           qz * dRq[6] + qw * dRq[7] - 2.f * qx * dRq[8]);
-            dq[2] = 2.f * (-2.f * qy * dRq[0] + qx * dRq[1] + qw * dRq[2] + qx * dRq[3] + qz * dRq[5] -
-                           qw * dRq[6] + qz * dRq[7] - 2.f * qy * dRq[8]);
-            dq[3] = 2.f * (-2.f * qz * dRq[0] - qw * dRq[1] + qx * dRq[2] + qw * dRq[3] - 2.f * qz * dRq[4] +
-                           qy * dRq[5] + qx * dRq[6] + qy * dRq[7]);
+            const float q[4] = {__ldg(a.quat + 4 * c), __ldg(a.quat + 4 * c + 1), __ldg(a.quat + 4 * c + 2),
+                                __ldg(a.quat + 4 * c + 3)};
+            proj_bwd_one(cm, (float)vt.W[v], (float)vt.H[v], m0, m1, m2, s, q, gmx, gmy, gka, gkb, gkc, dmu, ds, dq);
         }
 #pragma unroll
         for (int j = 0; j < 3; ++j) { a.dmu[3 * c + j] = dmu[j]; a.dscale[3 * c + j] = ds[j]; }
@@ -433,13 +323,33 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(ProjBwdArgs a, ViewTab
 }
 
 // ------------------------------------------------------------ launcher
+// Zeroes the splat gradients of the candidates that cover a tile (the only
+// ones the reverse pass adds into, and the only ones read afterwards).
+__global__ void __launch_bounds__(256) zero_sgrad_kernel(const int32_t *__restrict__ tiles,
+                                                         const int32_t *__restrict__ view_start, int V, int k,
+                                                         long long cap_cand, float *__restrict__ sgrad,
+                                                         const gs_status *st)
+{
+    if (has_error(st)) return;
+    const long long C = std::min<long long>((long long)__ldg(view_start + V) * k, cap_cand);
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < C; c += (long long)gridDim.x * blockDim.x)
+        if (__ldg(tiles + c) > 0) {
+            float *g = sgrad + 9 * c;
+#pragma unroll
+            for (int j = 0; j < 9; ++j) g[j] = 0.f;
+        }
+}
+
 int launch_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *sp, const gs_bins *bins,
                       const ViewTable &vt, int L, void *ws, const float *image, const float *d_image,
                       const int32_t *last, gs_splat_grad *sgrad, gs_gauss3d_grad *out, gs_status *st,
                       cudaStream_t s)
 {
     const long long cap_cand = g->cap_rows * (long long)g->k;
-    cudaMemsetAsync(sgrad->g, 0, sizeof(float) * 9 * (size_t)cap_cand, s);
+    const int zgrid = (int)std::max<long long>(1, std::min<long long>((cap_cand + 255) / 256,
+                                                                      (long long)sm_count() * 16));
+    zero_sgrad_kernel<<<zgrid, 256, 0, s>>>(sp->tiles, g->view_start, vt.V, g->k, cap_cand, sgrad->g, st);
+    count_launches(1);
     const float4 *rec = reinterpret_cast<const float4 *>(sp->rec);
     if (vt.total_tiles > 0) {
         const RenderPlan plan = render_plan(vt, bins->cap_pairs, L, ws);
@@ -449,6 +359,14 @@ int launch_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splat
             std::min<long long>(sp->cap, cap_cand), st);
         count_launches(1);
     }
+    if (!out) return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+    return launch_project_bwd(g, cams, sp, vt, sgrad, out, st, s);
+}
+
+int launch_project_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *sp, const ViewTable &vt,
+                       const gs_splat_grad *sgrad, gs_gauss3d_grad *out, gs_status *st, cudaStream_t s)
+{
+    const long long cap_cand = g->cap_rows * (long long)g->k;
     ProjBwdArgs a;
     a.mu = g->mu; a.scale = g->scale; a.quat = g->quat; a.view_start = g->view_start; a.tiles = sp->tiles;
     a.cams = cams; a.sgrad = sgrad->g; a.k = g->k; a.V = vt.V; a.cap_cand = cap_cand;

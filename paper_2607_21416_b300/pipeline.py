@@ -79,6 +79,7 @@ class RenderPass:
             self.dec_ws = api.workspace(api.decode_workspace(self.anchors, self.views, self.cap_rows), dev)
             self.agrad = api.AnchorGrad.like(self.anchors)
             self.dbwd_ws = api.workspace(api.decode_bwd_workspace(self.anchors, self.views, self.cap_rows), dev)
+            self.dpbwd_ws = api.workspace(api.decode_project_bwd_workspace(self.g, self.precision), dev)
         self.splats = api.Splats.alloc(C_, dev)
         self.bins = api.Bins.alloc(self.cap_pairs, self.views.total_tiles, dev, keys=self.want_keys)
         self.sort_ws = api.workspace(api.bin_sort_workspace(self.views, C_, self.cap_pairs), dev)
@@ -118,14 +119,21 @@ class RenderPass:
         return self.loss
 
     def backward(self, d_image=None, stream=None):
+        """Reverse of the iteration: the compositing's (splat gradients), then
+        for anchors the projection's and the decoders' in one call (fused on
+        the tensor-core path), for explicit Gaussians the projection's."""
+        dimg = self.d_image if d_image is None else d_image
+        last = self.last if self.store_state else None
+        if self.anchors is not None:
+            api.render_bwd(self.g, self.splats, self.bins, self.views, self.image, dimg, self.sgrad, None,
+                           self.status, self.render_ws, self.chunk, last, stream)
+            api.decode_project_bwd(self.anchors, self.views, self.g, self.splats, self.sgrad, self.agrad,
+                                   self.dpbwd_ws, self.status, self.precision, stream)
+            return self.agrad
         if self.ggrad is None or self.ggrad.dmu.shape[0] != self.g.mu.shape[0]:
             self.ggrad = api.Gauss3DGrad.like(self.g)
-        dimg = self.d_image if d_image is None else d_image
         api.render_bwd(self.g, self.splats, self.bins, self.views, self.image, dimg, self.sgrad, self.ggrad,
-                       self.status, self.render_ws, self.chunk, self.last if self.store_state else None, stream)
-        if self.anchors is not None:
-            api.decode_bwd(self.anchors, self.views, self.g, self.ggrad, self.agrad, self.dbwd_ws,
-                           self.status, self.precision, stream)
+                       self.status, self.render_ws, self.chunk, last, stream)
         return self.ggrad
 
     def step(self, target, stream=None):
@@ -156,7 +164,8 @@ class RenderPass:
                 raise L.GsError(f"stage {where}", code)
             if where == 1:
                 self.cap_rows = int(math.ceil(needed * 1.1)) + 16
-                self.cap_pairs = max(self.cap_pairs, 4 * self.cap_rows * self.k)
+                # one pair per candidate at least; a pair overflow on the next try sizes them exactly
+                self.cap_pairs = max(self.cap_pairs, self.cap_rows * self.k)
             else:
                 self.cap_pairs = int(math.ceil(needed * 1.15)) + 1024
             self._alloc()

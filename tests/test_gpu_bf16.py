@@ -142,3 +142,62 @@ def test_bf16_decode_bwd_close_to_oracle(make):
         cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-300)
         rel = np.linalg.norm(a - b) / (np.linalg.norm(b) + 1e-300)
         assert cos >= 0.999 and rel <= 3e-2, f"{name}: cosine {cos:.5f}, relative error {rel:.3e}"
+
+
+@pytest.mark.parametrize("make", [lambda: scenes.tiny_corridor(seed=0, n_anchors=900, hidden=16),
+                                  scenes.anchor_single_view, small_partitions])
+def test_bf16_fused_projection_and_decode_bwd(make):
+    """gs_decode_project_bwd with the tensor-core decoder (the projection's
+    chain rule applied inside the reverse decoder to the recomputed
+    Gaussians) against the FP64 oracle's projection and decoder reverse on
+    the same splat gradients (cosine >= 0.999, relative error <= 3e-2), and
+    against the unfused GPU path (gs_project_bwd then gs_decode_bwd) on the
+    same inputs (cosine >= 0.9999)."""
+    s = make()
+    A = api.Anchors.from_scene(s)
+    vw = api.Views(s.cams, s.wh)
+    cap = s.N * s.V
+    g = api.Gauss3D.alloc(cap, s.k, s.V)
+    st = api.new_status()
+    api.decode(A, vw, g, api.workspace(api.decode_workspace(A, vw, cap)), st, L.GS_PREC_BF16)
+    sp = api.Splats.alloc(cap * s.k)
+    api.project(g, vw, sp, st)
+    torch.cuda.synchronize()
+    assert api.read_status(st)[0] == 0
+    dec = O.decode(s)
+    prj = O.project(dec.mu, dec.scale, dec.quat, dec.opacity, s.cams, s.wh, dec.view_start, s.k)
+    Cn = dec.opacity.shape[0]
+    tiles = to_np(sp.tiles)[:Cn]
+    # splat gradients where both sides draw the candidate, away from every threshold
+    keep = ((prj.tiles > 0) & (tiles > 0) & (prj.flag == 0) & (dec.cand_flag == 0) &
+            (np.abs(dec.opacity) > 3e-2)).astype(np.float64)
+    assert keep.sum() > 100
+    rng = np.random.default_rng(6)
+    sg = (rng.normal(size=(Cn, 9)) * keep[:, None]).astype(np.float32)
+    sg[:, 2:5] *= 1e-2   # conic gradients at the scale of the mean gradients
+    sgrad = torch.zeros(cap * s.k, 9, device="cuda")
+    sgrad[:Cn] = torch.as_tensor(sg).cuda()
+    fused = api.AnchorGrad.like(A)
+    api.decode_project_bwd(A, vw, g, sp, sgrad, fused, api.workspace(api.decode_project_bwd_workspace(g, L.GS_PREC_BF16)),
+                           st, L.GS_PREC_BF16)
+    dg = api.Gauss3DGrad.like(g)
+    api.project_bwd(g, sp, vw, sgrad, dg, st)
+    unfused = api.AnchorGrad.like(A)
+    api.decode_bwd(A, vw, g, dg, unfused, api.workspace(api.decode_bwd_workspace(A, vw, cap)), st, L.GS_PREC_BF16)
+    torch.cuda.synchronize()
+    assert api.read_status(st)[0] == 0
+    sg64 = sg.astype(np.float64)
+    dmu, ds, dq = O.project_bwd(dec.mu, dec.scale, dec.quat, prj.status * (prj.tiles > 0), s.cams, s.wh,
+                                dec.view_start, sg64[:, 0:2], sg64[:, 2:5], s.k)
+    want = O.decode_bwd(s, dec, dmu, ds, dq, sg64[:, 5], sg64[:, 6:9])
+    for name, key in (("dxyz", "xyz"), ("dfeat", "feat"), ("dlog_scaling", "log_scaling"),
+                      ("doffsets", "offsets"), ("dmlp", "mlp")):
+        a = to_np(getattr(fused, name)).ravel().astype(np.float64)
+        b = want[key].ravel()
+        u = to_np(getattr(unfused, name)).ravel().astype(np.float64)
+        cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-300)
+        rel = np.linalg.norm(a - b) / (np.linalg.norm(b) + 1e-300)
+        cos_u = a @ u / (np.linalg.norm(a) * np.linalg.norm(u) + 1e-300)
+        print(f"[fused] {name}: cosine {cos:.6f} / {cos_u:.7f} (oracle / unfused), relative error {rel:.3e}")
+        assert cos >= 0.999 and rel <= 3e-2, f"{name}: cosine {cos:.5f}, relative error {rel:.3e}"
+        assert cos_u >= 0.9999, f"{name}: cosine to the unfused path {cos_u:.6f}"
