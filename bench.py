@@ -221,9 +221,13 @@ def run_ours(args, rank, world, dist):
     n_rows, n_pairs = rp.n_rows(), rp.n_pairs()
     counts = work_counts(rp)      # exact work of one iteration (untimed)
     stream = torch.cuda.Stream()
-    # decode_bwd: the projection's and the decoders' reverse in one call (gs_decode_project_bwd; the
-    # tensor-core path fuses them); explicit Gaussians: the projection's reverse (gs_project_bwd)
-    names = ["decode", "project", "bin_sort", "render_fwd", "l1", "render_bwd", "decode_bwd"]
+    # anchors: decode_project = visibility, decoding and projection in one call (gs_decode_project; the
+    # tensor-core decoder writes the splat records itself) and decode_bwd = the projection's and the
+    # decoders' reverse in one call (gs_decode_project_bwd); explicit Gaussians: project / project_bwd
+    if anchors is not None:
+        names = ["decode_project", "bin_sort", "render_fwd", "l1", "render_bwd", "decode_bwd"]
+    else:
+        names = ["project", "bin_sort", "render_fwd", "l1", "render_bwd", "project_bwd"]
     ev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(len(names) + 1)]
     shapes = ms.tuning if ms is not None and ms.tuning is not None else None
 
@@ -231,20 +235,20 @@ def run_ours(args, rank, world, dist):
         ev[0].record()
         rp.status.zero_()
         if anchors is not None:
-            api.decode(anchors, views, rp.g, rp.dec_ws, rp.status, prec)
+            api.decode_project(anchors, views, rp.g, rp.splats, rp.dec_ws, rp.status, prec)
+        else:
+            api.project(rp.g, views, rp.splats, rp.status)
         ev[1].record()
-        api.project(rp.g, views, rp.splats, rp.status)
-        ev[2].record()
         api.bin_sort(rp.splats, rp.g, views, rp.bins, rp.sort_ws, rp.status)
-        ev[3].record()
+        ev[2].record()
         api.render_fwd(rp.splats, rp.bins, views, rp.bg, rp.image, rp.status, rp.render_ws, rp.chunk,
                        rp.T_final, rp.last)
-        ev[4].record()
+        ev[3].record()
         api.l1_loss(rp.image, target, views, rp.loss, rp.d_image)
-        ev[5].record()
+        ev[4].record()
         api.render_bwd(rp.g, rp.splats, rp.bins, views, rp.image, rp.d_image, rp.sgrad, None, rp.status,
                        rp.render_ws, rp.chunk, rp.last)
-        ev[6].record()
+        ev[5].record()
         if anchors is not None:
             api.decode_project_bwd(anchors, views, rp.g, rp.splats, rp.sgrad, rp.agrad, rp.dpbwd_ws, rp.status,
                                    prec)
@@ -252,7 +256,7 @@ def run_ours(args, rank, world, dist):
             if rp.ggrad is None:
                 rp.ggrad = api.Gauss3DGrad.like(rp.g)
             api.project_bwd(rp.g, rp.splats, views, rp.sgrad, rp.ggrad, rp.status)
-        ev[7].record()
+        ev[6].record()
 
     # warm the launch path once eagerly (sets kernel attributes), then capture, with the tuned shapes
     prev_shapes = api.get_tuning()
@@ -392,7 +396,12 @@ def run_ours(args, rank, world, dist):
             return statistics.mean(ts)
 
         adam_ms = timed(opt.step)
-        stats_ms = timed(lambda: stats.accumulate(rp))
+        if not rp.gaussians_written:   # the timed step kept no 3D Gaussians: decode them (untimed)
+            api.decode(anchors, views, rp.g, rp.dec_ws, rp.status, prec)
+            torch.cuda.synchronize()
+        stats_ms = timed(lambda: api.densify_stats(rp.g, rp.views, rp.splats, rp.sgrad, stats.N, stats.grad_accum,
+                                                   stats.offset_denom, stats.opacity_accum, stats.anchor_denom,
+                                                   rp.status))
         hbm, hbm_of = hbm_peak()
         gbs = 28 * n_par / (adam_ms * 1e-3) / 1e9
         optim = {"adam_ms": adam_ms, "parameters": n_par, "densify_stats_ms": stats_ms,
@@ -508,7 +517,7 @@ def run_ours(args, rank, world, dist):
         del passes
 
     stages = {n: statistics.mean(v) for n, v in stage_ms.items()}
-    dom = max(("render_fwd", "render_bwd", "bin_sort", "decode", "decode_bwd"), key=lambda n: stages[n])
+    dom = max((n for n in names if n != "l1"), key=lambda n: stages[n])
     roof = roofline(dom, stages[dom], counts, n_pairs, n_rows, rp, scene, measured_peaks())
     if roof.get("bound") == "alu":
         roof["peak_measured"] = api.probe_peak(0) / 1e12   # FP32 FMA issue rate of this device
@@ -579,19 +588,20 @@ def roofline(dom, ms, counts, n_pairs, n_rows, rp, scene, peaks):
                 "traffic": profiled_traffic("render_bwd_kernel_keyframe_batch_8x1241x376.md",
                                             ("render_bwd.cu", "render_common.cuh")),
                 "work_per_launch": f"{exf} examined + {comp} composited pixel-splat pairs"}
-    if dom == "project_bwd":
-        C_ = n_rows * scene.k if scene.k else n_rows
-        byts = C_ * (4 + 9 * 4 + 40 + 56)
-        a = byts / (ms * 1e-3) / 1e9
-        return {"kernel": "project_bwd_kernel", "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s",
-                "frac": a / hbm, "traffic": None, "work_per_launch": f"{C_} candidates x 136 B"}
     if dom == "bin_sort":
         S = n_rows * (scene.k or 1)
         byts = S * 4 * 2 + n_pairs * 8 * 2 + n_pairs * 4
         a = byts / (ms * 1e-3) / 1e9
         return {"kernel": "bin_sort", "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s",
                 "frac": a / hbm, "traffic": None, "work_per_launch": f"{n_pairs} pairs"}
-    flops = n_rows * 13952 * (1 if dom == "decode" else 2)
+    if dom in ("project", "project_bwd"):
+        C_ = n_rows * (scene.k or 1)
+        per = 56 + 52 if dom == "project" else 4 + 36 + 40 + 56
+        byts = C_ * per
+        a = byts / (ms * 1e-3) / 1e9
+        return {"kernel": dom + "_kernel", "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s",
+                "frac": a / hbm, "traffic": None, "work_per_launch": f"{C_} candidates x {per} B"}
+    flops = n_rows * 13952 * (1 if dom == "decode_project" else 2)
     a = flops / (ms * 1e-3) / 1e12
     pk = peaks.get("bf16_tflops_sustained", 1400.0)
     return {"kernel": dom, "bound": "tensor", "achieved": a, "peak": pk, "unit": "TFLOP/s",

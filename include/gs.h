@@ -260,6 +260,20 @@ int gs_decode_noalloc(const gs_anchors *A, const gs_camera *cams, const gs_view 
 int gs_project(const gs_gauss3d *g, const gs_camera *cams, const gs_view *views, int32_t V,
                gs_splats *out, gs_status *status, void *stream);
 
+/* gs_decode followed by gs_project in one call: visible rows, then each
+ * candidate's splat record (same arithmetic, same records).  With
+ * GS_PREC_BF16 the tensor-core decoder projects each candidate in its
+ * epilogue and writes the records directly: the 3D Gaussians never reach
+ * device memory and g's candidate arrays (mu, scale, quat, opacity, colour)
+ * are left untouched -- g->row_anchor and g->view_start are written, as the
+ * reverse pass (gs_decode_project_bwd) needs them.  With GS_PREC_FP32 the two
+ * calls run one after the other and g's candidate arrays hold the decoded
+ * Gaussians.  Arguments as in gs_decode and gs_project (sp->rec 16-byte
+ * aligned, sp->cap >= g->cap_rows k); workspace: gs_decode_workspace. */
+int gs_decode_project(const gs_anchors *A, const gs_camera *cams, const gs_view *views, int32_t V,
+                      int32_t precision, gs_gauss3d *g, gs_splats *sp, void *ws, size_t ws_bytes,
+                      gs_status *status, void *stream);
+
 /* Tile binning and sort of the tile-based differentiable rasterizer the
  * paper renders with (Sec. II, the 3DGS rasterizer it builds on; Sec. III-A,
  * Eq. 1 composites each pixel's splats front to back, so every tile needs

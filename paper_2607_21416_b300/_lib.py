@@ -111,6 +111,8 @@ EXPORTS = {
     "gs_photometric_loss": (C.c_int, [vp, vp, P(gs_view), i32, C.c_float, vp, sz, vp, vp, vp]),
     "gs_render_bwd": (C.c_int, [P(gs_gauss3d), vp, P(gs_splats), P(gs_bins), P(gs_view), i32,
                                 i32, vp, sz, vp, vp, vp, P(gs_splat_grad), P(gs_gauss3d_grad), vp, vp]),
+    "gs_decode_project": (C.c_int, [P(gs_anchors), vp, P(gs_view), i32, i32, P(gs_gauss3d), P(gs_splats), vp,
+                                    sz, vp, vp]),
     "gs_project_bwd": (C.c_int, [P(gs_gauss3d), vp, P(gs_splats), P(gs_view), i32, P(gs_splat_grad),
                                  P(gs_gauss3d_grad), vp, vp]),
     "gs_decode_project_bwd_workspace": (sz, [i32, i64, i32]),

@@ -258,6 +258,17 @@ def decode_workspace(anchors: Anchors, views: Views, cap_rows):
     return int(L.load().gs_decode_workspace(anchors.N, views.V, anchors.M, cap_rows))
 
 
+def decode_project(anchors: Anchors, views: Views, g: Gauss3D, sp: Splats, ws, status, precision=L.GS_PREC_FP32,
+                   stream=None):
+    """Visible rows, decoding and projection in one call (the tensor-core
+    path writes the splat records straight from the decoder)."""
+    lib = L.load()
+    a, gs_, s = anchors.struct(), g.struct(), sp.struct()
+    L.check("gs_decode_project", lib.gs_decode_project(C.byref(a), _ptr(views.cams), views.ptr, views.V, precision,
+                                                       C.byref(gs_), C.byref(s), _ptr(ws), ws.numel(), _ptr(status),
+                                                       _stream(stream)))
+
+
 def project(g: Gauss3D, views: Views, out: Splats, status, stream=None):
     lib = L.load()
     gs, sp = g.struct(), out.struct()

@@ -23,6 +23,8 @@ namespace gs {
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;   // 2048 elements
+constexpr int kRadixItems = 8;                          // keys per thread of a radix pass tile
+constexpr int kRadixTile = kSortThreads * kRadixItems;  // 4096 keys
 constexpr int kSortWarps = kSortThreads / 32;
 
 __device__ __forceinline__ unsigned lanemask_lt()
@@ -33,9 +35,10 @@ __device__ __forceinline__ unsigned lanemask_lt()
 }
 
 // Tiles [t0, t1) of 2048 elements owned by block b of nb for n elements.
+template <int TILE = kSortTile>
 __device__ __forceinline__ void block_tiles(uint32_t n, int b, int nb, uint32_t *t0, uint32_t *t1)
 {
-    const uint32_t ntiles = (n + kSortTile - 1) / kSortTile;
+    const uint32_t ntiles = (n + TILE - 1) / TILE;
     const uint32_t per = (ntiles + nb - 1) / nb;
     *t0 = min(ntiles, per * (uint32_t)b);
     *t1 = min(ntiles, per * (uint32_t)(b + 1));
@@ -81,9 +84,9 @@ __global__ void __launch_bounds__(kSortThreads) radix_upsweep(const uint32_t *__
     __syncthreads();
     const uint32_t n = *n_ptr;
     uint32_t t0, t1;
-    block_tiles(n, blockIdx.x, gridDim.x, &t0, &t1);
+    block_tiles<kRadixTile>(n, blockIdx.x, gridDim.x, &t0, &t1);
     const int warp = threadIdx.x >> 5;
-    const uint32_t e0 = t0 * kSortTile, e1 = min(n, t1 * kSortTile);
+    const uint32_t e0 = t0 * kRadixTile, e1 = min(n, t1 * kRadixTile);
     for (uint32_t i = e0 + threadIdx.x; i < e1; i += kSortThreads)
         atomicAdd(&s_h[warp * 256 + ((keys[i] >> shift) & 0xffu)], 1u);
     __syncthreads();
@@ -130,8 +133,8 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep(
     const uint32_t *__restrict__ hist, const uint32_t *__restrict__ totals, const gs_status *st)
 {
     if (__syncthreads_or(has_error(st))) return;   // block-uniform exit
-    __shared__ uint32_t s_keys[kSortTile];
-    __shared__ uint32_t s_vals[kSortTile];
+    __shared__ uint32_t s_keys[kRadixTile];
+    __shared__ uint32_t s_vals[kRadixTile];
     // per-warp digit counts (then per-warp exclusive prefixes), flat
     // [warp][257]; column 256 collects the out-of-range lanes of a ragged tile
     __shared__ uint32_t s_wh[kSortWarps * 257];
@@ -140,7 +143,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep(
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t n = *n_ptr;
     uint32_t t0, t1;
-    block_tiles(n, blockIdx.x, gridDim.x, &t0, &t1);
+    block_tiles<kRadixTile>(n, blockIdx.x, gridDim.x, &t0, &t1);
     {   // global start of each digit for this block
         uint32_t tot;
         uint32_t pre = scan256(totals[tid], s_warp, &tot);
@@ -150,12 +153,12 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep(
     __syncthreads();
     const unsigned ltm = lanemask_lt();
     for (uint32_t t = t0; t < t1; ++t) {
-        const uint32_t tb = t * kSortTile;
-        uint32_t key[kSortItems], val[kSortItems], loc[kSortItems];
-        int dig[kSortItems];
+        const uint32_t tb = t * kRadixTile;
+        uint32_t key[kRadixItems], val[kRadixItems], loc[kRadixItems];
+        int dig[kRadixItems];
 #pragma unroll
-        for (int j = 0; j < kSortItems; ++j) {
-            const uint32_t i = tb + warp * (32 * kSortItems) + j * 32 + lane;
+        for (int j = 0; j < kRadixItems; ++j) {
+            const uint32_t i = tb + warp * (32 * kRadixItems) + j * 32 + lane;
             const bool ok = i < n;
             key[j] = ok ? kin[i] : 0u;
             val[j] = ok ? vin[i] : 0u;
@@ -167,7 +170,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep(
         // Each leader needs its atomic's result before the shuffle, so the rounds
         // are ordered by data dependence.
 #pragma unroll
-        for (int j = 0; j < kSortItems; ++j) {
+        for (int j = 0; j < kRadixItems; ++j) {
             const unsigned peers = __match_any_sync(0xffffffffu, dig[j]);
             const int leader = __ffs(peers) - 1;
             const uint32_t rank = __popc(peers & ltm);
@@ -191,16 +194,16 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep(
         }
         __syncthreads();   // s_tstart is written after the scan's last barrier
 #pragma unroll
-        for (int j = 0; j < kSortItems; ++j) {
+        for (int j = 0; j < kRadixItems; ++j) {
             if (dig[j] < 256) {
                 const uint32_t p = s_tstart[dig[j]] + s_wh[warp * 257 + dig[j]] + loc[j];
-                if (!idx_ok(st, p, kSortTile, 33)) continue;
+                if (!idx_ok(st, p, kRadixTile, 33)) continue;
                 s_keys[p] = key[j];
                 s_vals[p] = val[j];
             }
         }
         __syncthreads();
-        const uint32_t cnt = min((uint32_t)kSortTile, n - tb);
+        const uint32_t cnt = min((uint32_t)kRadixTile, n - tb);
         for (uint32_t i = tid; i < cnt; i += kSortThreads) {
             const uint32_t k = s_keys[i];
             const uint32_t d = (k >> shift) & 0xffu;

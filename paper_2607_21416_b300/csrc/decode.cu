@@ -290,7 +290,7 @@ size_t decode_workspace_bytes(int N, int V)
 }
 
 int launch_decode(const gs_anchors *A, const gs_camera *cams, const ViewTable &vt, int precision,
-                  gs_gauss3d *out, void *ws, gs_status *st, cudaStream_t s)
+                  gs_gauss3d *out, void *ws, gs_status *st, cudaStream_t s, const gs_splats *proj)
 {
     const int N = A->N, V = vt.V;
     const int nchunks = N > 0 ? div_up(N, kVisChunk) : 1;
@@ -311,7 +311,23 @@ int launch_decode(const gs_anchors *A, const gs_camera *cams, const ViewTable &v
     a.cams = cams; a.view_start = out->view_start; a.row_anchor = out->row_anchor;
     a.mu = out->mu; a.scale = out->scale; a.quat = out->quat; a.opacity = out->opacity;
     a.colour = out->colour; a.st = st; a.cap_rows = out->cap_rows; a.wait_ns = wait_limit_ns();
-    if (precision == GS_PREC_BF16) return launch_decode_bf16(a, s);
+    if (precision == GS_PREC_BF16 && proj) {   // decoded and projected in one kernel
+        ProjOut po;
+        po.rec = reinterpret_cast<float4 *>(proj->rec);
+        po.tiles = proj->tiles;
+        po.cap = std::min<long long>(proj->cap, out->cap_rows * (long long)out->k);
+        for (int v = 0; v < GS_MAX_VIEWS; ++v) {
+            po.W[v] = v < V ? vt.W[v] : 0;
+            po.H[v] = v < V ? vt.H[v] : 0;
+            po.TX[v] = v < V ? vt.TX[v] : 0;
+            po.TY[v] = v < V ? vt.TY[v] : 0;
+        }
+        return launch_decode_bf16(a, s, &po);
+    }
+    if (precision == GS_PREC_BF16) {
+        const int rc = launch_decode_bf16(a, s);
+        if (rc != GS_OK || !proj) return rc;
+    }
     const int nt = 128;
     const size_t smem = (size_t)(A->F + 4 + A->hidden) * nt * sizeof(float);
     const long long grid_max = (out->cap_rows + nt - 1) / nt;
@@ -321,7 +337,9 @@ int launch_decode(const gs_anchors *A, const gs_camera *cams, const ViewTable &v
         return GS_ERR_UNSUPPORTED;
     decode_fp32_kernel<<<grid, nt, smem, s>>>(a);
     count_launches(1);
-    return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+    if (cudaPeekAtLastError() != cudaSuccess) return GS_ERR_CUDA;
+    if (proj) return launch_project(out, cams, vt, const_cast<gs_splats *>(proj), st, s);
+    return GS_OK;
 }
 
 }  // namespace gs

@@ -23,6 +23,7 @@
 #include <cuda_bf16.h>
 
 #include "gs_internal.cuh"
+#include "proj_fwd.cuh"
 #include "tc05.cuh"
 
 namespace gs {
@@ -133,7 +134,10 @@ __device__ __forceinline__ void stage_out(const float *stage, float *dst, int n,
 }
 
 // vec: bit 0 = the five output arrays are 16-byte aligned, bit 1 = feature rows are.
-__global__ void __launch_bounds__(kTThreads) decode_tc_kernel(DecodeArgs a, TcShape s, int vec)
+// PROJ: instead of the decoded Gaussians, each candidate's splat record is
+// written (the projection of gs_project applied in the epilogue).
+template <bool PROJ>
+__global__ void __launch_bounds__(kTThreads) decode_tc_kernel(DecodeArgs a, TcShape s, int vec, ProjOut po)
 {
     if (__syncthreads_or(has_error(a.st))) return;   // block-uniform exit
     extern __shared__ __align__(1024) char sm[];
@@ -174,8 +178,9 @@ __global__ void __launch_bounds__(kTThreads) decode_tc_kernel(DecodeArgs a, TcSh
     for (int tile = (int)blockIdx.x * per_cta; tile < tile_end && !failed; ++tile) {
         // ---- this thread's row: anchor, partition, view inputs of Eq. 2, U row
         const int row = tile * kTRows + tid;
-        int an = -1, pm = -1;
+        int an = -1, pm = -1, vw = 0;
         float d0 = 0.f, d1 = 0.f, d2 = 0.f, dl = 1.f;
+        Cam cam;
         if (row < rows) {
             an = __ldg(a.row_anchor + row);
             if (!idx_ok(a.st, an, a.N, 13)) an = -1;
@@ -185,7 +190,9 @@ __global__ void __launch_bounds__(kTThreads) decode_tc_kernel(DecodeArgs a, TcSh
             if (!idx_ok(a.st, pm, a.M, 14)) { pm = -1; an = -1; }
         }
         if (an >= 0) {
-            const Cam c = load_cam(a.cams, view_of_row(a.view_start, a.V, row));
+            vw = view_of_row(a.view_start, a.V, row);
+            cam = load_cam(a.cams, vw);
+            const Cam &c = cam;
             float xc[3];
 #pragma unroll
             for (int i = 0; i < 3; ++i) xc[i] = -(c.R[i] * c.t[0] + c.R[3 + i] * c.t[1] + c.R[6 + i] * c.t[2]);
@@ -312,6 +319,50 @@ __global__ void __launch_bounds__(kTThreads) decode_tc_kernel(DecodeArgs a, TcSh
             tc::fence_after_sync();
 
             // ---- epilogue: this thread's row, if it belongs to partition p
+            if (PROJ) {
+                // each candidate decoded and projected straight to its splat record
+                const bool mine = !done && pm == p;
+                float el[6], xa[3];
+#pragma unroll
+                for (int e = 0; e < 6; ++e) el[e] = mine ? expf(__ldg(a.log_scaling + 6 * an + e)) : 0.f;
+#pragma unroll
+                for (int e = 0; e < 3; ++e) xa[e] = mine ? __ldg(a.xyz + 3 * an + e) : 0.f;
+                const float *off = a.offsets + (size_t)(an >= 0 ? an : 0) * k * 3;
+                const size_t c0 = (size_t)row * k;
+                for (int i = 0; i < k; ++i) {
+                    float vo[4], vc[8];
+                    __syncwarp();
+                    tc::tmem_ld4(tc::tmem_addr(tmem, warp, 4 * i), vo);            // all lanes: warp-collective
+                    tc::tmem_ld8(tc::tmem_addr(tmem, warp, s.Noc + 8 * i), vc);
+                    const size_t ci = c0 + i;
+                    if (mine && idx_ok(a.st, (long long)ci, po.cap, 16)) {
+                        const float op = tanh_fast(vo[0] + b2[4 * i]);
+                        const float col[3] = {sigmoid_fast(vo[1] + b2[4 * i + 1]), sigmoid_fast(vo[2] + b2[4 * i + 2]),
+                                              sigmoid_fast(vo[3] + b2[4 * i + 3])};
+                        const float *bc = b2 + s.Noc + 8 * i;
+                        const float sc[3] = {el[3] * sigmoid_fast(vc[0] + bc[0]), el[4] * sigmoid_fast(vc[1] + bc[1]),
+                                             el[5] * sigmoid_fast(vc[2] + bc[2])};
+                        float q[4] = {vc[3] + bc[3], vc[4] + bc[4], vc[5] + bc[5], vc[6] + bc[6]};
+                        const float inv = rsqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) q[e] *= inv;
+                        const float m0 = xa[0] + __ldg(off + 3 * i) * el[0];
+                        const float m1 = xa[1] + __ldg(off + 3 * i + 1) * el[1];
+                        const float m2 = xa[2] + __ldg(off + 3 * i + 2) * el[2];
+                        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
+                        int nt = 0;
+                        project_one(cam, (float)po.W[vw], (float)po.H[vw], po.TX[vw], po.TY[vw], m0, m1, m2, sc, q,
+                                    op, col, r0, r1, r2, nt);
+                        po.rec[3 * ci] = r0;
+                        po.rec[3 * ci + 1] = r1;
+                        po.rec[3 * ci + 2] = r2;
+                        po.tiles[ci] = nt;
+                    }
+                }
+                if (pm == p) done = true;
+                tc::fence_before_sync();
+                continue;
+            }
             const bool mine = !done && pm == p;
             const bool mixed = !__all_sync(0xffffffffu, mine || pm < 0);   // rows of other partitions in the warp
             const size_t c0 = (size_t)row * k;
@@ -415,7 +466,9 @@ __global__ void __launch_bounds__(kTThreads) decode_tc_kernel(DecodeArgs a, TcSh
     if (warp == 0) tc::tmem_dealloc(tmem, (uint32_t)s.tcols);
 }
 
-int launch_decode_bf16(const DecodeArgs &a, cudaStream_t st)
+// Shared memory, residency and grid of one decode_tc_kernel instantiation.
+template <bool PROJ>
+static int launch_decode_tc(const DecodeArgs &a, const ProjOut &po, cudaStream_t st)
 {
     const TcShape s = tc_shape(a.F, a.k, a.H);
     if (a.H % 16 != 0 || s.N1 > 256 || s.Noc > 256 || s.Ncov > 256 || s.tcols > 256 || s.KP > 256 ||
@@ -430,7 +483,7 @@ int launch_decode_bf16(const DecodeArgs &a, cudaStream_t st)
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&dev_reserve, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
-            cudaFuncGetAttributes(&fa, decode_tc_kernel) != cudaSuccess)
+            cudaFuncGetAttributes(&fa, decode_tc_kernel<PROJ>) != cudaSuccess)
             return GS_ERR_CUDA;
         static_smem = (int)fa.sharedSizeBytes;
         regs = fa.numRegs;
@@ -447,9 +500,9 @@ int launch_decode_bf16(const DecodeArgs &a, cudaStream_t st)
     if (smem > configured) {
         // the whole unified L1 / shared array as shared memory, or the runtime
         // may size the carveout for fewer resident CTAs
-        if (cudaFuncSetAttribute(decode_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        if (cudaFuncSetAttribute(decode_tc_kernel<PROJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
                 cudaSuccess ||
-            cudaFuncSetAttribute(decode_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+            cudaFuncSetAttribute(decode_tc_kernel<PROJ>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared) != cudaSuccess)
             return GS_ERR_UNSUPPORTED;
         configured = smem;
@@ -464,9 +517,19 @@ int launch_decode_bf16(const DecodeArgs &a, cudaStream_t st)
     const bool vec_feat = (reinterpret_cast<uintptr_t>(a.feat) & 15) == 0 && a.F % 4 == 0;
     const long long tiles = (a.cap_rows + kTRows - 1) / kTRows;
     const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, (long long)sm_count() * occ));
-    decode_tc_kernel<<<grid, kTThreads, smem, st>>>(a, s, (vec_out ? 1 : 0) | (vec_feat ? 2 : 0));
+    decode_tc_kernel<PROJ><<<grid, kTThreads, smem, st>>>(a, s, (vec_out ? 1 : 0) | (vec_feat ? 2 : 0), po);
     count_launches(1);
     return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+int launch_decode_bf16(const DecodeArgs &a, cudaStream_t st, const ProjOut *po)
+{
+    if (po) return launch_decode_tc<true>(a, *po, st);
+    ProjOut none;
+    none.rec = nullptr;
+    none.tiles = nullptr;
+    none.cap = 0;
+    return launch_decode_tc<false>(a, none, st);
 }
 
 }  // namespace gs

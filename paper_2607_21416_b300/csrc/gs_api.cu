@@ -170,6 +170,21 @@ int gs_decode(const gs_anchors *A, const gs_camera *cams, const gs_view *views, 
     return launch_decode(A, cams, vt, precision, out, ws, status, (cudaStream_t)stream);
 }
 
+int gs_decode_project(const gs_anchors *A, const gs_camera *cams, const gs_view *views, int32_t V,
+                      int32_t precision, gs_gauss3d *g, gs_splats *sp, void *ws, size_t ws_bytes, gs_status *status,
+                      void *stream)
+{
+    ViewTable vt;
+    if (!check_anchors(A) || !cams || !status || !check_gauss(g) || !g->row_anchor ||
+        !make_view_table(views, V, &vt) || g->k != A->k || !sp || !sp->rec || !sp->tiles)
+        return GS_ERR_INVALID_ARG;
+    if (precision != GS_PREC_FP32 && precision != GS_PREC_BF16) return GS_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(sp->rec) & 15) != 0 || sp->cap < g->cap_rows * (long long)g->k)
+        return GS_ERR_INVALID_ARG;
+    if (ws_bytes < decode_workspace_bytes(A->N, V) || (!ws && ws_bytes > 0)) return GS_ERR_INVALID_ARG;
+    return launch_decode(A, cams, vt, precision, g, ws, status, (cudaStream_t)stream, sp);
+}
+
 int gs_project(const gs_gauss3d *g, const gs_camera *cams, const gs_view *views, int32_t V, gs_splats *out,
                gs_status *status, void *stream)
 {

@@ -34,10 +34,19 @@ struct DecodeBwdArgsB {
 };
 int launch_decode_bwd_bf16(const DecodeBwdArgsB &a, cudaStream_t s);
 
+// Splat records written by the decoder itself (decode fused with the
+// projection): the output and the views' sizes in pixels and tiles.
+struct ProjOut {
+    float4 *rec;
+    int32_t *tiles;
+    long long cap;
+    int W[GS_MAX_VIEWS], H[GS_MAX_VIEWS], TX[GS_MAX_VIEWS], TY[GS_MAX_VIEWS];
+};
+
 size_t decode_workspace_bytes(int N, int V);
 int launch_decode(const gs_anchors *A, const gs_camera *cams, const ViewTable &vt, int precision,
-                  gs_gauss3d *out, void *ws, gs_status *st, cudaStream_t s);
-int launch_decode_bf16(const DecodeArgs &a, cudaStream_t s);
+                  gs_gauss3d *out, void *ws, gs_status *st, cudaStream_t s, const gs_splats *proj = nullptr);
+int launch_decode_bf16(const DecodeArgs &a, cudaStream_t s, const ProjOut *po = nullptr);
 
 int launch_project(const gs_gauss3d *g, const gs_camera *cams, const ViewTable &vt, gs_splats *out,
                    gs_status *st, cudaStream_t s);

@@ -1,15 +1,16 @@
 // render_bwd.cu -- reverse of the tile compositing (Eq. 1) over chunked work
 // items, and the chain rule of the projection.
 //
-// Per item and pixel the reverse traversal runs front to back, like the
-// forward: it recomputes the transmittance in front of each splat and the
-// colour composited so far with the forward's own arithmetic (so it takes the
-// forward's skip and stop decisions), and gets the colour behind a splat as
-// the pixel's final colour (the forward's image) minus that prefix.  Single-
-// chunk tiles need no per-pixel state from the forward; a later chunk of a
-// multi-chunk tile starts from the per-chunk state the forward left in the
-// render workspace.  Per-splat sums are reduced across the warp (shuffles)
-// before one global atomicAdd per warp and quantity.
+// A tile whose splat list is one work item is reversed front to back, like
+// the forward: the traversal recomputes the transmittance in front of each
+// splat and the colour composited so far with the forward's own arithmetic
+// (so it takes the forward's skip and stop decisions), and gets the colour
+// behind a splat as the pixel's final colour (the forward's image) minus that
+// prefix -- no per-pixel state is stored by the forward or recomputed in a
+// separate pass.  A chunk of a longer list starts from the per-chunk state
+// the forward left in the render workspace and is reversed back to front.
+// Per-splat sums are reduced across the warp (shuffles) before one global
+// atomicAdd per warp and quantity.
 #include "proj_bwd.cuh"
 #include "render_common.cuh"
 
@@ -80,10 +81,13 @@ __device__ __forceinline__ bool alpha_test(const float4 a, const float4 bb, floa
 // the pixels; after the warp reduction they become d mean2d and d conic
 // (conic_grads) and the opacity sum is divided by the opacity.  Eq. 1 gives,
 // for splat i with transmittance T_i in front of it, dC/dalpha_i = T_i c_i -
-// B_i / (1 - alpha_i) (B_i: colour behind i, background included), and g . B_i
-// = GC - Sp_i.  T and Sp advance past the splat.
-__device__ __forceinline__ void bwd_composite(float &T, float &Sp, float Tn, float GC, float g0, float g1, float g2,
-                                              const float4 bb, float cb, float dx, float dy, float ag, float acc[9])
+// B_i / (1 - alpha_i) (B_i: colour behind i, background included).
+//
+// Front to back: T = T_i and Sp = g . (colour up to splat i - 1) on entry; g .
+// B_i = GC - Sp_i with GC = g . (the pixel's final colour); T and Sp advance
+// past the splat (T' = T (1 - alpha) rounded as the forward rounds it).
+__device__ __forceinline__ void bwd_composite_f2b(float &T, float &Sp, float GC, float g0, float g1, float g2,
+                                                  const float4 bb, float cb, float dx, float dy, float ag, float acc[9])
 {
     const float alpha = fminf(kAlphaMax, ag);
     float inv;                             // 1 / (1 - alpha) on the SFU (relative error ~2^-23; the
@@ -95,10 +99,38 @@ __device__ __forceinline__ void bwd_composite(float &T, float &Sp, float Tn, flo
     const float gc = fmaf(g0, bb.z, fmaf(g1, bb.w, g2 * cb));
     Sp = fmaf(gc, w, Sp);
     const float dal = fmaf(gc, T, -(GC - Sp) * inv);
-    T = Tn;
+    T = __fmul_rn(T, 1.f - alpha);
     if (ag < kAlphaMax) {                  // the clamped branch passes no gradient to o exp(power)
         acc[5] = fmaf(dal, ag, acc[5]);
         const float dp = dal * alpha;      // d power (alpha = o exp(power))
+        const float t = dp * dx, u = dp * dy;
+        acc[0] += t;
+        acc[1] += u;
+        acc[2] = fmaf(t, dx, acc[2]);
+        acc[3] = fmaf(t, dy, acc[3]);
+        acc[4] = fmaf(u, dy, acc[4]);
+    }
+}
+
+// Back to front: T = T_(i+1) (transmittance behind the splat) and S = g . B_i
+// on entry; T becomes T_i = T_(i+1) / (1 - alpha_i) and S takes the splat in.
+__device__ __forceinline__ void bwd_composite_b2f(float &T, float &S, float g0, float g1, float g2, const float4 bb,
+                                                  float cb, float dx, float dy, float ag, float acc[9])
+{
+    const float alpha = fminf(kAlphaMax, ag);
+    float inv;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(1.f - alpha));
+    T = T * inv;                           // transmittance in front of this splat
+    const float w = alpha * T;
+    acc[6] = fmaf(w, g0, acc[6]);
+    acc[7] = fmaf(w, g1, acc[7]);
+    acc[8] = fmaf(w, g2, acc[8]);
+    const float gc = fmaf(g0, bb.z, fmaf(g1, bb.w, g2 * cb));
+    const float dal = fmaf(gc, T, -S * inv);
+    S = fmaf(gc, w, S);
+    if (ag < kAlphaMax) {
+        acc[5] = fmaf(dal, ag, acc[5]);
+        const float dp = dal * alpha;
         const float t = dp * dx, u = dp * dy;
         acc[0] += t;
         acc[1] += u;
@@ -139,15 +171,38 @@ __device__ __forceinline__ float conic_grads(const LaneRole &r, float total, flo
     return fmaf(cs, total, co * other);
 }
 
-// Reverse pass of one work unit (block `warp` of item b), front to back.  Per
-// pixel the traversal recomputes, splat by splat, the transmittance in front
-// of it and the colour composited so far -- the forward's own arithmetic, so
-// every skip / stop decision is the forward's -- and takes the colour behind
-// a splat as the pixel's final colour (the forward's image) minus that
-// prefix.  Nothing per pixel is stored by the forward for single-chunk tiles;
-// a later chunk of a multi-chunk tile starts from the transmittance in front
-// of it and the colour prefix of the chunk before (the per-chunk state) and
-// composites up to its last composited position.
+// The 9 per-splat sums of a staged splat: reduced across the warp, turned
+// into the splat's gradient and added to its entry (one atomic per value).
+__device__ __forceinline__ void splat_sums_out(const float acc[9], const LaneRole &role, int vi, float4 a, float4 bb,
+                                               uint32_t id, float *__restrict__ sgrad)
+{
+    const int lane = threadIdx.x & 31;
+    const float io = ex2_approx(-bb.y);   // 1 / opacity from the record's log2 opacity
+    const float t8 = warp_sum8(acc);
+    const float t9 = warp_sum(acc[8]);
+    const float other = __shfl_xor_sync(0xffffffffu, t8, 4);
+    const float g = conic_grads(role, t8, other, a, bb, io);
+    float *o = sgrad + 9 * (size_t)id;
+    if ((lane & 3) == 0) atomicAdd(o + vi, g);
+    if (lane == 1) atomicAdd(o + 8, t9);
+}
+
+// Reverse pass of one work unit (block `warp` of item b).
+//
+// A tile whose list is one work item is walked front to back: per pixel the
+// traversal recomputes, splat by splat, the transmittance in front of it and
+// the colour composited so far -- the forward's own arithmetic, so every
+// skip / stop decision is the forward's -- and takes the colour behind a
+// splat as the pixel's final colour (the forward's image) minus that prefix.
+// Nothing per pixel is stored by the forward, and no separate pass
+// recomputes its state.
+//
+// A chunk of a longer list starts from the state the forward left for it --
+// the transmittance after its last composited splat, that position, and the
+// colour prefix up to its end (the colour behind the chunk is the final
+// colour minus it) -- and is walked back to front from the last composited
+// position, recovering the transmittance in front of each splat by dividing
+// by 1 - alpha.
 __device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const uint32_t *__restrict__ vals,
                                          const uint32_t *__restrict__ ranges, const ViewTable &vt,
                                          const RenderPlan &plan, const float *__restrict__ image,
@@ -170,13 +225,13 @@ __device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const u
     const long long pix0 = (long long)py * W + px0;
     const int n_items = (int)(it.s1 - it.s0);
     const bool multi = it.nk > 1;
+    // per pixel: g = dL/dC and GC = g . (final colour)
     PixBwd p0, p1;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         PixBwd &ps = h ? p1 : p0;
         const bool in = h ? lpx.in1 : lpx.in0;
         const long long pix = pix0 + 8 * h;
-        const int pid = pid0 + 8 * h;
         ps.T = 1.f;
         ps.Sp = ps.GC = ps.g0 = ps.g1 = ps.g2 = 0.f;
         ps.lim = 0;
@@ -188,32 +243,70 @@ __device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const u
         ps.g1 = dimg[W * H + pix];
         ps.g2 = dimg[2 * W * H + pix];
         ps.GC = fmaf(ps.g0, img[pix], fmaf(ps.g1, img[W * H + pix], ps.g2 * img[2 * W * H + pix]));
-        if (multi) {
-            const int item = it.base + it.k;
-            const float T0 = state_plane(plan.state, item, 0)[pid];
-            if (T0 >= kTMin) {   // active chunk: enter with its transmittance and the prefix in front of it
-                ps.T = T0;
-                ps.lim = min(reinterpret_cast<const int *>(state_plane(plan.state, item, 5))[pid], n_items);
-                if (it.k > 0)
-                    ps.Sp = fmaf(ps.g0, state_plane(plan.state, item - 1, 2)[pid],
-                                 fmaf(ps.g1, state_plane(plan.state, item - 1, 3)[pid],
-                                      ps.g2 * state_plane(plan.state, item - 1, 4)[pid]));
-            }
-        } else {
-            ps.lim = last_in ? min(last_in[vt.pix_base[v] + pix], n_items) : n_items;
-        }
+        ps.lim = last_in ? min(last_in[vt.pix_base[v] + pix], n_items) : n_items;
         ps.done = ps.lim <= 0;
     }
     const int vi = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
     const LaneRole role = lane_role(vi);
+    if (multi) {
+        // ---- a chunk of a longer list, back to front from its last composited splat
+        const int item = it.base + it.k;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            PixBwd &ps = h ? p1 : p0;
+            const int pid = pid0 + 8 * h;
+            ps.lim = 0;
+            if (!(h ? lpx.in1 : lpx.in0)) continue;
+            const float T0 = state_plane(plan.state, item, 0)[pid];
+            if (!(T0 >= kTMin)) continue;   // behind the pixel's stop
+            ps.T = state_plane(plan.state, item, 1)[pid];
+            ps.lim = min(reinterpret_cast<const int *>(state_plane(plan.state, item, 5))[pid], n_items);
+            // g . (colour behind the chunk) = GC - g . (colour up to and including it)
+            ps.Sp = ps.GC - fmaf(ps.g0, state_plane(plan.state, item, 2)[pid],
+                                 fmaf(ps.g1, state_plane(plan.state, item, 3)[pid],
+                                      ps.g2 * state_plane(plan.state, item, 4)[pid]));
+        }
+        const int maxlast = __reduce_max_sync(0xffffffffu, max(p0.lim, p1.lim));
+        for (int hi = maxlast; hi > 0; hi -= 32) {
+            const int pl = hi - 1 - lane;   // lane l <-> position hi - 1 - l: hits come back to front
+            const int cnt = warp_stage<false>(WSw, rec, vals, it.s0 + (uint32_t)max(pl, 0), it.s0, pl >= 0,
+                                                    cap_cand, st, 53, bx0, bx1, by0, by1);
+            for (int e = 0; e < cnt; ++e) {
+                const int p = WSw.pos[e];
+                const float4 a = WSw.a[e];
+                const float4 bb = WSw.b[e];
+                float dx0 = 0.f, dy0 = 0.f, ag0 = 0.f, dx1 = 0.f, dy1 = 0.f, ag1 = 0.f;
+                const bool c0 = p < p0.lim && alpha_test(a, bb, fx0, fy, &dx0, &dy0, &ag0);
+                const bool c1 = p < p1.lim && alpha_test(a, bb, fx1, fy, &dx1, &dy1, &ag1);
+                const bool contrib = c0 || c1;
+                if (!__any_sync(0xffffffffu, contrib)) continue;
+                float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                const float cb = WSw.c[e];
+                {   // pixel 0 where it composites the splat, else pixel 1
+                    const bool u1 = !c0;
+                    float T = u1 ? p1.T : p0.T, S = u1 ? p1.Sp : p0.Sp;
+                    if (contrib) {
+                        bwd_composite_b2f(T, S, u1 ? p1.g0 : p0.g0, u1 ? p1.g1 : p0.g1, u1 ? p1.g2 : p0.g2, bb, cb,
+                                          u1 ? dx1 : dx0, u1 ? dy1 : dy0, u1 ? ag1 : ag0, acc);
+                        if (u1) { p1.T = T; p1.Sp = S; } else { p0.T = T; p0.Sp = S; }
+                    }
+                }
+                if (__any_sync(0xffffffffu, c0 && c1) && c0 && c1)   // a lane that composites it at both pixels
+                    bwd_composite_b2f(p1.T, p1.Sp, p1.g0, p1.g1, p1.g2, bb, cb, dx1, dy1, ag1, acc);
+                splat_sums_out(acc, role, vi, a, bb, WSw.id[e], sgrad);
+            }
+            __syncwarp();
+        }
+        return;
+    }
+    // ---- a tile whose list is one work item, front to back (the forward's stop rule decided again
+    // unless `last` is given)
     const int maxlim = __reduce_max_sync(0xffffffffu, max(p0.done ? 0 : p0.lim, p1.done ? 0 : p1.lim));
-    // the forward's stop rule is decided again here for single-chunk tiles (unless `last` is given);
-    // chunks of longer lists composite up to their recorded last position
-    const bool stop_rule = !multi && !last_in;
+    const bool stop_rule = !last_in;
     for (int b0 = 0; b0 < maxlim; b0 += 32) {
         if (__all_sync(0xffffffffu, p0.done && p1.done)) break;
         const int pl = b0 + lane;
-        const int cnt = warp_stage<true, true>(WSw, rec, vals, it.s0 + (uint32_t)pl, it.s0, pl < maxlim, cap_cand,
+        const int cnt = warp_stage<true>(WSw, rec, vals, it.s0 + (uint32_t)pl, it.s0, pl < maxlim, cap_cand,
                                                st, 53, bx0, bx1, by0, by1);
         for (int e = 0; e < cnt; ++e) {
             const int q1 = WSw.pos[e] + 1;
@@ -223,12 +316,9 @@ __device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const u
             float dx0 = 0.f, dy0 = 0.f, ag0 = 0.f, dx1 = 0.f, dy1 = 0.f, ag1 = 0.f;
             bool c0 = (hm & 1) && !p0.done && q1 <= p0.lim && alpha_test(a, bb, fx0, fy, &dx0, &dy0, &ag0);
             bool c1 = (hm & 2) && !p1.done && q1 <= p1.lim && alpha_test(a, bb, fx1, fy, &dx1, &dy1, &ag1);
-            // transmittance behind the splat, rounded as the forward rounds it
-            const float Tn0 = __fmul_rn(p0.T, 1.f - fminf(kAlphaMax, ag0));
-            const float Tn1 = __fmul_rn(p1.T, 1.f - fminf(kAlphaMax, ag1));
-            if (stop_rule) {
-                if (c0 && Tn0 < kTMin) { p0.done = true; c0 = false; }
-                if (c1 && Tn1 < kTMin) { p1.done = true; c1 = false; }
+            if (stop_rule) {   // T (1 - alpha) < 1e-4 stops the pixel before the splat, as in the forward
+                if (c0 && __fmul_rn(p0.T, 1.f - fminf(kAlphaMax, ag0)) < kTMin) { p0.done = true; c0 = false; }
+                if (c1 && __fmul_rn(p1.T, 1.f - fminf(kAlphaMax, ag1)) < kTMin) { p1.done = true; c1 = false; }
             }
             const bool contrib = c0 || c1;
             if (!__any_sync(0xffffffffu, contrib)) continue;
@@ -238,23 +328,15 @@ __device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const u
                 const bool u1 = !c0;
                 float T = u1 ? p1.T : p0.T, Sp = u1 ? p1.Sp : p0.Sp;
                 if (contrib) {
-                    bwd_composite(T, Sp, u1 ? Tn1 : Tn0, u1 ? p1.GC : p0.GC, u1 ? p1.g0 : p0.g0,
-                                  u1 ? p1.g1 : p0.g1, u1 ? p1.g2 : p0.g2, bb, cb, u1 ? dx1 : dx0, u1 ? dy1 : dy0,
-                                  u1 ? ag1 : ag0, acc);
+                    bwd_composite_f2b(T, Sp, u1 ? p1.GC : p0.GC, u1 ? p1.g0 : p0.g0, u1 ? p1.g1 : p0.g1,
+                                      u1 ? p1.g2 : p0.g2, bb, cb, u1 ? dx1 : dx0, u1 ? dy1 : dy0, u1 ? ag1 : ag0,
+                                      acc);
                     if (u1) { p1.T = T; p1.Sp = Sp; } else { p0.T = T; p0.Sp = Sp; }
                 }
             }
             if (__any_sync(0xffffffffu, c0 && c1) && c0 && c1)   // a lane that composites it at both pixels
-                bwd_composite(p1.T, p1.Sp, Tn1, p1.GC, p1.g0, p1.g1, p1.g2, bb, cb, dx1, dy1, ag1, acc);
-            {
-                const float t8 = warp_sum8(acc);
-                const float t9 = warp_sum(acc[8]);
-                const float other = __shfl_xor_sync(0xffffffffu, t8, 4);
-                const float g = conic_grads(role, t8, other, a, bb, WSw.io[e]);
-                float *o = sgrad + 9 * (size_t)WSw.id[e];
-                if ((lane & 3) == 0) atomicAdd(o + vi, g);
-                if (lane == 1) atomicAdd(o + 8, t9);
-            }
+                bwd_composite_f2b(p1.T, p1.Sp, p1.GC, p1.g0, p1.g1, p1.g2, bb, cb, dx1, dy1, ag1, acc);
+            splat_sums_out(acc, role, vi, a, bb, WSw.id[e], sgrad);
         }
         __syncwarp();
         // pixels whose last position lies in this batch are finished

@@ -19,9 +19,9 @@
 //   Tend   transmittance after the chunk's compositing (stop rule applied)
 //   P[3]   colour composited up to and including this chunk (prefix)
 //   last   1-based position (in the chunk) of its last composited splat
-// and the tile's first item also holds the pixel's final colour F[3] (image
-// value, background included), so the reverse pass of chunk k starts from
-// Tend, last and the colour behind the chunk, F - P_k, in O(1).
+// so the reverse pass of chunk k starts from Tend, last and the colour behind
+// the chunk, F - P_k (F the pixel's final colour, the forward's image), in
+// O(1).
 #pragma once
 
 #include "gs_internal.cuh"
@@ -30,8 +30,8 @@ namespace gs {
 
 constexpr int kRT = kTilePix;      // pixels per tile / work item
 constexpr int kRThreads = 128;     // threads per CTA of the compositing kernels (4 warps, one 16x4 block each)
-constexpr int kStateWords = 10;    // T0 (Tprod during the forward), Tend, P0..2 (C during the forward), last,
-                                   // composited count, F0..2 (first item only)  (x 256 pixels)
+constexpr int kStateWords = 7;     // T0 (Tprod during the forward), Tend, P0..2 (C during the forward), last,
+                                   // composited count (x 256 pixels)
 
 // 2^x on the special-function unit (ex2.approx, max relative error ~2^-22).
 __device__ __forceinline__ float ex2_approx(float x)
@@ -144,7 +144,6 @@ struct WarpStage {
     float4 a[32];      // mean x, mean y, A, B
     float4 b[32];      // C, L, r, g
     float c[32];       // b
-    float io[32];      // 1 / opacity (backward)
     uint32_t id[32];   // candidate id
     int pos[32];       // list position within the item (0-based)
     int half[32];      // forward: bit 0 / 1 = the alpha box meets the left / right 8 columns of the block
@@ -174,9 +173,9 @@ __device__ __forceinline__ bool meets_block(float4 a, float4 b, float bx0, float
 // Reads list position `pos` of the item (when valid) and tests it against the
 // warp's block; the hits are compacted into the warp's stage in list order
 // (lane order).  Returns the number of hits.
-// IO: also stage 1 / opacity (the reverse pass); HALF: also stage which 8-column
-// halves of the block the splat's alpha box meets.
-template <bool IO, bool HALF>
+// HALF: also stage which 8-column halves of the block the splat's alpha box
+// meets.
+template <bool HALF>
 __device__ __forceinline__ int warp_stage(WarpStage &W, const float4 *__restrict__ rec,
                                           const uint32_t *__restrict__ vals, uint32_t pos, uint32_t s0, bool valid,
                                           long long cap_cand, const gs_status *st, int site,
@@ -201,7 +200,6 @@ __device__ __forceinline__ int warp_stage(WarpStage &W, const float4 *__restrict
         W.a[slot] = a;
         W.b[slot] = b;
         W.c[slot] = __ldg(reinterpret_cast<const float *>(&rec[3 * (size_t)id + 2]));
-        if (IO) W.io[slot] = exp2f(-b.y);
         W.id[slot] = id;
         W.pos[slot] = (int)(pos - s0);
         // which 8-column half of the block the box meets.  A lane's first pixel lies in the left

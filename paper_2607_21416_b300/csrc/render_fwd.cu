@@ -189,7 +189,7 @@ __device__ __forceinline__ void chunk_unit(const float4 *__restrict__ rec, const
     for (uint32_t b0 = it.s0; b0 < it.s1; b0 += 32) {
         if (__all_sync(0xffffffffu, p0.done && p1.done)) break;
         const uint32_t pos = b0 + lane;
-        const int cnt = warp_stage<false, true>(W, rec, vals, pos, it.s0, pos < it.s1, cap_cand, st, 42, bx0, bx1,
+        const int cnt = warp_stage<true>(W, rec, vals, pos, it.s0, pos < it.s1, cap_cand, st, 42, bx0, bx1,
                                                  by0, by1);
         if (exact) {
             for (int e = 0; e < cnt; ++e) {
@@ -242,9 +242,6 @@ __device__ __forceinline__ void chunk_unit(const float4 *__restrict__ rec, const
             c1[pix] = f1;
             c2[pix] = f2;
             reinterpret_cast<int *>(state_plane(plan.state, item, 5))[pix] = ps.last;
-            state_plane(plan.state, it.base, 7)[pix] = fmaf(ps.T, bg0, f0);
-            state_plane(plan.state, it.base, 8)[pix] = fmaf(ps.T, bg1, f1);
-            state_plane(plan.state, it.base, 9)[pix] = fmaf(ps.T, bg2, f2);
             write_image(vt, tc.v, px, py, f0, f1, f2, ps.T, ps.last > 0 ? it.k * plan.L + ps.last : -1, bg0, bg1,
                         bg2, image, T_final, last);
             continue;
@@ -398,9 +395,6 @@ __global__ void __launch_bounds__(2 * kRThreads) combine_kernel(const uint32_t *
         }
         for (; k < nk; ++k) state_plane(plan.state, base + k, 0)[pix] = 0.f;   // behind the stop: inactive
         if (!marked) {
-            state_plane(plan.state, base, 7)[pix] = fmaf(T0, bg0, C0);
-            state_plane(plan.state, base, 8)[pix] = fmaf(T0, bg1, C1);
-            state_plane(plan.state, base, 9)[pix] = fmaf(T0, bg2, C2);
             if (inside) write_image(vt, tc.v, tc.px, py, C0, C1, C2, T0, lastg, bg0, bg1, bg2, image, T_final, last);
         }
     }

@@ -32,14 +32,19 @@ class RenderPass:
 
     anchors: api.Anchors or None (explicit Gaussians passed to `set_explicit`).
     store_state: keep the forward's per-pixel T_final / last contributor for
-    the backward (plain path) or recompute them inside the backward (batched
-    path, less HBM).
+    the backward (plain path), or let the backward decide the stop rule again
+    on its front-to-back walk (batched path: nothing per pixel is stored).
+    fuse_projection: decode and project in one call (gs_decode_project); with
+    BF16 decoding the 3D Gaussians then never reach device memory (g's
+    candidate arrays stay unwritten) -- turn it off when the decoded
+    Gaussians themselves are needed (densification statistics).
     """
 
     def __init__(self, views: api.Views, anchors: api.Anchors | None = None, k: int = 1,
                  cap_rows: int | None = None, cap_pairs: int | None = None,
                  precision: int = L.GS_PREC_FP32, store_state: bool = True,
-                 bg=(0.0, 0.0, 0.0), device="cuda", keys=False, chunk=0, loss="l1", lam=0.8):
+                 bg=(0.0, 0.0, 0.0), device="cuda", keys=False, chunk=0, loss="l1", lam=0.8,
+                 fuse_projection=True):
         self.views = views
         self.anchors = anchors
         self.k = anchors.k if anchors is not None else k
@@ -49,6 +54,7 @@ class RenderPass:
         self.device = device
         self.want_keys = keys
         self.chunk = int(chunk)
+        self.fuse_projection = bool(fuse_projection)
         if loss not in ("l1", "photometric"):
             raise ValueError(f"loss must be 'l1' or 'photometric', not {loss!r}")
         self.loss_kind = loss
@@ -95,12 +101,24 @@ class RenderPass:
             self._alloc()
         self.g = g
 
+    @property
+    def gaussians_written(self) -> bool:
+        """Whether the forward leaves the decoded 3D Gaussians in g."""
+        return self.anchors is None or not self.fuse_projection or self.precision != L.GS_PREC_BF16
+
     # ---------------------------------------------------------------- passes
     def forward(self, count_evals=False, stream=None):
+        """decode + project (one call: with BF16 decoding the decoder writes the
+        splat records itself and g's candidate arrays are not written), then
+        bin/sort and composite."""
         self.status.zero_()
-        if self.anchors is not None:
-            api.decode(self.anchors, self.views, self.g, self.dec_ws, self.status, self.precision, stream)
-        api.project(self.g, self.views, self.splats, self.status, stream)
+        if self.anchors is not None and self.fuse_projection:
+            api.decode_project(self.anchors, self.views, self.g, self.splats, self.dec_ws, self.status,
+                               self.precision, stream)
+        else:
+            if self.anchors is not None:
+                api.decode(self.anchors, self.views, self.g, self.dec_ws, self.status, self.precision, stream)
+            api.project(self.g, self.views, self.splats, self.status, stream)
         api.bin_sort(self.splats, self.g, self.views, self.bins, self.sort_ws, self.status, stream)
         api.render_fwd(self.splats, self.bins, self.views, self.bg, self.image, self.status,
                        self.render_ws, self.chunk,
@@ -195,11 +213,12 @@ class MappingStep:
 
     def __init__(self, views: api.Views, anchors: api.Anchors, precision: int = L.GS_PREC_BF16,
                  cap_rows: int | None = None, store_state: bool = False, chunk: int = 0, device="cuda",
-                 loss: str = "l1", lam: float = 0.8, tune: bool = False, tune_cache: str | None = None):
+                 loss: str = "l1", lam: float = 0.8, tune: bool = False, tune_cache: str | None = None,
+                 fuse_projection: bool = True):
         self.views = views
         self.anchors = anchors
         self._args = dict(cap_rows=cap_rows, precision=precision, store_state=store_state, device=device,
-                          loss=loss, lam=lam)
+                          loss=loss, lam=lam, fuse_projection=fuse_projection)
         self.rp = RenderPass(views, anchors, chunk=chunk, **self._args)
         self.target = torch.zeros(3 * views.total_pixels, device=device)
         self.stream = torch.cuda.Stream(device=device)
@@ -340,7 +359,12 @@ class DensifyStats:
             t.zero_()
 
     def accumulate(self, rp: RenderPass, stream=None):
-        """Adds the statistics of the iteration `rp` has just run (after its backward)."""
+        """Adds the statistics of the iteration `rp` has just run (after its backward).
+        They read the decoded opacities: `rp` must leave them in g
+        (RenderPass / MappingStep with fuse_projection=False for BF16)."""
+        if not rp.gaussians_written:
+            raise ValueError("densification statistics need the decoded Gaussians: build the pass with "
+                             "fuse_projection=False")
         api.densify_stats(rp.g, rp.views, rp.splats, rp.sgrad, self.N, self.grad_accum, self.offset_denom,
                           self.opacity_accum, self.anchor_denom, rp.status, stream)
 

@@ -24,7 +24,8 @@ from _helpers import PIX_TOL, assert_grad_close, f32, image_mask, to_np
 from oracle import oracle as O
 from paper_2607_21416_b300 import _lib as L
 from paper_2607_21416_b300 import api, pipeline, scenes
-from test_gpu_fullsize import _at, _records, _row_subset, _sample_rows, _tile_pixel_mask, check_pairs, check_projection
+from test_gpu_fullsize import (_at, _records, _row_subset, _sample_rows, _tile_pixel_mask, check_pairs,
+                               check_projection, decoded)
 
 pytestmark = pytest.mark.gpu
 
@@ -46,8 +47,9 @@ def run(request):
     tgt_host = torch.from_numpy(np.concatenate([t.reshape(-1) for t in s.targets]).astype(np.float32)).pin_memory()
     ms.step(tgt_host)
     torch.cuda.synchronize()
-    yield s, views, A, ms
-    del ms
+    gdec = decoded(ms, A, views)
+    yield s, views, A, ms, gdec
+    del ms, gdec
     torch.cuda.empty_cache()
 
 
@@ -81,7 +83,7 @@ def _tiles_and_lists(ms, views, n_per_view, seed, n_views=6):
 
 
 def test_visibility_rows_exact(run):
-    s, views, A, ms = run
+    s, views, A, ms, gdec = run
     vs_g = to_np(ms.rp.g.view_start).astype(np.int64)
     R = int(vs_g[-1])
     ra = to_np(ms.rp.g.row_anchor)[:R].astype(np.int64)
@@ -95,8 +97,8 @@ def test_visibility_rows_exact(run):
 
 
 def test_decode_sampled_rows(run):
-    s, views, A, ms = run
-    g = ms.rp.g
+    s, views, A, ms, gdec = run
+    g = gdec
     vs_g = to_np(g.view_start).astype(np.int64)
     rows = _sample_rows(int(vs_g[-1]), 1000, 11)
     dec = O.decode(s, rows=_row_subset(rows, vs_g, to_np(g.row_anchor)))
@@ -111,17 +113,17 @@ def test_decode_sampled_rows(run):
 
 
 def test_project_sampled_candidates(run):
-    s, views, A, ms = run
-    check_projection(s, views, ms.rp, 20000, 16)
+    s, views, A, ms, gdec = run
+    check_projection(s, views, gdec, ms.rp, 20000, 16)
 
 
 def test_bin_sort_invariants_all_pairs(run):
-    s, views, A, ms = run
+    s, views, A, ms, gdec = run
     check_pairs(s, views, ms.rp, 10_000_000)
 
 
 def test_render_sampled_tiles(run):
-    s, views, A, ms = run
+    s, views, A, ms, gdec = run
     rp = ms.rp
     tiles_sel, used, r_sub, v_sub = _tiles_and_lists(ms, views, 2, 12)
     r = _records(_at(rp.splats.rec, used))
@@ -141,9 +143,9 @@ def test_render_sampled_tiles(run):
     assert err.max() <= PIX_TOL, f"max pixel error {err.max():.3e}"
     dimg = np.random.default_rng(13).normal(size=3 * views.total_pixels) * m
     sgrad = torch.zeros_like(rp.sgrad)
-    out = api.Gauss3DGrad.like(rp.g)
+    out = api.Gauss3DGrad.like(gdec)
     st = api.new_status()
-    api.render_bwd(rp.g, rp.splats, rp.bins, views, rp.image, torch.as_tensor(f32(dimg)).cuda(), sgrad, out, st,
+    api.render_bwd(gdec, rp.splats, rp.bins, views, rp.image, torch.as_tensor(f32(dimg)).cuda(), sgrad, out, st,
                    rp.render_ws, rp.chunk)
     torch.cuda.synchronize()
     assert api.read_status(st)[0] == 0
@@ -159,8 +161,8 @@ def test_render_sampled_tiles(run):
 
 
 def test_decode_bwd_sampled_rows(run):
-    s, views, A, ms = run
-    g = ms.rp.g
+    s, views, A, ms, gdec = run
+    g = gdec
     vs_g = to_np(g.view_start).astype(np.int64)
     rows = _sample_rows(int(vs_g[-1]), 1000, 14)
     dec = O.decode(s, rows=_row_subset(rows, vs_g, to_np(g.row_anchor)))

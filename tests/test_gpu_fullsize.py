@@ -40,7 +40,20 @@ def run():
     tgt_host = torch.from_numpy(np.concatenate([t.reshape(-1) for t in s.targets]).astype(np.float32)).pin_memory()
     ms.step(tgt_host)
     torch.cuda.synchronize()
-    return s, views, A, ms
+    return s, views, A, ms, decoded(ms, A, views)
+
+
+def decoded(ms, A, views):
+    """The batch's decoded Gaussians: the benchmarked step decodes and projects
+    in one kernel and keeps no 3D Gaussians, so the tests decode again (same
+    BF16 decoder, same rows) to check them and the projection."""
+    g = api.Gauss3D.alloc(ms.rp.cap_rows, A.k, views.V)
+    st = api.new_status()
+    api.decode(A, views, g, ms.rp.dec_ws, st, L.GS_PREC_BF16)
+    torch.cuda.synchronize()
+    assert api.read_status(st)[0] == 0
+    assert torch.equal(g.view_start, ms.rp.g.view_start)
+    return g
 
 
 def _records(rec):
@@ -67,7 +80,7 @@ def _row_subset(rows, view_start, row_anchor):
 
 
 def test_visibility_rows_exact(run):
-    s, views, A, ms = run
+    s, views, A, ms, gdec = run
     vs_g = to_np(ms.rp.g.view_start).astype(np.int64)
     R = int(vs_g[-1])
     ra = to_np(ms.rp.g.row_anchor)[:R]
@@ -80,8 +93,8 @@ def test_visibility_rows_exact(run):
 
 
 def test_decode_sampled_rows(run):
-    s, views, A, ms = run
-    g = ms.rp.g
+    s, views, A, ms, gdec = run
+    g = gdec
     vs_g = to_np(g.view_start).astype(np.int64)
     rows = _sample_rows(int(vs_g[-1]), 3000, 1)
     dec = O.decode(s, rows=_row_subset(rows, vs_g, to_np(g.row_anchor)))
@@ -99,10 +112,9 @@ def _at(t, idx):
     return to_np(t[torch.as_tensor(np.asarray(idx, np.int64)).to(t.device)])
 
 
-def check_projection(s, views, rp, n, seed):
+def check_projection(s, views, g, rp, n, seed):
     """Splat records of n sampled candidates against the oracle's projection
-    of the GPU's own decoded Gaussians (3DGS preliminaries of Sec. III-A)."""
-    g = rp.g
+    of the GPU's own decoded Gaussians g (3DGS preliminaries of Sec. III-A)."""
     vs_g = to_np(g.view_start).astype(np.int64)
     C_ = int(vs_g[-1]) * s.k
     cand = _sample_rows(C_, n, seed)
@@ -188,12 +200,12 @@ def check_pairs(s, views, rp, min_pairs):
 
 
 def test_project_sampled_candidates(run):
-    s, views, A, ms = run
-    check_projection(s, views, ms.rp, 20000, 2)
+    s, views, A, ms, gdec = run
+    check_projection(s, views, gdec, ms.rp, 20000, 2)
 
 
 def test_bin_sort_invariants_all_pairs(run):
-    s, views, A, ms = run
+    s, views, A, ms, gdec = run
     check_pairs(s, views, ms.rp, 10_000_000)
 
 
@@ -249,7 +261,7 @@ def _tile_pixel_mask(views, tiles_sel):
 
 
 def test_render_sampled_tiles_forward_and_backward(run):
-    s, views, A, ms = run
+    s, views, A, ms, gdec = run
     rp = ms.rp
     tiles_sel = _sampled_tiles(ms, views)
     used, r_sub, v_sub = _compact(ms, tiles_sel)
@@ -268,9 +280,9 @@ def test_render_sampled_tiles_forward_and_backward(run):
     # backward of an image gradient on those tiles, same launch as the batched iteration
     dimg = np.random.default_rng(4).normal(size=3 * views.total_pixels) * m
     sgrad = torch.zeros_like(rp.sgrad)
-    out = api.Gauss3DGrad.like(rp.g)
+    out = api.Gauss3DGrad.like(gdec)
     st = api.new_status()
-    api.render_bwd(rp.g, rp.splats, rp.bins, views, rp.image, torch.as_tensor(f32(dimg)).cuda(), sgrad, out, st,
+    api.render_bwd(gdec, rp.splats, rp.bins, views, rp.image, torch.as_tensor(f32(dimg)).cuda(), sgrad, out, st,
                    rp.render_ws, rp.chunk)
     torch.cuda.synchronize()
     assert api.read_status(st)[0] == 0
@@ -285,7 +297,7 @@ def test_render_sampled_tiles_forward_and_backward(run):
     rest[used] = False
     assert np.abs(sg[rest]).max() == 0.0
     # projection chain rule of those splats, from the GPU's decoded Gaussians
-    g = rp.g
+    g = gdec
     vs_c = to_np(g.view_start).astype(np.int64) * s.k
     v = np.searchsorted(vs_c, used, side="right") - 1
     vs_sub = np.concatenate([[0], np.cumsum(np.bincount(v, minlength=views.V))]).astype(np.int64)
@@ -298,8 +310,8 @@ def test_render_sampled_tiles_forward_and_backward(run):
 
 
 def test_decode_bwd_sampled_rows(run):
-    s, views, A, ms = run
-    g = ms.rp.g
+    s, views, A, ms, gdec = run
+    g = gdec
     vs_g = to_np(g.view_start).astype(np.int64)
     rows = _sample_rows(int(vs_g[-1]), 3000, 5)
     dec = O.decode(s, rows=_row_subset(rows, vs_g, to_np(g.row_anchor)))

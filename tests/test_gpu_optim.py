@@ -147,7 +147,7 @@ def test_optimizer_steps_lower_the_mapping_loss():
     views = api.Views(s.cams, s.wh)
     A = api.Anchors.from_scene(s)
     tgt_host = torch.as_tensor(f32(O.targets_flat(s))).pin_memory()
-    ms = pipeline.MappingStep(views, A, precision=L.GS_PREC_BF16)
+    ms = pipeline.MappingStep(views, A, precision=L.GS_PREC_BF16, fuse_projection=False)
     opt = pipeline.Optimizer(A, ms.rp.agrad)
     stats = pipeline.DensifyStats(A)
     xyz0 = A.xyz.clone()
