@@ -467,9 +467,9 @@ int gs_flow_triangulate(const gs_camera *cam1, const gs_camera *cam2, int32_t wi
  * to decide the stop rule again.  chunk and ws must be those of the forward,
  * ws untouched since: tiles cut into several chunks start each chunk from
  * the transmittance and colour prefix the forward left there.  sgrad:
- * per-splat view-space gradients, overwritten for the candidates that cover
- * a tile (sp->tiles > 0; the others are neither written nor read).  out:
- * NULL, or overwritten for every candidate (zeros for culled ones). */
+ * per-splat view-space gradients, overwritten for every candidate up to the
+ * row count (zeros for the ones that cover no tile).  out: NULL, or
+ * overwritten for every candidate (zeros for culled ones). */
 int gs_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *sp,
                   const gs_bins *bins, const gs_view *views, int32_t V, int32_t chunk, void *ws,
                   size_t ws_bytes, const float *image, const float *d_image, const int32_t *last,

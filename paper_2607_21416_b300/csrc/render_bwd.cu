@@ -405,21 +405,25 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(ProjBwdArgs a, ViewTab
 }
 
 // ------------------------------------------------------------ launcher
-// Zeroes the splat gradients of the candidates that cover a tile (the only
-// ones the reverse pass adds into, and the only ones read afterwards).
-__global__ void __launch_bounds__(256) zero_sgrad_kernel(const int32_t *__restrict__ tiles,
-                                                         const int32_t *__restrict__ view_start, int V, int k,
+// Zeroes the splat gradients of every candidate up to the row count (the
+// reverse pass adds into those that cover a tile).  Whole 16-byte pieces:
+// zeroing only the covering candidates would leave sectors shared with a
+// non-covering neighbour partly written, which costs DRAM read-modify-writes.
+__global__ void __launch_bounds__(256) zero_sgrad_kernel(const int32_t *__restrict__ view_start, int V, int k,
                                                          long long cap_cand, float *__restrict__ sgrad,
                                                          const gs_status *st)
 {
     if (has_error(st)) return;
-    const long long C = std::min<long long>((long long)__ldg(view_start + V) * k, cap_cand);
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < C; c += (long long)gridDim.x * blockDim.x)
-        if (__ldg(tiles + c) > 0) {
-            float *g = sgrad + 9 * c;
-#pragma unroll
-            for (int j = 0; j < 9; ++j) g[j] = 0.f;
-        }
+    const long long n = 9 * std::min<long long>((long long)__ldg(view_start + V) * k, cap_cand);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if ((reinterpret_cast<uintptr_t>(sgrad) & 15) == 0) {
+        float4 *v = reinterpret_cast<float4 *>(sgrad);
+        for (long long i = t0; i < n / 4; i += stride) v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (long long i = 4 * (n / 4) + t0; i < n; i += stride) sgrad[i] = 0.f;
+    } else {
+        for (long long i = t0; i < n; i += stride) sgrad[i] = 0.f;
+    }
 }
 
 int launch_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *sp, const gs_bins *bins,
@@ -430,7 +434,7 @@ int launch_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splat
     const long long cap_cand = g->cap_rows * (long long)g->k;
     const int zgrid = (int)std::max<long long>(1, std::min<long long>((cap_cand + 255) / 256,
                                                                       (long long)sm_count() * 16));
-    zero_sgrad_kernel<<<zgrid, 256, 0, s>>>(sp->tiles, g->view_start, vt.V, g->k, cap_cand, sgrad->g, st);
+    zero_sgrad_kernel<<<zgrid, 256, 0, s>>>(g->view_start, vt.V, g->k, cap_cand, sgrad->g, st);
     count_launches(1);
     const float4 *rec = reinterpret_cast<const float4 *>(sp->rec);
     if (vt.total_tiles > 0) {
