@@ -127,10 +127,19 @@ __global__ void __launch_bounds__(1024) radix_scan_rows(uint32_t *__restrict__ h
     if (threadIdx.x == 0) totals[d] = s_warp[31];
 }
 
-__global__ void __launch_bounds__(kSortThreads) radix_downsweep(
+// One scatter pass of the LSD radix sort (8-bit digit at `shift`), stable.
+// kMatch: in-warp ranking by match_any, fast when a warp holds few distinct
+// digits (the top digit of depth or tile keys); otherwise by one ballot per
+// digit bit, whose cost does not depend on the digits.  kRanges (last pass of
+// the tile sort): also records each tile's [start, end) in `ranges`, starts
+// by atomicMin and ends by atomicMin of their complement (the array is set to
+// all ones beforehand; finish_ranges turns untouched tiles into empty ones).
+template <bool kMatch, bool kRanges>
+__global__ void __launch_bounds__(kSortThreads, 4) radix_downsweep(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const uint32_t *__restrict__ n_ptr, int shift,
-    const uint32_t *__restrict__ hist, const uint32_t *__restrict__ totals, const gs_status *st)
+    const uint32_t *__restrict__ hist, const uint32_t *__restrict__ totals, uint32_t *__restrict__ ranges,
+    int n_ranges, const gs_status *st)
 {
     if (__syncthreads_or(has_error(st))) return;   // block-uniform exit
     __shared__ uint32_t s_keys[kRadixTile];
@@ -152,6 +161,17 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep(
     for (int i = tid; i < kSortWarps * 257; i += kSortThreads) s_wh[i] = 0;
     __syncthreads();
     const unsigned ltm = lanemask_lt();
+    // the next tile's keys and values are loaded while the current one is ranked and scattered
+    uint32_t nkey[kRadixItems], nval[kRadixItems];
+    auto load_tile = [&](uint32_t t) {
+#pragma unroll
+        for (int j = 0; j < kRadixItems; ++j) {
+            const uint32_t i = t * kRadixTile + warp * (32 * kRadixItems) + j * 32 + lane;
+            nkey[j] = i < n ? kin[i] : 0u;
+            nval[j] = i < n ? vin[i] : 0u;
+        }
+    };
+    if (t0 < t1) load_tile(t0);
     for (uint32_t t = t0; t < t1; ++t) {
         const uint32_t tb = t * kRadixTile;
         uint32_t key[kRadixItems], val[kRadixItems], loc[kRadixItems];
@@ -159,19 +179,32 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep(
 #pragma unroll
         for (int j = 0; j < kRadixItems; ++j) {
             const uint32_t i = tb + warp * (32 * kRadixItems) + j * 32 + lane;
-            const bool ok = i < n;
-            key[j] = ok ? kin[i] : 0u;
-            val[j] = ok ? vin[i] : 0u;
-            dig[j] = ok ? (int)((key[j] >> shift) & 0xffu) : 256;
+            key[j] = nkey[j];
+            val[j] = nval[j];
+            dig[j] = i < n ? (int)((key[j] >> shift) & 0xffu) : 256;
         }
-        // Stable in-warp ranking, round by round: the lowest lane of each
-        // digit group adds the group size to the warp's counter (shared-memory
-        // atomic, returning the old count) and hands the old count to its peers.
-        // Each leader needs its atomic's result before the shuffle, so the rounds
-        // are ordered by data dependence.
+        if (t + 1 < t1) load_tile(t + 1);
+        // Stable in-warp ranking, round by round: the lanes holding the same
+        // digit are found from one ballot per digit bit (nine bits: 256 marks
+        // an out-of-range lane), at a cost that does not depend on how many
+        // distinct digits the warp holds; the lowest lane of each digit group
+        // adds the group size to the warp's counter (shared-memory atomic,
+        // returning the old count) and hands the old count to its peers.  Each
+        // leader needs its atomic's result before the shuffle, so the rounds are
+        // ordered by data dependence.
 #pragma unroll
         for (int j = 0; j < kRadixItems; ++j) {
-            const unsigned peers = __match_any_sync(0xffffffffu, dig[j]);
+            unsigned peers = 0xffffffffu;
+            if (kMatch) {
+                peers = __match_any_sync(0xffffffffu, dig[j]);
+            } else {
+#pragma unroll
+                for (int bit = 0; bit < 9; ++bit) {
+                    const bool set = (dig[j] >> bit) & 1;
+                    const unsigned b = __ballot_sync(0xffffffffu, set);
+                    peers &= set ? b : ~b;
+                }
+            }
             const int leader = __ffs(peers) - 1;
             const uint32_t rank = __popc(peers & ltm);
             uint32_t old = 0;
@@ -211,6 +244,11 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep(
             if (!idx_ok(st, g, n, 32)) continue;
             kout[g] = k;
             vout[g] = s_vals[i];
+            if (kRanges) {   // equal keys are contiguous in the tile (ordered by the lower digits)
+                if (!idx_ok(st, k, n_ranges, 38)) continue;
+                if (i == 0 || s_keys[i - 1] != k) atomicMin(ranges + 2 * k, g);
+                if (i + 1 == cnt || s_keys[i + 1] != k) atomicMin(ranges + 2 * k + 1, ~(g + 1));
+            }
         }
         __syncthreads();
         s_goff[tid] += s_tcnt[tid];
@@ -306,9 +344,15 @@ __global__ void __launch_bounds__(kSortThreads) compact_valid_kernel(
 #pragma unroll
             for (int j = 0; j < kSortItems; ++j) tl[j] = i0 + j < C ? __ldg(tiles + i0 + j) : 0;
         }
+        // depth keys of the covering candidates, all loads issued before the block scan
+        const float *recf = reinterpret_cast<const float *>(rec);
+        uint32_t dk[kSortItems];
         uint32_t n = 0;
 #pragma unroll
-        for (int j = 0; j < kSortItems; ++j) n += tl[j] > 0;
+        for (int j = 0; j < kSortItems; ++j) {
+            dk[j] = tl[j] > 0 ? __float_as_uint(__ldg(recf + 12 * (size_t)(i0 + j) + 9)) : 0u;
+            n += tl[j] > 0;
+        }
         uint32_t tot;
         uint32_t off = base + scan256(n, s_warp, &tot);
 #pragma unroll
@@ -316,7 +360,7 @@ __global__ void __launch_bounds__(kSortThreads) compact_valid_kernel(
             if (tl[j] > 0) {
                 if (idx_ok(st, (long long)off, C, 31)) {
                     ids[off] = i0 + j;
-                    dkeys[off] = __float_as_uint(__ldg(&rec[3 * (size_t)(i0 + j) + 2]).y);
+                    dkeys[off] = dk[j];
                 }
                 ++off;
             }
@@ -335,8 +379,21 @@ __global__ void __launch_bounds__(kSortThreads) count_pairs_kernel(
     uint32_t t0, t1;
     block_tiles(S, blockIdx.x, gridDim.x, &t0, &t1);
     unsigned long long n = 0;
-    for (uint32_t i = t0 * kSortTile + threadIdx.x; i < min(S, t1 * kSortTile); i += kSortThreads)
-        if (idx_ok(st, ids[i], cap_cand, 34)) n += (uint32_t)__ldg(tiles + ids[i]);
+    for (uint32_t b = t0 * kSortTile; b < min(S, t1 * kSortTile); b += kSortThreads * kSortItems) {
+        uint32_t id[kSortItems];
+        int32_t c[kSortItems];
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {   // the ids, then every tile count, loads issued together
+            const uint32_t i = b + j * kSortThreads + threadIdx.x;
+            id[j] = i < S ? ids[i] : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j)
+            c[j] = (b + j * kSortThreads + threadIdx.x < S && id[j] < cap_cand) ? __ldg(tiles + id[j]) : 0;
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j)
+            if (b + j * kSortThreads + threadIdx.x < S && idx_ok(st, id[j], cap_cand, 34)) n += (uint32_t)c[j];
+    }
     // the per-block total fits 32 bits when the whole total does (checked later)
     __shared__ uint32_t s_warp[32];
     uint32_t tot;
@@ -364,15 +421,16 @@ __global__ void __launch_bounds__(kSortThreads) pair_offsets_kernel(
     uint32_t base = block_off[blockIdx.x];
     for (uint32_t t = t0; t < t1; ++t) {
         const uint32_t i0 = t * kSortTile + threadIdx.x * kSortItems;
-        uint32_t cnt[kSortItems];
+        uint32_t cnt[kSortItems], id[kSortItems];
         uint32_t n = 0;
 #pragma unroll
+        for (int j = 0; j < kSortItems; ++j) id[j] = i0 + j < S ? ids[i0 + j] : 0u;
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j)   // every tile count load issued before any is used
+            cnt[j] = (i0 + j < S && id[j] < cap_cand) ? (uint32_t)__ldg(tiles + id[j]) : 0u;
+#pragma unroll
         for (int j = 0; j < kSortItems; ++j) {
-            cnt[j] = 0;
-            if (i0 + j < S) {
-                const uint32_t id = ids[i0 + j];
-                if (idx_ok(st, id, cap_cand, 35)) cnt[j] = (uint32_t)__ldg(tiles + id);
-            }
+            if (i0 + j < S && !idx_ok(st, id[j], cap_cand, 35)) cnt[j] = 0;
             n += cnt[j];
         }
         uint32_t tot;
@@ -412,13 +470,16 @@ __device__ __forceinline__ uint32_t scanmax256_excl(uint32_t x, uint32_t *s_warp
 }
 
 // Load-balanced emission: CTA rounds write pairs [p0, p0 + 2048).  The splats
-// that own those pairs (at most 2048, every compacted splat owns >= 1; the
-// first from round_first, the last from the next round's first) are staged
-// with their rectangle's first tile, width and the view's tile row length
-// (every thread's loads issued together); each staged splat marks the
-// round-local position of its first pair in s_own and a max-scan fills every
-// pair's position with its owner.  Pair t of a splat is tile (t % w, t / w)
-// of its rectangle, row-major.
+// owning them run from round_first[r] (the splat holding p0) to
+// round_first[r + 1] (the one holding the next round's first pair; it owns a
+// pair of this round unless it starts exactly there) -- at most 2048 splats,
+// since every compacted splat owns >= 1 pair.  Every thread reads the two
+// bounds itself, and those of the CTA's next round are loaded while the
+// current round runs.  The staged splats keep their rectangle's first tile,
+// width and the view's tile row length (every thread's loads issued
+// together); each marks the round-local position of its first pair in s_own
+// and a max-scan fills every pair's position with its owner.  Pair t of a
+// splat is tile (t % w, t / w) of its rectangle, row-major.
 __global__ void __launch_bounds__(kSortThreads) emit_pairs_kernel(
     const uint32_t *__restrict__ ids, const uint32_t *__restrict__ n_ptr, const uint32_t *__restrict__ np_ptr,
     const uint32_t *__restrict__ offs, const uint32_t *__restrict__ round_first, const float4 *__restrict__ rec,
@@ -428,51 +489,60 @@ __global__ void __launch_bounds__(kSortThreads) emit_pairs_kernel(
     if (__syncthreads_or(has_error(st))) return;   // block-uniform exit
     constexpr int kPer = kEmitPairs / kSortThreads;   // staged splats / pairs per thread and round
     const uint32_t S = *n_ptr, P = *np_ptr;
+    const uint32_t nrounds = (P + kEmitPairs - 1) / kEmitPairs;
     __shared__ uint32_t s_off[kEmitPairs], s_t00[kEmitPairs], s_id[kEmitPairs];
     __shared__ __align__(16) uint32_t s_own[kEmitPairs];
     __shared__ uint16_t s_w[kEmitPairs], s_tx[kEmitPairs];
-    __shared__ uint32_t s_first, s_count, s_warp[32];
+    __shared__ uint32_t s_warp[32];
     const int tid = threadIdx.x;
     uint4 *own4 = reinterpret_cast<uint4 *>(s_own);
-    for (uint32_t p0 = blockIdx.x * (uint32_t)kEmitPairs; p0 < P; p0 += gridDim.x * (uint32_t)kEmitPairs) {
-        const uint32_t p1 = min(P, p0 + (uint32_t)kEmitPairs);
-        if (tid == 0) {   // splats owning p0 and p1 - 1
-            const uint32_t r = p0 / (uint32_t)kEmitPairs;
-            const uint32_t a = round_first[r];
-            uint32_t c = S - 1;
-            if (p1 < P) {   // the splat owning p1, unless p1 starts it
-                c = round_first[r + 1];
-                if (idx_ok(st, (long long)c, S, 39) && offs[c] == p1) --c;
-            }
-            const bool ok = idx_ok(st, (long long)a, S, 39) && idx_ok(st, (long long)c, S, 39) &&
-                            idx_ok(st, (long long)c - (long long)a, kEmitPairs, 39);
-            s_first = a;
-            s_count = ok ? c - a + 1 : 0;
-        }
+    uint32_t na = 0, nc = 0;   // bounds of the CTA's next round
+    auto bounds = [&](uint32_t r) {
+        na = round_first[r];
+        nc = r + 1 < nrounds ? round_first[r + 1] : S - 1;
+    };
+    if (blockIdx.x < nrounds) bounds(blockIdx.x);
+    for (uint32_t r = blockIdx.x; r < nrounds; r += gridDim.x) {
+        const uint32_t p0 = r * (uint32_t)kEmitPairs, p1 = min(P, p0 + (uint32_t)kEmitPairs);
+        const uint32_t sa = na, sc = nc;
+        if (r + gridDim.x < nrounds) bounds(r + gridDim.x);
+        uint32_t ns = 0;
+        if (sa < S && sc < S && sc >= sa && sc - sa <= (uint32_t)kEmitPairs)
+            ns = min(sc - sa + 1, (uint32_t)kEmitPairs);   // 2049 only if the last starts at p1
+        else if (tid == 0)
+            idx_ok(st, (long long)sc - (long long)sa, -1, 39);
         own4[2 * tid] = make_uint4(0u, 0u, 0u, 0u);
         own4[2 * tid + 1] = make_uint4(0u, 0u, 0u, 0u);
-        __syncthreads();
-        const uint32_t sa = s_first, ns = s_count;
-        uint32_t idv[kPer];
+        uint32_t idv[kPer], ov[kPer], oe[kPer];
 #pragma unroll
         for (int u = 0; u < kPer; ++u) {
             const uint32_t j = tid + u * kSortThreads;
-            idv[u] = j < ns ? ids[sa + j] : 0u;
+            const bool in = j < ns;
+            idv[u] = in ? ids[sa + j] : 0u;
+            ov[u] = in ? offs[sa + j] : 0u;
+            oe[u] = in ? (sa + j + 1 < S ? offs[sa + j + 1] : P) : 0u;
         }
+        float2 rv[kPer];
+        const float2 *rec2 = reinterpret_cast<const float2 *>(rec);
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {   // every rectangle load of the round issued before any is used
+            const uint32_t j = tid + u * kSortThreads;
+            rv[u] = (j < ns && idv[u] < cap_cand) ? __ldg(rec2 + 6 * (size_t)idv[u] + 5) : make_float2(0.f, 0.f);
+        }
+        __syncthreads();   // s_own cleared (the previous round's readers are done)
 #pragma unroll
         for (int u = 0; u < kPer; ++u) {
             const uint32_t j = tid + u * kSortThreads;
             if (j >= ns) continue;
-            const uint32_t sidx = sa + j, id = idv[u];
-            const uint32_t o = offs[sidx];
+            const uint32_t id = idv[u];
+            const uint32_t o = ov[u];
             uint32_t t00 = 0, w = 1, tx = 1;
             if (idx_ok(st, id, cap_cand, 36)) {
-                const float4 r2 = __ldg(&rec[3 * (size_t)id + 2]);
-                const uint32_t rx = __float_as_uint(r2.z), ry = __float_as_uint(r2.w);
+                const uint32_t rx = __float_as_uint(rv[u].x), ry = __float_as_uint(rv[u].y);
                 const int x0 = rx & 0xffff, x1 = rx >> 16, y0 = ry & 0xffff, y1 = ry >> 16;
                 const int v = view_of_row(view_start, vt.V, (int)(id / (uint32_t)k));
                 // the splat's tile count from its offsets (no second read of tiles_touched)
-                const long long cnt = (long long)(sidx + 1 < S ? offs[sidx + 1] : P) - (long long)o;
+                const long long cnt = (long long)oe[u] - (long long)o;
                 if ((long long)(x1 - x0) * (y1 - y0) != cnt || x1 > vt.TX[v] || y1 > vt.TY[v] || x1 <= x0)
                     idx_ok(st, (long long)id, -1, 36);
                 w = (uint32_t)max(x1 - x0, 1);
@@ -484,8 +554,10 @@ __global__ void __launch_bounds__(kSortThreads) emit_pairs_kernel(
             s_w[j] = (uint16_t)w;
             s_tx[j] = (uint16_t)tx;
             s_id[j] = id;
+            if (o >= p1) continue;                      // starts at the next round's first pair
             const uint32_t at = o > p0 ? o - p0 : 0u;   // the first staged splat starts at or before p0
-            if (idx_ok(st, (long long)at, kEmitPairs, 39)) s_own[at] = j;
+            if (j > 0 && o < p0) idx_ok(st, (long long)o, -1, 39);   // only the first may start before p0
+            s_own[at] = j;
         }
         __syncthreads();
         {   // fill forward: thread t owns positions 8t .. 8t + 7
@@ -512,18 +584,15 @@ __global__ void __launch_bounds__(kSortThreads) emit_pairs_kernel(
     }
 }
 
-__global__ void __launch_bounds__(256) ranges_kernel(const uint32_t *__restrict__ tkeys,
-                                                     const uint32_t *__restrict__ n_ptr,
-                                                     uint32_t *__restrict__ ranges, int total_tiles,
+// Tiles no pair touched keep the all-ones fill: empty range (0, 0); the
+// others hold the complement of their end.
+__global__ void __launch_bounds__(256) finish_ranges(uint32_t *__restrict__ ranges, int total_tiles,
                                                      const gs_status *st)
 {
     if (has_error(st)) return;
-    const uint32_t P = *n_ptr;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
-        const uint32_t t = tkeys[i];
-        if (!idx_ok(st, t, total_tiles, 38)) continue;
-        if (i == 0 || tkeys[i - 1] != t) ranges[2 * t] = i;
-        if (i == P - 1 || tkeys[i + 1] != t) ranges[2 * t + 1] = i + 1;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total_tiles; t += gridDim.x * blockDim.x) {
+        const uint2 r = reinterpret_cast<const uint2 *>(ranges)[t];
+        reinterpret_cast<uint2 *>(ranges)[t] = r.x == 0xffffffffu ? make_uint2(0u, 0u) : make_uint2(r.x, ~r.y);
     }
 }
 
@@ -585,14 +654,26 @@ size_t bin_sort_workspace_bytes(const ViewTable &vt, long long cap_cand, long lo
     return layout(cap_cand, cap_pairs).total;
 }
 
+// LSD radix sort of (key, value) over the low `bits` bits, 8 per pass.  The
+// top digit is ranked by match_any (few distinct values in depth and tile
+// keys); with `ranges`, the last pass also records the tile ranges.
 static void radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, const uint32_t *n_ptr,
                        int bits, uint32_t *hist, uint32_t *totals, int nb, gs_status *st, cudaStream_t s,
-                       uint32_t **k_out, uint32_t **v_out)
+                       uint32_t **k_out, uint32_t **v_out, uint32_t *ranges = nullptr, int n_ranges = 0)
 {
     for (int shift = 0; shift < bits; shift += 8) {
         radix_upsweep<<<nb, kSortThreads, 0, s>>>(k0, n_ptr, shift, hist, st);
         radix_scan_rows<<<256, 1024, 0, s>>>(hist, nb, totals, st);
-        radix_downsweep<<<nb, kSortThreads, 0, s>>>(k0, v0, k1, v1, n_ptr, shift, hist, totals, st);
+        const bool top = shift + 8 >= bits;
+        if (top && ranges)
+            radix_downsweep<true, true><<<nb, kSortThreads, 0, s>>>(k0, v0, k1, v1, n_ptr, shift, hist, totals,
+                                                                    ranges, n_ranges, st);
+        else if (top)
+            radix_downsweep<true, false><<<nb, kSortThreads, 0, s>>>(k0, v0, k1, v1, n_ptr, shift, hist, totals,
+                                                                     nullptr, 0, st);
+        else
+            radix_downsweep<false, false><<<nb, kSortThreads, 0, s>>>(k0, v0, k1, v1, n_ptr, shift, hist, totals,
+                                                                      nullptr, 0, st);
         std::swap(k0, k1);
         std::swap(v0, v1);
         count_launches(3);
@@ -645,12 +726,14 @@ int launch_bin_sort(const gs_splats *sp, int k, const int32_t *view_start, long 
                                                               view_start, k, ek, ev, vt, cap_cand, st);
     count_launches(4);
     // 4. stable sort on the tile id
+    // 5. tile ranges, recorded by the last pass (+ optional 64-bit keys)
     uint32_t *tk_s, *tv_s;
-    radix_sort(ek, ev, ok, ov, n_pairs, tile_bits, hist, totals, nb, st, s, &tk_s, &tv_s);
-    // 5. ranges (+ optional 64-bit keys)
-    cudaMemsetAsync(bins->ranges, 0, sizeof(uint32_t) * 2 * (size_t)vt.total_tiles, s);
+    cudaMemsetAsync(bins->ranges, 0xff, sizeof(uint32_t) * 2 * (size_t)vt.total_tiles, s);
+    radix_sort(ek, ev, ok, ov, n_pairs, tile_bits, hist, totals, nb, st, s, &tk_s, &tv_s, bins->ranges,
+               (int)vt.total_tiles);
     const int g = sm_count() * 8;
-    ranges_kernel<<<g, 256, 0, s>>>(tk_s, n_pairs, bins->ranges, vt.total_tiles, st);
+    finish_ranges<<<(int)std::min<long long>(g, (vt.total_tiles + 255) / 256), 256, 0, s>>>(bins->ranges,
+                                                                                       (int)vt.total_tiles, st);
     count_launches(1);
     if (bins->keys) {
         keys_kernel<<<g, 256, 0, s>>>(tk_s, tv_s, n_pairs, rec, reinterpret_cast<unsigned long long *>(bins->keys), st);

@@ -41,7 +41,8 @@ __device__ __forceinline__ void proj_bwd_one(const Cam &cm, float W, float H, fl
     const bool inx = ux >= -limx && ux <= limx, iny = uy >= -limy && uy <= limy;
     const float txz = fminf(fmaxf(ux, -limx), limx), tyz = fminf(fmaxf(uy, -limy), limy);
     const float fx = cm.fx, fy = cm.fy, z = pz;
-    const float J[6] = {fx / z, 0.f, -fx * txz / z, 0.f, fy / z, -fy * tyz / z};
+    const float iz = 1.f / z;   // one division; the clamp decisions above use the forward's quotients
+    const float J[6] = {fx * iz, 0.f, -fx * txz * iz, 0.f, fy * iz, -fy * tyz * iz};
     float T[6];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
@@ -96,15 +97,15 @@ __device__ __forceinline__ void proj_bwd_one(const Cam &cm, float W, float H, fl
 #pragma unroll
         for (int j = 0; j < 3; ++j)
             dJ[3 * i + j] = dT[3 * i] * cm.R[3 * j] + dT[3 * i + 1] * cm.R[3 * j + 1] + dT[3 * i + 2] * cm.R[3 * j + 2];
-    const float iz2 = 1.f / (z * z);
+    const float iz2 = iz * iz;
     float dp0 = 0.f, dp1 = 0.f, dp2 = 0.f;
     dp2 += dJ[0] * (-fx * iz2) + dJ[4] * (-fy * iz2);
     dp2 += dJ[2] * (fx * txz * iz2);
-    if (inx) { dp0 += dJ[2] * (-fx * iz2); dp2 += dJ[2] * (fx * px * iz2 / z); }
+    if (inx) { dp0 += dJ[2] * (-fx * iz2); dp2 += dJ[2] * (fx * px * iz2 * iz); }
     dp2 += dJ[5] * (fy * tyz * iz2);
-    if (iny) { dp1 += dJ[5] * (-fy * iz2); dp2 += dJ[5] * (fy * py * iz2 / z); }
-    dp0 += gmx * fx / z;
-    dp1 += gmy * fy / z;
+    if (iny) { dp1 += dJ[5] * (-fy * iz2); dp2 += dJ[5] * (fy * py * iz2 * iz); }
+    dp0 += gmx * fx * iz;
+    dp1 += gmy * fy * iz;
     dp2 += gmx * (-fx * px * iz2) + gmy * (-fy * py * iz2);
 #pragma unroll
     for (int j = 0; j < 3; ++j) dmu[j] = cm.R[j] * dp0 + cm.R[3 + j] * dp1 + cm.R[6 + j] * dp2;
