@@ -199,10 +199,12 @@ uint64_t gs_kernel_launches(void);
 int gs_set_wait_limit(int64_t ns);
 /* Launch shapes (no counterpart in the paper; set by the autotuner of the
  * Python layer): CTAs per SM of the persistent forward and reverse
- * compositing kernels, of the one-sweep radix-sort passes and of the pair
+ * compositing kernels, of the radix-sort and compaction passes and of the pair
  * emission.  0 keeps the library's choice (as many as fit on an SM for the
- * persistent kernels, 4 for the emission); larger values than fit are
- * clamped to what fits.  None of them changes a result bit except through
+ * persistent kernels, 4 for the sort passes and the emission); the
+ * persistent kernels clamp larger values to what fits, the sort passes take
+ * at most 1024 CTAs and the emission at most 8 per SM.  None of them
+ * changes a result bit except through
  * the order of the reverse pass's floating-point atomics.  Process-wide and
  * read when a call enqueues its kernels (a captured CUDA graph keeps the
  * shapes of its capture).  gs_set_tuning(NULL) restores the defaults;
@@ -502,9 +504,11 @@ int gs_decode_bwd(const gs_anchors *A, const gs_camera *cams, const gs_view *vie
  * applies the projection's chain rule (the near-degenerate branch included)
  * to each candidate it recomputes -- mean x_a + offset exp(l[0:3]), scale
  * exp(l[3:6]) sigmoid, unit quaternion, evaluated with the reverse pass's
- * recomputed decoder activations -- and needs no workspace; with
- * GS_PREC_FP32 the two steps run one after the other through a workspace of
- * gs_decode_project_bwd_workspace bytes (256-byte aligned).  sp->tiles marks
+ * recomputed decoder activations; its workspace holds the splat gradients
+ * rearranged in tiles of 128 rows (9 k floats per row), so that the decoder's
+ * one-thread-per-row reads are coalesced.  With GS_PREC_FP32 the two steps
+ * run one after the other through the workspace.  Workspace:
+ * gs_decode_project_bwd_workspace bytes, 256-byte aligned.  sp->tiles marks
  * the candidates that cover a tile (the others get no gradient).  out is
  * overwritten. */
 size_t gs_decode_project_bwd_workspace(int32_t k, int64_t cap_rows, int32_t precision);

@@ -9,7 +9,7 @@ device:
                     is cut into chunks of this many splats)
   fwd_ctas_per_sm   CTAs per SM of the persistent forward compositing kernels
   bwd_ctas_per_sm   CTAs per SM of the persistent reverse compositing kernel
-  sort_ctas_per_sm  CTAs per SM of the one-sweep radix-sort passes
+  sort_ctas_per_sm  CTAs per SM of the radix-sort and compaction passes
   emit_ctas_per_sm  CTAs per SM of the pair emission
 
 (0 is the library's own choice for the last four; see gs_set_tuning).  `tune`
@@ -40,7 +40,7 @@ SPACE = {
     "chunk": (0, 256, 512, 768, 1024),
     "bwd_ctas_per_sm": (0, 4, 6, 8),
     "fwd_ctas_per_sm": (0, 4, 6, 8),
-    "sort_ctas_per_sm": (0, 1, 2),
+    "sort_ctas_per_sm": (0, 2, 3),
     "emit_ctas_per_sm": (0, 2, 6, 8),
 }
 

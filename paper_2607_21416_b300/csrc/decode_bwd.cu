@@ -288,8 +288,7 @@ static int launch_decode_bwd_impl(const gs_anchors *A, const gs_camera *cams, co
         a.dmu = dg->dmu; a.dscale = dg->dscale; a.dquat = dg->dquat; a.dopacity = dg->dopacity; a.dcolour = dg->dcolour;
     }
     a.dxyz = out->dxyz; a.dfeat = out->dfeat; a.dls = out->dlog_scaling; a.doff = out->doffsets; a.dmlp = out->dmlp;
-    a.sgrad = dg ? nullptr : sgrad;
-    a.tiles = dg ? nullptr : sp->tiles;
+    a.sgT = dg ? nullptr : sgrad;
     for (int v = 0; v < GS_MAX_VIEWS; ++v) {
         a.W[v] = v < vt.V ? vt.W[v] : 0;
         a.H[v] = v < vt.V ? vt.H[v] : 0;
@@ -321,9 +320,55 @@ int launch_decode_bwd(const gs_anchors *A, const gs_camera *cams, const ViewTabl
 
 // Workspace of the fused reverse: none for the tensor-core path; the FP32 path
 // keeps the candidates' 3D gradients (14 floats each) between its two steps.
+// Rows per tile of the tensor-core reverse decoder (its kBRows).
+constexpr int kRowTile = 128;
+
+// The splat gradients [C][9] of the candidates rearranged in row tiles,
+// out[((t k + i) 9 + v) 128 + r] = sgrad[9 ((128 t + r) k + i) + v] for the
+// candidates that cover a tile and zero for the others and for rows past the
+// row count: in that layout the reverse decoder, one thread per row, reads
+// each value with one coalesced load per warp.  A block stages one tile's
+// contiguous gradients (128 k 9 floats) and tile counts in shared memory.
+__global__ void __launch_bounds__(256) sgrad_row_tiles(const float *__restrict__ sgrad,
+                                                       const int32_t *__restrict__ tiles,
+                                                       const int32_t *__restrict__ view_start, int V, int k,
+                                                       long long cap_rows, float *__restrict__ out,
+                                                       const gs_status *st)
+{
+    if (has_error(st)) return;
+    extern __shared__ __align__(16) float s_g[];   // [128 k 9] gradients, then [128 k] tile counts
+    int32_t *s_t = reinterpret_cast<int32_t *>(s_g + (size_t)kRowTile * k * 9);
+    const long long rows = std::min<long long>(__ldg(view_start + V), cap_rows);
+    const long long ntiles = (rows + kRowTile - 1) / kRowTile;
+    const int per = kRowTile * k;   // candidates per tile
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const long long c0 = t * per;
+        const int nc = (int)std::min<long long>(per, rows * k - c0);   // candidates of this tile below the row count
+        const float *src = sgrad + 9 * c0;
+        if ((reinterpret_cast<uintptr_t>(src) & 15) == 0 && (nc * 9) % 4 == 0) {
+            for (int i = threadIdx.x; i < nc * 9 / 4; i += blockDim.x)
+                reinterpret_cast<float4 *>(s_g)[i] = __ldg(reinterpret_cast<const float4 *>(src) + i);
+        } else {
+            for (int i = threadIdx.x; i < nc * 9; i += blockDim.x) s_g[i] = __ldg(src + i);
+        }
+        for (int i = threadIdx.x; i < per; i += blockDim.x) s_t[i] = i < nc ? __ldg(tiles + c0 + i) : 0;
+        __syncthreads();
+        float *dst = out + (size_t)t * per * 9;
+        for (int o = threadIdx.x; o < per * 9; o += blockDim.x) {
+            const int r = o % kRowTile, q = o / kRowTile;   // q = 9 i + v
+            const int c = r * k + q / 9;
+            dst[o] = s_t[c] > 0 ? s_g[9 * c + q % 9] : 0.f;
+        }
+        __syncthreads();
+    }
+}
+
 size_t decode_project_bwd_workspace_bytes(int k, long long cap_rows, int precision)
 {
-    if (precision == GS_PREC_BF16) return 0;
+    if (precision == GS_PREC_BF16) {
+        const size_t tiles = (size_t)std::max<long long>((cap_rows + kRowTile - 1) / kRowTile, 1);
+        return align_up(sizeof(float) * 9 * (size_t)k * kRowTile * tiles, 256);
+    }
     const size_t C = (size_t)std::max<long long>(cap_rows * k, 1);
     return align_up(sizeof(float) * 3 * C, 256) * 3 + align_up(sizeof(float) * 4 * C, 256) +
            align_up(sizeof(float) * C, 256);
@@ -333,8 +378,24 @@ int launch_decode_project_bwd(const gs_anchors *A, const gs_camera *cams, const 
                               const gs_gauss3d *g, const gs_splats *sp, const gs_splat_grad *sgrad,
                               gs_anchor_grad *out, void *ws, gs_status *st, cudaStream_t s)
 {
-    if (precision == GS_PREC_BF16)
-        return launch_decode_bwd_impl(A, cams, vt, precision, g, nullptr, sp, sgrad->g, out, st, s);
+    if (precision == GS_PREC_BF16) {
+        // the splat gradients in row tiles (workspace), then the fused reverse
+        float *sgT = reinterpret_cast<float *>(ws);
+        const size_t smem = sizeof(float) * 10 * (size_t)kRowTile * g->k;
+        static size_t configured = 0;
+        if (smem > 48 * 1024 && smem > configured) {
+            if (cudaFuncSetAttribute(sgrad_row_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess)
+                return GS_ERR_UNSUPPORTED;
+            configured = smem;
+        }
+        const long long tiles = std::max<long long>((g->cap_rows + kRowTile - 1) / kRowTile, 1);
+        const int grid = (int)std::min<long long>(tiles, (long long)sm_count() * 4);
+        sgrad_row_tiles<<<grid, 256, smem, s>>>(sgrad->g, sp->tiles, g->view_start, vt.V, g->k, g->cap_rows, sgT,
+                                                st);
+        count_launches(1);
+        return launch_decode_bwd_impl(A, cams, vt, precision, g, nullptr, sp, sgT, out, st, s);
+    }
     // FP32: the projection's chain rule into the workspace, then the decoders' reverse
     const size_t C = (size_t)std::max<long long>(g->cap_rows * g->k, 1);
     char *w = reinterpret_cast<char *>(ws);

@@ -300,8 +300,22 @@ __global__ void __launch_bounds__(kBThreads) decode_bwd_tc_kernel(DecodeBwdArgsB
         // overwrite it, so every further pass of the tile writes it again)
         auto write_u = [&](bool hi_too) {
             const float *fr = f.feat + (size_t)(an >= 0 ? an : 0) * s.F;
+            // 16-byte feature loads where the rows allow them (fewer requests of this uncoalesced read)
+            const bool fvec = (s.F & 3) == 0 && (reinterpret_cast<uintptr_t>(f.feat) & 15) == 0;
             for (int kc = 0; kc < s.KP; kc += 8) {
-                float u[8], lo[8];
+                float u[8], lo[8], fv[8];
+                if (an >= 0 && fvec && kc >= 8 && kc + 8 <= 8 + s.F) {
+                    const float4 q0 = __ldg(reinterpret_cast<const float4 *>(fr + (kc - 8)));
+                    const float4 q1 = __ldg(reinterpret_cast<const float4 *>(fr + (kc - 4)));
+                    fv[0] = q0.x; fv[1] = q0.y; fv[2] = q0.z; fv[3] = q0.w;
+                    fv[4] = q1.x; fv[5] = q1.y; fv[6] = q1.z; fv[7] = q1.w;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int c = kc + j;
+                        fv[j] = (an >= 0 && c >= 8 && c < 8 + s.F) ? __ldg(fr + (c - 8)) : 0.f;
+                    }
+                }
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int c = kc + j;
@@ -312,7 +326,7 @@ __global__ void __launch_bounds__(kBThreads) decode_bwd_tc_kernel(DecodeBwdArgsB
                         else if (c == 2) x = d2 * inv_dl;
                         else if (c == 3) x = dl;
                         else if (c == 4) x = 1.f;
-                        else if (c >= 8 && c < 8 + s.F) x = __ldg(fr + (c - 8));
+                        else if (c >= 8 && c < 8 + s.F) x = fv[j];
                     }
                     u[j] = x;
                     lo[j] = x - __bfloat162float(__float2bfloat16_rn(x));
@@ -412,6 +426,25 @@ __global__ void __launch_bounds__(kBThreads) decode_bwd_tc_kernel(DecodeBwdArgsB
             for (int cc = 0; cc < 4; ++cc) {
                 if (16 * cc >= s.Noc) break;
                 float dz[16];
+                // d opacity, d colour of the chunk's candidates: from their splat gradients (fused
+                // with the projection's reverse; zero for a splat that covers no tile) or given --
+                // every load issued before any is used
+                float gin[16];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int i = 4 * cc + j;
+                    const bool ok = mine && i < k;
+                    const size_t ci = c0 + (ok ? i : 0);
+                    if (a.sgT) {   // row-tiled splat gradients: one coalesced load per value and warp
+                        const float *sgp = a.sgT + ((size_t)tile * k + (ok ? i : 0)) * 9 * kBRows + tid;
+#pragma unroll
+                        for (int ch = 0; ch < 4; ++ch) gin[4 * j + ch] = ok ? __ldg(sgp + (5 + ch) * kBRows) : 0.f;
+                    } else {
+                        gin[4 * j] = ok ? __ldg(a.dopacity + ci) : 0.f;
+#pragma unroll
+                        for (int ch = 0; ch < 3; ++ch) gin[4 * j + 1 + ch] = ok ? __ldg(a.dcolour + 3 * ci + ch) : 0.f;
+                    }
+                }
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const int i = 4 * cc + j, o = 16 * cc + 4 * j;
@@ -420,20 +453,7 @@ __global__ void __launch_bounds__(kBThreads) decode_bwd_tc_kernel(DecodeBwdArgsB
                     const float op = tanh_fast(zoc[o] + b2[o]);
                     if (!(op > 0.f)) continue;   // culled by decoding: no gradient
                     live |= 1u << i;
-                    // d opacity, d colour: from the candidate's splat gradient (fused with the
-                    // projection's reverse; zero for a splat that covers no tile) or given
-                    float gop, gcol[3];
-                    if (a.sgrad) {
-                        const bool drawn = __ldg(a.tiles + c0 + i) > 0;
-                        const float *sgp = a.sgrad + 9 * (c0 + i);
-                        gop = drawn ? __ldg(sgp + 5) : 0.f;
-#pragma unroll
-                        for (int ch = 0; ch < 3; ++ch) gcol[ch] = drawn ? __ldg(sgp + 6 + ch) : 0.f;
-                    } else {
-                        gop = __ldg(a.dopacity + c0 + i);
-#pragma unroll
-                        for (int ch = 0; ch < 3; ++ch) gcol[ch] = __ldg(a.dcolour + 3 * (c0 + i) + ch);
-                    }
+                    const float gop = gin[4 * j], gcol[3] = {gin[4 * j + 1], gin[4 * j + 2], gin[4 * j + 3]};
                     dz[4 * j] = gop * (1.f - op * op);
 #pragma unroll
                     for (int ch = 0; ch < 3; ++ch) {
@@ -459,44 +479,73 @@ __global__ void __launch_bounds__(kBThreads) decode_bwd_tc_kernel(DecodeBwdArgsB
             for (int cc = 0; cc < s.Ncov; cc += 16) {
                 float v[16], dz[16];
                 tc::tmem_ld16(tc::tmem_addr(tmem, warp, cc), v);
+                // inputs of the chunk's two candidates, every load issued before any is used: the
+                // offsets, and the splat gradients (d mean2d, d conic) or the given 3D gradients
+                float pin[2][10], ofv[2][3];
+                bool drawn[2];
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int i = cc / 8 + j;
+                    const bool ok = i < k && (live >> i & 1u);
+                    const size_t ci = c0 + (ok ? i : 0);
+                    const float *off = f.offsets + ((size_t)(ok ? an : 0) * k + (ok ? i : 0)) * 3;
+#pragma unroll
+                    for (int e = 0; e < 3; ++e) ofv[j][e] = ok ? __ldg(off + e) : 0.f;
+                    if (a.sgT) {
+                        const float *sgp = a.sgT + ((size_t)tile * k + (ok ? i : 0)) * 9 * kBRows + tid;
+#pragma unroll
+                        for (int e = 0; e < 5; ++e) pin[j][e] = ok ? __ldg(sgp + e * kBRows) : 0.f;
+#pragma unroll
+                        for (int e = 5; e < 10; ++e) pin[j][e] = 0.f;
+                        // zero for a splat that covers no tile: no projection reverse (and no
+                        // arithmetic on a culled candidate's projection)
+                        drawn[j] = ok && (pin[j][0] != 0.f || pin[j][1] != 0.f || pin[j][2] != 0.f ||
+                                          pin[j][3] != 0.f || pin[j][4] != 0.f);
+                    } else {
+                        drawn[j] = ok;
+#pragma unroll
+                        for (int e = 0; e < 3; ++e) {
+                            pin[j][e] = ok ? __ldg(a.dscale + 3 * ci + e) : 0.f;
+                            pin[j][3 + e] = ok ? __ldg(a.dmu + 3 * ci + e) : 0.f;
+                        }
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) pin[j][6 + e] = ok ? __ldg(a.dquat + 4 * ci + e) : 0.f;
+                    }
+                }
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
                     const int i = cc / 8 + j, o = s.Noc + cc + 8 * j;
 #pragma unroll
                     for (int e = 0; e < 8; ++e) dz[8 * j + e] = 0.f;
                     if (i >= k || !(live >> i & 1u)) continue;
-                    const size_t ci = c0 + i;
-                    const float *off = f.offsets + ((size_t)an * k + i) * 3;
                     float sgv[3], q[4], dsv[3], dq[4], dmv[3], qd = 0.f;
 #pragma unroll
                     for (int e = 0; e < 3; ++e) sgv[e] = sigmoid_fast(v[8 * j + e] + b2[o + e]);
 #pragma unroll
                     for (int e = 0; e < 4; ++e) q[e] = v[8 * j + 3 + e] + b2[o + 3 + e];
                     const float inv = rsqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-                    if (a.sgrad) {
+                    if (a.sgT) {
                         // the projection's reverse on the recomputed Gaussian: mean x_a + offset *
                         // exp(l[0:3]), scale exp(l[3:6]) sigmoid, unit quaternion
 #pragma unroll
                         for (int e = 0; e < 3; ++e) dsv[e] = dmv[e] = 0.f;
 #pragma unroll
                         for (int e = 0; e < 4; ++e) dq[e] = 0.f;
-                        if (__ldg(a.tiles + ci) > 0) {
-                            const float *sgp = a.sgrad + 9 * ci;
+                        if (drawn[j]) {
                             const float sc[3] = {el[3] * sgv[0], el[4] * sgv[1], el[5] * sgv[2]};
                             const float qu[4] = {q[0] * inv, q[1] * inv, q[2] * inv, q[3] * inv};
-                            proj_bwd_one(cam, (float)a.W[vw], (float)a.H[vw], xa[0] + __ldg(off) * el[0],
-                                         xa[1] + __ldg(off + 1) * el[1], xa[2] + __ldg(off + 2) * el[2], sc, qu,
-                                         __ldg(sgp), __ldg(sgp + 1), __ldg(sgp + 2), __ldg(sgp + 3), __ldg(sgp + 4),
-                                         dmv, dsv, dq);
+                            proj_bwd_one(cam, (float)a.W[vw], (float)a.H[vw], xa[0] + ofv[j][0] * el[0],
+                                         xa[1] + ofv[j][1] * el[1], xa[2] + ofv[j][2] * el[2], sc, qu, pin[j][0],
+                                         pin[j][1], pin[j][2], pin[j][3], pin[j][4], dmv, dsv, dq);
                         }
                     } else {
 #pragma unroll
                         for (int e = 0; e < 3; ++e) {
-                            dsv[e] = __ldg(a.dscale + 3 * ci + e);
-                            dmv[e] = __ldg(a.dmu + 3 * ci + e);
+                            dsv[e] = pin[j][e];
+                            dmv[e] = pin[j][3 + e];
                         }
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) dq[e] = __ldg(a.dquat + 4 * ci + e);
+                        for (int e = 0; e < 4; ++e) dq[e] = pin[j][6 + e];
                     }
 #pragma unroll
                     for (int e = 0; e < 3; ++e) {
@@ -512,7 +561,7 @@ __global__ void __launch_bounds__(kBThreads) decode_bwd_tc_kernel(DecodeBwdArgsB
                         const float gm = dmv[e];
                         gx[e] += gm;
                         atomicAdd(a.doff + ((size_t)an * k + i) * 3 + e, gm * el[e]);
-                        gls[e] += gm * __ldg(off + e) * el[e];
+                        gls[e] += gm * ofv[j][e] * el[e];
                     }
                 }
                 put8_bf16(sm + s.o_A, tc::kmajor_offset(tid, s.Noc + cc, s.NZ), dz);

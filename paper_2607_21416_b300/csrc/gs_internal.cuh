@@ -27,9 +27,10 @@ struct DecodeBwdArgsB {
     const float *dmu, *dscale, *dquat, *dopacity, *dcolour;
     float *dxyz, *dfeat, *dls, *doff, *dmlp;
     // fused with the projection's reverse (tcgen05 path): the splat gradients
-    // [C][9] and tile counts replace the five gradients above (NULL: not fused)
-    const float *sgrad;
-    const int32_t *tiles;
+    // in row tiles, [tile of 128 rows][i < k][9][128 rows] (zero for a
+    // candidate that covers no tile), replace the five gradients above (NULL:
+    // not fused)
+    const float *sgT;
     int W[GS_MAX_VIEWS], H[GS_MAX_VIEWS];
 };
 int launch_decode_bwd_bf16(const DecodeBwdArgsB &a, cudaStream_t s);
