@@ -329,8 +329,15 @@ __global__ void __launch_bounds__(kTThreads) decode_tc_kernel(DecodeArgs a, TcSh
                 for (int e = 0; e < 3; ++e) xa[e] = mine ? __ldg(a.xyz + 3 * an + e) : 0.f;
                 const float *off = a.offsets + (size_t)(an >= 0 ? an : 0) * k * 3;
                 const size_t c0 = (size_t)row * k;
+                // the offsets of candidate i + 1 are loaded while candidate i is projected
+                float on[3];
+#pragma unroll
+                for (int e = 0; e < 3; ++e) on[e] = mine ? __ldg(off + e) : 0.f;
                 for (int i = 0; i < k; ++i) {
                     float vo[4], vc[8];
+                    const float oc[3] = {on[0], on[1], on[2]};
+#pragma unroll
+                    for (int e = 0; e < 3; ++e) on[e] = (mine && i + 1 < k) ? __ldg(off + 3 * (i + 1) + e) : 0.f;
                     __syncwarp();
                     tc::tmem_ld4(tc::tmem_addr(tmem, warp, 4 * i), vo);            // all lanes: warp-collective
                     tc::tmem_ld8(tc::tmem_addr(tmem, warp, s.Noc + 8 * i), vc);
@@ -346,9 +353,9 @@ __global__ void __launch_bounds__(kTThreads) decode_tc_kernel(DecodeArgs a, TcSh
                         const float inv = rsqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
 #pragma unroll
                         for (int e = 0; e < 4; ++e) q[e] *= inv;
-                        const float m0 = xa[0] + __ldg(off + 3 * i) * el[0];
-                        const float m1 = xa[1] + __ldg(off + 3 * i + 1) * el[1];
-                        const float m2 = xa[2] + __ldg(off + 3 * i + 2) * el[2];
+                        const float m0 = xa[0] + oc[0] * el[0];
+                        const float m1 = xa[1] + oc[1] * el[1];
+                        const float m2 = xa[2] + oc[2] * el[2];
                         float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
                         int nt = 0;
                         project_one(cam, (float)po.W[vw], (float)po.H[vw], po.TX[vw], po.TY[vw], m0, m1, m2, sc, q,
