@@ -37,11 +37,11 @@ __device__ __forceinline__ void proj_bwd_one(const Cam &cm, float W, float H, fl
         for (int j = 0; j < 3; ++j)
             S3[3 * i + j] = M[3 * i] * M[3 * j] + M[3 * i + 1] * M[3 * j + 1] + M[3 * i + 2] * M[3 * j + 2];
     const float limx = kTanClamp * (W / (2.f * cm.fx)), limy = kTanClamp * (H / (2.f * cm.fy));
-    const float ux = px / pz, uy = py / pz;
+    const float iz = 1.f / pz;
+    const float ux = px * iz, uy = py * iz;   // the forward's quotients (same clamp decisions)
     const bool inx = ux >= -limx && ux <= limx, iny = uy >= -limy && uy <= limy;
     const float txz = fminf(fmaxf(ux, -limx), limx), tyz = fminf(fmaxf(uy, -limy), limy);
     const float fx = cm.fx, fy = cm.fy, z = pz;
-    const float iz = 1.f / z;   // one division; the clamp decisions above use the forward's quotients
     const float J[6] = {fx * iz, 0.f, -fx * txz * iz, 0.f, fy * iz, -fy * tyz * iz};
     float T[6];
 #pragma unroll

@@ -45,10 +45,13 @@ __device__ __forceinline__ void project_one(const Cam &cm, float Wv, float Hv, i
         S[5] = Rq[6] * Rq[6] * q0 + Rq[7] * Rq[7] * q1 + Rq[8] * Rq[8] * q2;
         const float W = Wv, H = Hv;
         const float limx = kTanClamp * (W / (2.f * cm.fx)), limy = kTanClamp * (H / (2.f * cm.fy));
-        const float txz = fminf(fmaxf(px / pz, -limx), limx);
-        const float tyz = fminf(fmaxf(py / pz, -limy), limy);
-        const float j00 = cm.fx / pz, j02 = -cm.fx * txz / pz;
-        const float j11 = cm.fy / pz, j12 = -cm.fy * tyz / pz;
+        // one reciprocal of the depth (the reverse pass forms the same quotients for its clamp test)
+        const float iz = 1.f / pz;
+        const float ux = px * iz, uy = py * iz;
+        const float txz = fminf(fmaxf(ux, -limx), limx);
+        const float tyz = fminf(fmaxf(uy, -limy), limy);
+        const float j00 = cm.fx * iz, j02 = -cm.fx * txz * iz;
+        const float j11 = cm.fy * iz, j12 = -cm.fy * tyz * iz;
         // T = J R (2x3)
         float T0[3], T1[3];
 #pragma unroll
@@ -90,8 +93,8 @@ __device__ __forceinline__ void project_one(const Cam &cm, float Wv, float Hv, i
             const float mid = 0.5f * (ca + cc);
             const float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - det));
             const float rad = ceilf(3.f * sqrtf(lam));
-            const float mx = cm.fx * px / pz + cm.cx;
-            const float my = cm.fy * py / pz + cm.cy;
+            const float mx = fmaf(cm.fx, ux, cm.cx);
+            const float my = fmaf(cm.fy, uy, cm.cy);
             const float TX = (float)TXv, TY = (float)TYv;
             const float fx0 = fminf(fmaxf(floorf((mx - rad) * (1.f / kTile)), 0.f), TX);
             const float fx1 = fminf(fmaxf(floorf((mx + rad) * (1.f / kTile)) + 1.f, 0.f), TX);
