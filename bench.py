@@ -184,7 +184,7 @@ def run_ours(args, rank, world, dist):
     import torch
 
     from paper_2607_21416_b300 import _lib as L
-    from paper_2607_21416_b300 import api, pipeline
+    from paper_2607_21416_b300 import api, pipeline, scenes
 
     dev = torch.device("cuda", torch.cuda.current_device())
     scene, path, prec_name, batched = build_workload(args.workload, rank, args.anchors, args.views)
