@@ -267,9 +267,21 @@ __device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const u
                                       ps.g2 * state_plane(plan.state, item, 4)[pid]));
         }
         const int maxlast = __reduce_max_sync(0xffffffffu, max(p0.lim, p1.lim));
-        for (int hi = maxlast; hi > 0; hi -= 32) {
-            const int pl = hi - 1 - lane;   // lane l <-> position hi - 1 - l: hits come back to front
-            const int cnt = warp_stage<false>(WSw, rec, vals, it.s0 + (uint32_t)max(pl, 0), it.s0, pl >= 0,
+        // the block's list (ascending positions): its entries in front of maxlast, back to front
+        const uint32_t *bl = plan.blist + 4ull * it.s0 + (size_t)warp * (it.s1 - it.s0);
+        int je = 0;   // entries with position < maxlast (binary search, every lane the same)
+        {
+            int lo = 0, hi = plan.bcnt[4 * b + warp];
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if ((int)__ldg(bl + mid) < maxlast) lo = mid + 1; else hi = mid;
+            }
+            je = lo;
+        }
+        for (int hj = je; hj > 0; hj -= 32) {
+            const int jl = hj - 1 - lane;   // lane l <-> entry hj - 1 - l: hits come back to front
+            const uint32_t pos = it.s0 + (jl >= 0 ? __ldg(bl + jl) : 0u);
+            const int cnt = warp_stage<false>(WSw, rec, vals, pos, it.s0, jl >= 0,
                                                     cap_cand, st, 53, bx0, bx1, by0, by1);
             for (int e = 0; e < cnt; ++e) {
                 const int p = WSw.pos[e];

@@ -214,6 +214,20 @@ __device__ __forceinline__ int warp_stage(WarpStage &W, const float4 *__restrict
     return __popc(m);
 }
 
+// The 16x4 block w of tile coordinates tc: [bx0, bx1] x [by0, by1].
+struct BlockRect {
+    float x0, x1, y0, y1;
+};
+__device__ __forceinline__ BlockRect block_rect(const TileCoord &tc, int w)
+{
+    BlockRect r;
+    r.x0 = (float)tc.x0;
+    r.x1 = r.x0 + (float)(kTile - 1);
+    r.y0 = (float)(tc.y0 + 4 * w);
+    r.y1 = r.y0 + 3.f;
+    return r;
+}
+
 // Next work unit of the calling warp from a device counter (lane 0 takes it).
 __device__ __forceinline__ int next_unit(int32_t *counter)
 {
@@ -224,10 +238,16 @@ __device__ __forceinline__ int next_unit(int32_t *counter)
 
 struct RenderPlan {
     const int32_t *item_base;   // [T+1]
-    int32_t *counters;          // [4] work-unit counters: forward, fix-up, backward
+    int32_t *counters;          // [8] work-unit counters: forward, fix-up, backward, fix count, block lists
     int32_t *fix;               // [max_items] flags: items with pixels to composite again
     int32_t *fix_list;          // [max_items] those items, counters[3] of them
     float *state;               // [max_items][kStateWords][256]
+    // Block lists of the items of tiles cut into several chunks: for item i
+    // (list positions [s0, s1)) and pixel block w, the positions (relative to
+    // s0, ascending) of the splats whose alpha box meets the block, at
+    // blist[4 s0 + w (s1 - s0) ...], bcnt[4 i + w] of them.
+    uint32_t *blist;            // [4 cap_pairs]
+    int32_t *bcnt;              // [max_items][4]
     int L;
     int max_items;
 };

@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(const uint32_t *__restrict__
                                                     const gs_status *st)
 {
     for (int i = threadIdx.x; i < max_items; i += blockDim.x) fix[i] = 0;
-    if (threadIdx.x < 4) counters[threadIdx.x] = 0;
+    if (threadIdx.x < 8) counters[threadIdx.x] = 0;
     __shared__ int s_warp[32];
     __shared__ long long s_carry;
     if (threadIdx.x == 0) s_carry = 0;
@@ -145,6 +145,57 @@ __device__ __forceinline__ void count_add(unsigned long long *n_eval, unsigned l
     }
 }
 
+// Block lists of the items of tiles cut into several chunks (persistent
+// warps, one item at a time): the item's list is read once, each splat's
+// alpha box tested against the four 16x4 blocks of the tile (the test of
+// warp_stage, so a block's list holds exactly the splats its walk would
+// stage), and the hits appended to the blocks' lists in list order.  The
+// compositing walks of those items then read only their block's list instead
+// of the whole chunk, four times over.
+__global__ void __launch_bounds__(kRThreads) block_lists_kernel(const float4 *__restrict__ rec,
+                                                                const uint32_t *__restrict__ vals,
+                                                                const uint32_t *__restrict__ ranges, ViewTable vt,
+                                                                RenderPlan plan, long long cap_cand,
+                                                                const gs_status *st)
+{
+    if (has_error(st)) return;
+    const int lane = threadIdx.x & 31;
+    unsigned lt;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+    const int n_items = __ldg(plan.item_base + vt.total_tiles);
+    int32_t *counter = plan.counters + 4;
+    for (int b = next_unit(counter); b < n_items; b = next_unit(counter)) {
+        Item it;
+        if (!item_of(b, plan.item_base, vt.total_tiles, ranges, plan.L, &it) || it.nk <= 1) continue;
+        const TileCoord tc = tile_coord(vt, it.t, 0);
+        const uint32_t n = it.s1 - it.s0;
+        uint32_t *bl = plan.blist + 4ull * it.s0;
+        int cnt[4] = {0, 0, 0, 0};
+        for (uint32_t b0 = it.s0; b0 < it.s1; b0 += 32) {
+            const uint32_t pos = b0 + lane;
+            bool hit[4] = {false, false, false, false};
+            if (pos < it.s1) {
+                uint32_t id = vals[pos];
+                if (!idx_ok(st, (long long)id, cap_cand, 44)) id = 0;
+                const float4 a = __ldg(&rec[3 * (size_t)id]);
+                const float4 bb = __ldg(&rec[3 * (size_t)id + 1]);
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    const BlockRect r = block_rect(tc, w);
+                    hit[w] = meets_block(a, bb, r.x0, r.x1, r.y0, r.y1);
+                }
+            }
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                const unsigned m = __ballot_sync(0xffffffffu, hit[w]);
+                if (hit[w]) bl[w * n + cnt[w] + __popc(m & lt)] = pos - it.s0;
+                cnt[w] += __popc(m);
+            }
+        }
+        if (lane < 4) plan.bcnt[4 * b + lane] = lane == 0 ? cnt[0] : (lane == 1 ? cnt[1] : (lane == 2 ? cnt[2] : cnt[3]));
+    }
+}
+
 // Compositing of one work item (FIX: the fix-up pass over marked chunks).
 // Each warp walks only the staged splats whose alpha box meets its pixel
 // block.  With COUNT, the pairs the method examines (every list position up to
@@ -185,11 +236,16 @@ __device__ __forceinline__ void chunk_unit(const float4 *__restrict__ rec, const
         if (!p1.done) p1.T = tp[lp.pid0 + 8];
     }
     const bool act0 = !p0.done, act1 = !p1.done;
-    // the warp walks the item's list on its own, 32 positions at a time
-    for (uint32_t b0 = it.s0; b0 < it.s1; b0 += 32) {
+    // the warp walks the item's list on its own, 32 entries at a time: every position of a
+    // single-chunk tile's list, or its block's list in a tile cut into several chunks
+    const uint32_t *bl = plan.blist + 4ull * it.s0 + (size_t)warp * (it.s1 - it.s0);
+    const uint32_t n_walk = multi ? (uint32_t)plan.bcnt[4 * b + warp] : it.s1 - it.s0;
+    for (uint32_t j0 = 0; j0 < n_walk; j0 += 32) {
         if (__all_sync(0xffffffffu, p0.done && p1.done)) break;
-        const uint32_t pos = b0 + lane;
-        const int cnt = warp_stage<true>(W, rec, vals, pos, it.s0, pos < it.s1, cap_cand, st, 42, bx0, bx1,
+        const uint32_t j = j0 + lane;
+        const bool valid = j < n_walk;
+        const uint32_t pos = it.s0 + (multi ? (valid ? bl[j] : 0u) : j);
+        const int cnt = warp_stage<true>(W, rec, vals, pos, it.s0, valid, cap_cand, st, 42, bx0, bx1,
                                                  by0, by1);
         if (exact) {
             for (int e = 0; e < cnt; ++e) {
@@ -448,11 +504,13 @@ size_t render_workspace_bytes(const ViewTable &vt, long long cap_pairs, int L)
     const long long items = render_max_items(vt, cap_pairs, L);
     return align_up(sizeof(int32_t) * ((size_t)vt.total_tiles + 1), 256) + 256 +
            2 * align_up(sizeof(int32_t) * (size_t)items, 256) +
-           align_up(sizeof(float) * (size_t)items * kStateWords * kRT, 256);
+           align_up(sizeof(float) * (size_t)items * kStateWords * kRT, 256) +
+           align_up(sizeof(int32_t) * 4 * (size_t)items, 256) +
+           align_up(sizeof(uint32_t) * 4 * (size_t)std::max<long long>(cap_pairs, 1), 256);
 }
 
-// Workspace: item_base [T + 1] | counters [4] | fix flags [max_items] | fix list [max_items] |
-// state [max_items][kStateWords][256]
+// Workspace: item_base [T + 1] | counters [8] | fix flags [max_items] | fix list [max_items] |
+// state [max_items][kStateWords][256] | block-list counts [max_items][4] | block lists [4 cap_pairs]
 RenderPlan render_plan(const ViewTable &vt, long long cap_pairs, int L, void *ws)
 {
     RenderPlan p;
@@ -462,11 +520,15 @@ RenderPlan render_plan(const ViewTable &vt, long long cap_pairs, int L, void *ws
     const size_t o0 = align_up(sizeof(int32_t) * ((size_t)vt.total_tiles + 1), 256);
     const size_t o1 = o0 + 256;
     const size_t o2 = o1 + 2 * align_up(sizeof(int32_t) * (size_t)p.max_items, 256);
+    const size_t o3 = o2 + align_up(sizeof(float) * (size_t)p.max_items * kStateWords * kRT, 256);
+    const size_t o4 = o3 + align_up(sizeof(int32_t) * 4 * (size_t)p.max_items, 256);
     p.item_base = reinterpret_cast<int32_t *>(w);
     p.counters = reinterpret_cast<int32_t *>(w + o0);
     p.fix = reinterpret_cast<int32_t *>(w + o1);
     p.fix_list = reinterpret_cast<int32_t *>(w + o1 + align_up(sizeof(int32_t) * (size_t)p.max_items, 256));
     p.state = reinterpret_cast<float *>(w + o2);
+    p.bcnt = reinterpret_cast<int32_t *>(w + o3);
+    p.blist = reinterpret_cast<uint32_t *>(w + o4);
     return p;
 }
 
@@ -494,6 +556,8 @@ int launch_render_fwd(const gs_splats *sp, const gs_bins *bins, const ViewTable 
     const RenderPlan plan = render_plan(vt, bins->cap_pairs, L, ws);
     plan_kernel<<<1, 1024, 0, s>>>(bins->ranges, vt.total_tiles, L, plan.max_items,
                                    const_cast<int32_t *>(plan.item_base), plan.fix, plan.counters, st);
+    block_lists_kernel<<<persistent_grid((const void *)block_lists_kernel), kRThreads, 0, s>>>(
+        rec, bins->vals, bins->ranges, vt, plan, sp->cap, st);
     if (n_eval) {
         cudaMemsetAsync(n_eval, 0, 4 * sizeof(long long), s);
         launch_items<true>(rec, bins, vt, plan, bg, image, T_final, last,
@@ -501,7 +565,7 @@ int launch_render_fwd(const gs_splats *sp, const gs_bins *bins, const ViewTable 
     } else {
         launch_items<false>(rec, bins, vt, plan, bg, image, T_final, last, nullptr, sp->cap, st, s);
     }
-    count_launches(4);
+    count_launches(5);
     return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 
