@@ -325,10 +325,11 @@ constexpr int kRowTile = 128;
 
 // The splat gradients [C][9] of the candidates rearranged in row tiles,
 // out[((t k + i) 9 + v) 128 + r] = sgrad[9 ((128 t + r) k + i) + v] for the
-// candidates that cover a tile and zero for the others and for rows past the
-// row count: in that layout the reverse decoder, one thread per row, reads
-// each value with one coalesced load per warp.  A block stages one tile's
-// contiguous gradients (128 k 9 floats) and tile counts in shared memory.
+// candidates that cover a tile and zero for the others: in that layout the
+// reverse decoder, one thread per row, reads each value with one coalesced
+// load per warp.  One thread per row here too: it reads its row's 9 k
+// contiguous values (8-byte loads where aligned) and writes each to its
+// plane, where the warp's 32 consecutive rows make one coalesced store.
 __global__ void __launch_bounds__(256) sgrad_row_tiles(const float *__restrict__ sgrad,
                                                        const int32_t *__restrict__ tiles,
                                                        const int32_t *__restrict__ view_start, int V, int k,
@@ -336,30 +337,37 @@ __global__ void __launch_bounds__(256) sgrad_row_tiles(const float *__restrict__
                                                        const gs_status *st)
 {
     if (has_error(st)) return;
-    extern __shared__ __align__(16) float s_g[];   // [128 k 9] gradients, then [128 k] tile counts
-    int32_t *s_t = reinterpret_cast<int32_t *>(s_g + (size_t)kRowTile * k * 9);
     const long long rows = std::min<long long>(__ldg(view_start + V), cap_rows);
-    const long long ntiles = (rows + kRowTile - 1) / kRowTile;
-    const int per = kRowTile * k;   // candidates per tile
-    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const long long c0 = t * per;
-        const int nc = (int)std::min<long long>(per, rows * k - c0);   // candidates of this tile below the row count
-        const float *src = sgrad + 9 * c0;
-        if ((reinterpret_cast<uintptr_t>(src) & 15) == 0 && (nc * 9) % 4 == 0) {
-            for (int i = threadIdx.x; i < nc * 9 / 4; i += blockDim.x)
-                reinterpret_cast<float4 *>(s_g)[i] = __ldg(reinterpret_cast<const float4 *>(src) + i);
-        } else {
-            for (int i = threadIdx.x; i < nc * 9; i += blockDim.x) s_g[i] = __ldg(src + i);
+    const bool pairs = ((9 * k) & 1) == 0 && (reinterpret_cast<uintptr_t>(sgrad) & 7) == 0;
+    for (long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x; row < rows;
+         row += (long long)gridDim.x * blockDim.x) {
+        const long long t = row / kRowTile;
+        const int r = (int)(row - t * kRowTile);
+        const float *src = sgrad + 9 * (size_t)k * row;
+        float *dst = out + (size_t)t * k * 9 * kRowTile + r;
+        for (int i = 0; i < k; ++i) {
+            const bool drawn = __ldg(tiles + (size_t)k * row + i) > 0;
+            float v[10];
+            if (pairs) {   // 9 values from 8-byte pieces: candidate i starts at an even or odd float
+                const int f0 = 9 * i, e0 = f0 & ~1;
+                const float2 *p2 = reinterpret_cast<const float2 *>(src + e0);
+#pragma unroll
+                for (int j = 0; j < 5; ++j) {
+                    const float2 q = __ldg(p2 + j);
+                    v[2 * j] = q.x;
+                    v[2 * j + 1] = q.y;
+                }
+                if (f0 & 1) {
+#pragma unroll
+                    for (int j = 0; j < 9; ++j) v[j] = v[j + 1];
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 9; ++j) v[j] = __ldg(src + 9 * i + j);
+            }
+#pragma unroll
+            for (int j = 0; j < 9; ++j) dst[((size_t)i * 9 + j) * kRowTile] = drawn ? v[j] : 0.f;
         }
-        for (int i = threadIdx.x; i < per; i += blockDim.x) s_t[i] = i < nc ? __ldg(tiles + c0 + i) : 0;
-        __syncthreads();
-        float *dst = out + (size_t)t * per * 9;
-        for (int o = threadIdx.x; o < per * 9; o += blockDim.x) {
-            const int r = o % kRowTile, q = o / kRowTile;   // q = 9 i + v
-            const int c = r * k + q / 9;
-            dst[o] = s_t[c] > 0 ? s_g[9 * c + q % 9] : 0.f;
-        }
-        __syncthreads();
     }
 }
 
@@ -381,18 +389,9 @@ int launch_decode_project_bwd(const gs_anchors *A, const gs_camera *cams, const 
     if (precision == GS_PREC_BF16) {
         // the splat gradients in row tiles (workspace), then the fused reverse
         float *sgT = reinterpret_cast<float *>(ws);
-        const size_t smem = sizeof(float) * 10 * (size_t)kRowTile * g->k;
-        static size_t configured = 0;
-        if (smem > 48 * 1024 && smem > configured) {
-            if (cudaFuncSetAttribute(sgrad_row_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-                cudaSuccess)
-                return GS_ERR_UNSUPPORTED;
-            configured = smem;
-        }
-        const long long tiles = std::max<long long>((g->cap_rows + kRowTile - 1) / kRowTile, 1);
-        const int grid = (int)std::min<long long>(tiles, (long long)sm_count() * 4);
-        sgrad_row_tiles<<<grid, 256, smem, s>>>(sgrad->g, sp->tiles, g->view_start, vt.V, g->k, g->cap_rows, sgT,
-                                                st);
+        const int grid = (int)std::max<long long>(
+            1, std::min<long long>((g->cap_rows + 255) / 256, (long long)sm_count() * 8));
+        sgrad_row_tiles<<<grid, 256, 0, s>>>(sgrad->g, sp->tiles, g->view_start, vt.V, g->k, g->cap_rows, sgT, st);
         count_launches(1);
         return launch_decode_bwd_impl(A, cams, vt, precision, g, nullptr, sp, sgT, out, st, s);
     }

@@ -211,7 +211,7 @@ __device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const u
                                          int warp, WarpStage &WSw)
 {
     Item it;
-    if (!item_of(b, plan.item_base, vt.total_tiles, ranges, plan.L, &it)) return;
+    if (!item_of(b, plan.item_base, plan.item_tile, vt.total_tiles, ranges, plan.L, &it)) return;
     const int lane = threadIdx.x & 31, tid = warp * 32 + lane;
     const TileCoord tc = tile_coord(vt, it.t, tid);
     const int v = tc.v;

@@ -109,16 +109,14 @@ struct Item {
     uint32_t s0, s1;  // this chunk's list range
 };
 
-// Item of block b; returns false when b is past the last item.
-__device__ __forceinline__ bool item_of(int b, const int32_t *__restrict__ item_base, int T,
+// Item b (its tile from the plan's item -> tile table); returns false when b
+// is past the last item.
+__device__ __forceinline__ bool item_of(int b, const int32_t *__restrict__ item_base,
+                                        const int32_t *__restrict__ item_tile, int T,
                                         const uint32_t *__restrict__ ranges, int L, Item *it)
 {
     if (b >= __ldg(item_base + T)) return false;
-    int lo = 0, hi = T - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(item_base + mid) <= b) lo = mid; else hi = mid - 1;
-    }
+    const int lo = __ldg(item_tile + b);
     it->t = lo;
     it->base = __ldg(item_base + lo);
     it->k = b - it->base;
@@ -248,6 +246,7 @@ struct RenderPlan {
     // blist[4 s0 + w (s1 - s0) ...], bcnt[4 i + w] of them.
     uint32_t *blist;            // [4 cap_pairs]
     int32_t *bcnt;              // [max_items][4]
+    int32_t *item_tile;         // [max_items] tile of each item
     int L;
     int max_items;
 };

@@ -76,6 +76,18 @@ __global__ void __launch_bounds__(1024) plan_kernel(const uint32_t *__restrict__
     }
 }
 
+// The tile of every item (one thread per tile writes its items' entries), so
+// that a work unit finds its tile without a search.
+__global__ void __launch_bounds__(256) item_tiles_kernel(const int32_t *__restrict__ item_base, int T,
+                                                         int max_items, int32_t *__restrict__ item_tile)
+{
+    const int n = min(item_base[T], max_items);   // 0 when the plan overflowed (no item runs)
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
+        const int b0 = item_base[t], b1 = t + 1 < T ? min(item_base[t + 1], n) : n;
+        for (int b = max(b0, 0); b < b1; ++b) item_tile[b] = t;
+    }
+}
+
 // Front-to-back state of one pixel.
 struct PixFwd {
     float T, C0, C1, C2;
@@ -166,30 +178,38 @@ __global__ void __launch_bounds__(kRThreads) block_lists_kernel(const float4 *__
     int32_t *counter = plan.counters + 4;
     for (int b = next_unit(counter); b < n_items; b = next_unit(counter)) {
         Item it;
-        if (!item_of(b, plan.item_base, vt.total_tiles, ranges, plan.L, &it) || it.nk <= 1) continue;
+        if (!item_of(b, plan.item_base, plan.item_tile, vt.total_tiles, ranges, plan.L, &it) || it.nk <= 1) continue;
         const TileCoord tc = tile_coord(vt, it.t, 0);
         const uint32_t n = it.s1 - it.s0;
         uint32_t *bl = plan.blist + 4ull * it.s0;
         int cnt[4] = {0, 0, 0, 0};
-        for (uint32_t b0 = it.s0; b0 < it.s1; b0 += 32) {
-            const uint32_t pos = b0 + lane;
-            bool hit[4] = {false, false, false, false};
-            if (pos < it.s1) {
-                uint32_t id = vals[pos];
-                if (!idx_ok(st, (long long)id, cap_cand, 44)) id = 0;
-                const float4 a = __ldg(&rec[3 * (size_t)id]);
-                const float4 bb = __ldg(&rec[3 * (size_t)id + 1]);
+        constexpr int kAhead = 4;   // 32-position batches whose loads are issued together
+        for (uint32_t b0 = it.s0; b0 < it.s1; b0 += 32 * kAhead) {
+            uint32_t id[kAhead];
+            float4 a[kAhead], bb[kAhead];
+#pragma unroll
+            for (int u = 0; u < kAhead; ++u) {
+                const uint32_t pos = b0 + 32 * u + lane;
+                id[u] = pos < it.s1 ? vals[pos] : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < kAhead; ++u) {
+                const uint32_t pos = b0 + 32 * u + lane;
+                if (pos < it.s1 && !idx_ok(st, (long long)id[u], cap_cand, 44)) id[u] = 0;
+                a[u] = pos < it.s1 ? __ldg(&rec[3 * (size_t)id[u]]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                bb[u] = pos < it.s1 ? __ldg(&rec[3 * (size_t)id[u] + 1]) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < kAhead; ++u) {
+                const uint32_t pos = b0 + 32 * u + lane;
 #pragma unroll
                 for (int w = 0; w < 4; ++w) {
                     const BlockRect r = block_rect(tc, w);
-                    hit[w] = meets_block(a, bb, r.x0, r.x1, r.y0, r.y1);
+                    const bool hit = pos < it.s1 && meets_block(a[u], bb[u], r.x0, r.x1, r.y0, r.y1);
+                    const unsigned m = __ballot_sync(0xffffffffu, hit);
+                    if (hit) bl[w * n + cnt[w] + __popc(m & lt)] = pos - it.s0;
+                    cnt[w] += __popc(m);
                 }
-            }
-#pragma unroll
-            for (int w = 0; w < 4; ++w) {
-                const unsigned m = __ballot_sync(0xffffffffu, hit[w]);
-                if (hit[w]) bl[w * n + cnt[w] + __popc(m & lt)] = pos - it.s0;
-                cnt[w] += __popc(m);
             }
         }
         if (lane < 4) plan.bcnt[4 * b + lane] = lane == 0 ? cnt[0] : (lane == 1 ? cnt[1] : (lane == 2 ? cnt[2] : cnt[3]));
@@ -211,7 +231,7 @@ __device__ __forceinline__ void chunk_unit(const float4 *__restrict__ rec, const
 {
     if (FIX && plan.fix[b] == 0) return;
     Item it;
-    if (!item_of(b, plan.item_base, vt.total_tiles, ranges, plan.L, &it)) return;
+    if (!item_of(b, plan.item_base, plan.item_tile, vt.total_tiles, ranges, plan.L, &it)) return;
     const int lane = threadIdx.x & 31, tid = warp * 32 + lane;
     const TileCoord tc = tile_coord(vt, it.t, tid);
     const LanePix lp = lane_pixels(tc, warp, lane, vt.W[tc.v], vt.H[tc.v]);
@@ -505,12 +525,13 @@ size_t render_workspace_bytes(const ViewTable &vt, long long cap_pairs, int L)
     return align_up(sizeof(int32_t) * ((size_t)vt.total_tiles + 1), 256) + 256 +
            2 * align_up(sizeof(int32_t) * (size_t)items, 256) +
            align_up(sizeof(float) * (size_t)items * kStateWords * kRT, 256) +
-           align_up(sizeof(int32_t) * 4 * (size_t)items, 256) +
+           align_up(sizeof(int32_t) * 4 * (size_t)items, 256) + align_up(sizeof(int32_t) * (size_t)items, 256) +
            align_up(sizeof(uint32_t) * 4 * (size_t)std::max<long long>(cap_pairs, 1), 256);
 }
 
 // Workspace: item_base [T + 1] | counters [8] | fix flags [max_items] | fix list [max_items] |
-// state [max_items][kStateWords][256] | block-list counts [max_items][4] | block lists [4 cap_pairs]
+// state [max_items][kStateWords][256] | block-list counts [max_items][4] | item tiles [max_items] |
+// block lists [4 cap_pairs]
 RenderPlan render_plan(const ViewTable &vt, long long cap_pairs, int L, void *ws)
 {
     RenderPlan p;
@@ -521,13 +542,15 @@ RenderPlan render_plan(const ViewTable &vt, long long cap_pairs, int L, void *ws
     const size_t o1 = o0 + 256;
     const size_t o2 = o1 + 2 * align_up(sizeof(int32_t) * (size_t)p.max_items, 256);
     const size_t o3 = o2 + align_up(sizeof(float) * (size_t)p.max_items * kStateWords * kRT, 256);
-    const size_t o4 = o3 + align_up(sizeof(int32_t) * 4 * (size_t)p.max_items, 256);
+    const size_t o35 = o3 + align_up(sizeof(int32_t) * 4 * (size_t)p.max_items, 256);
+    const size_t o4 = o35 + align_up(sizeof(int32_t) * (size_t)p.max_items, 256);
     p.item_base = reinterpret_cast<int32_t *>(w);
     p.counters = reinterpret_cast<int32_t *>(w + o0);
     p.fix = reinterpret_cast<int32_t *>(w + o1);
     p.fix_list = reinterpret_cast<int32_t *>(w + o1 + align_up(sizeof(int32_t) * (size_t)p.max_items, 256));
     p.state = reinterpret_cast<float *>(w + o2);
     p.bcnt = reinterpret_cast<int32_t *>(w + o3);
+    p.item_tile = reinterpret_cast<int32_t *>(w + o35);
     p.blist = reinterpret_cast<uint32_t *>(w + o4);
     return p;
 }
@@ -556,6 +579,8 @@ int launch_render_fwd(const gs_splats *sp, const gs_bins *bins, const ViewTable 
     const RenderPlan plan = render_plan(vt, bins->cap_pairs, L, ws);
     plan_kernel<<<1, 1024, 0, s>>>(bins->ranges, vt.total_tiles, L, plan.max_items,
                                    const_cast<int32_t *>(plan.item_base), plan.fix, plan.counters, st);
+    item_tiles_kernel<<<(int)std::max<long long>(1, std::min<long long>((vt.total_tiles + 255) / 256, (long long)sm_count() * 4)),
+                        256, 0, s>>>(plan.item_base, vt.total_tiles, plan.max_items, plan.item_tile);
     block_lists_kernel<<<persistent_grid((const void *)block_lists_kernel), kRThreads, 0, s>>>(
         rec, bins->vals, bins->ranges, vt, plan, sp->cap, st);
     if (n_eval) {
@@ -565,7 +590,7 @@ int launch_render_fwd(const gs_splats *sp, const gs_bins *bins, const ViewTable 
     } else {
         launch_items<false>(rec, bins, vt, plan, bg, image, T_final, last, nullptr, sp->cap, st, s);
     }
-    count_launches(5);
+    count_launches(6);
     return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 
