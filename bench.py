@@ -518,7 +518,8 @@ def run_ours(args, rank, world, dist):
 
     stages = {n: statistics.mean(v) for n, v in stage_ms.items()}
     dom = max((n for n in names if n != "l1"), key=lambda n: stages[n])
-    roof = roofline(dom, stages[dom], counts, n_pairs, n_rows, rp, scene, measured_peaks())
+    roof = roofline(dom, stages[dom], counts, n_pairs, n_rows, rp, scene, measured_peaks(),
+                    fp32_decode=prec != L.GS_PREC_BF16)
     if roof.get("bound") == "alu":
         roof["peak_measured"] = api.probe_peak(0) / 1e12   # FP32 FMA issue rate of this device
         roof["sfu_ex2_peak_measured"] = api.probe_peak(1) / 1e12
@@ -563,7 +564,7 @@ def profiled_traffic(kernel_file, sources):
     return traffic
 
 
-def roofline(dom, ms, counts, n_pairs, n_rows, rp, scene, peaks):
+def roofline(dom, ms, counts, n_pairs, n_rows, rp, scene, peaks, fp32_decode=False):
     hbm = peaks.get("hbm_gbs", 6400.0)
     alu_peak = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12   # T FP32 lane ops/s (nominal)
     ex, comp, rev = counts["examined"], counts["composited"], counts["reverse_examined"]
@@ -603,6 +604,10 @@ def roofline(dom, ms, counts, n_pairs, n_rows, rp, scene, peaks):
                 "frac": a / hbm, "traffic": None, "work_per_launch": f"{C_} candidates x {per} B"}
     flops = n_rows * 13952 * (1 if dom == "decode_project" else 2)
     a = flops / (ms * 1e-3) / 1e12
+    if fp32_decode:   # the SIMT FP32 decoders: FP32 lane peak
+        return {"kernel": dom, "bound": "alu", "achieved": a, "peak": alu_peak, "unit": "T FP32 ops/s",
+                "frac": a / alu_peak, "traffic": None,
+                "work_per_launch": f"{n_rows} anchor-view rows x 13,952 FLOP per decode"}
     pk = peaks.get("bf16_tflops_sustained", 1400.0)
     return {"kernel": dom, "bound": "tensor", "achieved": a, "peak": pk, "unit": "TFLOP/s",
             "frac": a / pk, "traffic": None, "work_per_launch": f"{n_rows} anchor-view rows"}
