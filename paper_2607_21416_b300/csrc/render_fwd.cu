@@ -501,16 +501,28 @@ __global__ void __launch_bounds__(256) l1_kernel(const float *__restrict__ image
 {
     const long long n = 3 * vt.total_pixels;
     float acc = 0.f;
+    // a thread's elements increase, so its view (and the view's 1 / (3 pixels)) is carried along
+    int v = 0;
+    float inv = 1.f / (float)(3 * vt.pix_base[1]);
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        int v = 0;
-        while (v + 1 < vt.V && 3 * vt.pix_base[v + 1] <= i) ++v;
-        const float inv = 1.f / (float)(3 * vt.pix_base[v + 1] - 3 * vt.pix_base[v]);
+        if (v + 1 < vt.V && 3 * vt.pix_base[v + 1] <= i) {
+            while (v + 1 < vt.V && 3 * vt.pix_base[v + 1] <= i) ++v;
+            inv = 1.f / (float)(3 * vt.pix_base[v + 1] - 3 * vt.pix_base[v]);
+        }
         const float d = image[i] - target[i];
         acc += fabsf(d) * inv;
         d_image[i] = d > 0.f ? inv : (d < 0.f ? -inv : 0.f);
     }
+    // block sum, then one atomic per block (one per warp contended on a single address)
+    __shared__ float s_w[8];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = threadIdx.x < (blockDim.x >> 5) ? s_w[threadIdx.x] : 0.f;
+        for (int o = 4; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) atomicAdd(loss, acc);
+    }
 }
 
 // ------------------------------------------------------------ launchers
