@@ -247,11 +247,11 @@ def run_ours(args, rank, world, dist):
         api.l1_loss(rp.image, target, views, rp.loss, rp.d_image)
         ev[4].record()
         api.render_bwd(rp.g, rp.splats, rp.bins, views, rp.image, rp.d_image, rp.sgrad, None, rp.status,
-                       rp.render_ws, rp.chunk, rp.last)
+                       rp.render_ws, rp.chunk, rp.last, None, rp.sgrad_layout)
         ev[5].record()
         if anchors is not None:
             api.decode_project_bwd(anchors, views, rp.g, rp.splats, rp.sgrad, rp.agrad, rp.dpbwd_ws, rp.status,
-                                   prec)
+                                   prec, None, rp.sgrad_layout)
         else:
             if rp.ggrad is None:
                 rp.ggrad = api.Gauss3DGrad.like(rp.g)
@@ -396,10 +396,16 @@ def run_ours(args, rank, world, dist):
             return statistics.mean(ts)
 
         adam_ms = timed(opt.step)
+        sg_c = rp.sgrad
         if not rp.gaussians_written:   # the timed step kept no 3D Gaussians: decode them (untimed)
             api.decode(anchors, views, rp.g, rp.dec_ws, rp.status, prec)
             torch.cuda.synchronize()
-        stats_ms = timed(lambda: api.densify_stats(rp.g, rp.views, rp.splats, rp.sgrad, stats.N, stats.grad_accum,
+        if rp.sgrad_layout != L.GS_SGRAD_CANDIDATE:   # the statistics read candidate-major splat gradients
+            sg_c = api.splat_grad_alloc(rp.g)
+            api.render_bwd(rp.g, rp.splats, rp.bins, views, rp.image, rp.d_image, sg_c, None, rp.status,
+                           rp.render_ws, rp.chunk, rp.last)
+            torch.cuda.synchronize()
+        stats_ms = timed(lambda: api.densify_stats(rp.g, rp.views, rp.splats, sg_c, stats.N, stats.grad_accum,
                                                    stats.offset_denom, stats.opacity_accum, stats.anchor_denom,
                                                    rp.status))
         hbm, hbm_of = hbm_peak()

@@ -148,11 +148,22 @@ typedef struct gs_splats {
     int32_t *tiles;   /* [C] */
 } gs_splats;
 
-/* Per-splat gradients of the rendering (view space), candidate-indexed:
- * float[9] = d mean_x, d mean_y, d conic_a, d conic_b, d conic_c, d opacity,
- * d r, d g, d b. */
+/* Per-splat gradients of the rendering (view space), nine per candidate:
+ * d mean_x, d mean_y, d conic_a, d conic_b, d conic_c, d opacity, d r, d g,
+ * d b.  Two layouts:
+ *   GS_SGRAD_CANDIDATE  g[9 c + v] for candidate c = row k + i ([C][9]);
+ *   GS_SGRAD_ROW_TILES  g[((t k + i) 9 + v) 128 + r] for row 128 t + r: rows
+ *                       in tiles of 128, each value of a tile's rows
+ *                       contiguous (what the tensor-core reverse decoder reads
+ *                       one row per thread); g holds ceil(cap_rows / 128) 128
+ *                       k 9 floats.
+ * gs_render_bwd writes either (with out = NULL); gs_decode_project_bwd at
+ * GS_PREC_BF16 reads either; every other reader takes GS_SGRAD_CANDIDATE. */
+#define GS_SGRAD_CANDIDATE 0
+#define GS_SGRAD_ROW_TILES 1
 typedef struct gs_splat_grad {
-    float *g;         /* [C][9] */
+    float *g;
+    int32_t layout;   /* GS_SGRAD_* */
 } gs_splat_grad;
 
 /* Sorted binning of splats into tiles. */
@@ -469,9 +480,11 @@ int gs_flow_triangulate(const gs_camera *cam1, const gs_camera *cam2, int32_t wi
  * to decide the stop rule again.  chunk and ws must be those of the forward,
  * ws untouched since: tiles cut into several chunks start each chunk from
  * the transmittance and colour prefix the forward left there.  sgrad:
- * per-splat view-space gradients, overwritten for every candidate up to the
- * row count (zeros for the ones that cover no tile).  out: NULL, or
- * overwritten for every candidate (zeros for culled ones). */
+ * per-splat view-space gradients in either layout, overwritten for every
+ * candidate up to the row count (zeros for the ones that cover no tile; in
+ * the row-tiled layout the whole last tile of rows).  out: NULL, or
+ * overwritten for every candidate (zeros for culled ones); it needs
+ * GS_SGRAD_CANDIDATE. */
 int gs_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *sp,
                   const gs_bins *bins, const gs_view *views, int32_t V, int32_t chunk, void *ws,
                   size_t ws_bytes, const float *image, const float *d_image, const int32_t *last,
@@ -483,7 +496,7 @@ int gs_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *s
  * derivative (on the compensated covariance) for near-degenerate splats as in
  * gs_project; d opacity and d colour pass through.  Candidates with
  * sp->tiles == 0 get zeros.  out is overwritten for every candidate up to the
- * row count. */
+ * row count.  sgrad: GS_SGRAD_CANDIDATE. */
 int gs_project_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *sp, const gs_view *views,
                    int32_t V, const gs_splat_grad *sgrad, gs_gauss3d_grad *out, gs_status *status,
                    void *stream);
@@ -504,13 +517,13 @@ int gs_decode_bwd(const gs_anchors *A, const gs_camera *cams, const gs_view *vie
  * applies the projection's chain rule (the near-degenerate branch included)
  * to each candidate it recomputes -- mean x_a + offset exp(l[0:3]), scale
  * exp(l[3:6]) sigmoid, unit quaternion, evaluated with the reverse pass's
- * recomputed decoder activations; its workspace holds the splat gradients
- * rearranged in tiles of 128 rows (9 k floats per row), so that the decoder's
- * one-thread-per-row reads are coalesced.  With GS_PREC_FP32 the two steps
- * run one after the other through the workspace.  Workspace:
- * gs_decode_project_bwd_workspace bytes, 256-byte aligned.  sp->tiles marks
- * the candidates that cover a tile (the others get no gradient).  out is
- * overwritten. */
+ * recomputed decoder activations, reading the splat gradients one row per
+ * thread: GS_SGRAD_ROW_TILES directly (no workspace needed: ws may be NULL),
+ * GS_SGRAD_CANDIDATE after rearranging them in the workspace.  With
+ * GS_PREC_FP32 (GS_SGRAD_CANDIDATE only) the two steps run one after the
+ * other through the workspace.  Workspace: gs_decode_project_bwd_workspace
+ * bytes, 256-byte aligned.  sp->tiles marks the candidates that cover a tile
+ * (the others get no gradient).  out is overwritten. */
 size_t gs_decode_project_bwd_workspace(int32_t k, int64_t cap_rows, int32_t precision);
 int gs_decode_project_bwd(const gs_anchors *A, const gs_camera *cams, const gs_view *views, int32_t V,
                           int32_t precision, const gs_gauss3d *g, const gs_splats *sp,

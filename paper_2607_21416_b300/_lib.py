@@ -52,7 +52,11 @@ class gs_splats(C.Structure):
 
 
 class gs_splat_grad(C.Structure):
-    _fields_ = [("g", vp)]
+    _fields_ = [("g", vp), ("layout", i32)]
+
+
+GS_SGRAD_CANDIDATE = 0
+GS_SGRAD_ROW_TILES = 1
 
 
 class gs_bins(C.Structure):

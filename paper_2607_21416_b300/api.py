@@ -395,14 +395,21 @@ def flow_triangulate(cams, wh, flow, samples, tau, kept, points, n_kept, ws, sta
                                                            _stream(stream)))
 
 
+def splat_grad_alloc(g: Gauss3D, layout=L.GS_SGRAD_CANDIDATE, device="cuda"):
+    """Splat-gradient buffer for g's capacity: [C][9] candidate-major, or in
+    row tiles of 128 (GS_SGRAD_ROW_TILES: the whole last tile)."""
+    rows = g.cap_rows if layout == L.GS_SGRAD_CANDIDATE else (g.cap_rows + 127) // 128 * 128
+    return torch.zeros(max(rows * g.k, 1), 9, device=device)
+
+
 def render_bwd(g: Gauss3D, sp: Splats, bins: Bins, views: Views, image, d_image, sgrad, out: Gauss3DGrad,
-               status, ws, chunk=0, last=None, stream=None):
+               status, ws, chunk=0, last=None, stream=None, sgrad_layout=L.GS_SGRAD_CANDIDATE):
     """Reverse of the compositing and (unless out is None) of the projection.
     image: the forward's output; last: its optional per-pixel last
-    composited position."""
+    composited position; sgrad_layout: GS_SGRAD_* of sgrad."""
     lib = L.load()
     gs_, s, b = g.struct(), sp.struct(), bins.struct()
-    sg = L.gs_splat_grad(sgrad.data_ptr())
+    sg = L.gs_splat_grad(sgrad.data_ptr(), sgrad_layout)
     o = C.byref(out.struct()) if out is not None else None
     L.check("gs_render_bwd", lib.gs_render_bwd(C.byref(gs_), _ptr(views.cams), C.byref(s), C.byref(b),
                                                views.ptr, views.V, chunk, _ptr(ws), ws.numel(), _ptr(image),
@@ -425,12 +432,13 @@ def decode_project_bwd_workspace(g: Gauss3D, precision=L.GS_PREC_FP32):
 
 
 def decode_project_bwd(anchors: Anchors, views: Views, g: Gauss3D, sp: Splats, sgrad, out: AnchorGrad, ws,
-                       status, precision=L.GS_PREC_FP32, stream=None):
+                       status, precision=L.GS_PREC_FP32, stream=None, sgrad_layout=L.GS_SGRAD_CANDIDATE):
     """Reverse of the projection and the decoders from render_bwd's splat
-    gradients (tensor-core path fused; FP32 path through ws)."""
+    gradients (tensor-core path fused; FP32 path through ws).  Row-tiled
+    splat gradients (tensor-core path only) need no workspace."""
     lib = L.load()
     a, gs_, s = anchors.struct(), g.struct(), sp.struct()
-    sg = L.gs_splat_grad(sgrad.data_ptr())
+    sg = L.gs_splat_grad(sgrad.data_ptr(), sgrad_layout)
     o = out.struct()
     L.check("gs_decode_project_bwd", lib.gs_decode_project_bwd(C.byref(a), _ptr(views.cams), views.ptr, views.V,
                                                                precision, C.byref(gs_), C.byref(s), C.byref(sg),

@@ -387,6 +387,8 @@ int launch_decode_project_bwd(const gs_anchors *A, const gs_camera *cams, const 
                               gs_anchor_grad *out, void *ws, gs_status *st, cudaStream_t s)
 {
     if (precision == GS_PREC_BF16) {
+        if (sgrad->layout == GS_SGRAD_ROW_TILES)   // already in row tiles: read in place
+            return launch_decode_bwd_impl(A, cams, vt, precision, g, nullptr, sp, sgrad->g, out, st, s);
         // the splat gradients in row tiles (workspace), then the fused reverse
         float *sgT = reinterpret_cast<float *>(ws);
         const int grid = (int)std::max<long long>(

@@ -340,8 +340,10 @@ int gs_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *s
     ViewTable vt;
     if (!check_gauss(g) || !cams || !sp || !sp->rec || !sp->tiles || !bins || !bins->vals || !bins->ranges ||
         !bins->n_pairs || !image || !d_image || !sgrad || !sgrad->g ||
-        (out && (!out->dmu || !out->dscale || !out->dquat || !out->dopacity || !out->dcolour)) || !status ||
-        !make_view_table(views, V, &vt) || sp->cap < g->cap_rows * (long long)g->k)
+        (sgrad->layout != GS_SGRAD_CANDIDATE && sgrad->layout != GS_SGRAD_ROW_TILES) ||
+        (out && (sgrad->layout != GS_SGRAD_CANDIDATE || !out->dmu || !out->dscale || !out->dquat || !out->dopacity ||
+                 !out->dcolour)) ||
+        !status || !make_view_table(views, V, &vt) || sp->cap < g->cap_rows * (long long)g->k)
         return GS_ERR_INVALID_ARG;
     if ((chunk != 0 && (chunk < 256 || chunk > (1 << 24))) || !ws ||
         (reinterpret_cast<uintptr_t>(ws) & 255) != 0 ||
@@ -355,9 +357,9 @@ int gs_project_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splats *
                    int32_t V, const gs_splat_grad *sgrad, gs_gauss3d_grad *out, gs_status *status, void *stream)
 {
     ViewTable vt;
-    if (!check_gauss(g) || !cams || !sp || !sp->tiles || !sgrad || !sgrad->g || !out || !out->dmu || !out->dscale ||
-        !out->dquat || !out->dopacity || !out->dcolour || !status || !make_view_table(views, V, &vt) ||
-        sp->cap < g->cap_rows * (long long)g->k)
+    if (!check_gauss(g) || !cams || !sp || !sp->tiles || !sgrad || !sgrad->g ||
+        sgrad->layout != GS_SGRAD_CANDIDATE || !out || !out->dmu || !out->dscale || !out->dquat || !out->dopacity ||
+        !out->dcolour || !status || !make_view_table(views, V, &vt) || sp->cap < g->cap_rows * (long long)g->k)
         return GS_ERR_INVALID_ARG;
     return launch_project_bwd(g, cams, sp, vt, sgrad, out, status, (cudaStream_t)stream);
 }
@@ -377,8 +379,12 @@ int gs_decode_project_bwd(const gs_anchors *A, const gs_camera *cams, const gs_v
         !status || !make_view_table(views, V, &vt) || g->k != A->k || sp->cap < g->cap_rows * (long long)g->k)
         return GS_ERR_INVALID_ARG;
     if (precision != GS_PREC_FP32 && precision != GS_PREC_BF16) return GS_ERR_INVALID_ARG;
-    if (ws_bytes < decode_project_bwd_workspace_bytes(g->k, g->cap_rows, precision) ||
-        (ws_bytes > 0 && (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0)))
+    if (sgrad->layout != GS_SGRAD_CANDIDATE &&
+        (sgrad->layout != GS_SGRAD_ROW_TILES || precision != GS_PREC_BF16))
+        return GS_ERR_INVALID_ARG;
+    const bool needs_ws = sgrad->layout == GS_SGRAD_CANDIDATE;   // the row-tiled gradients are read in place
+    if ((needs_ws && ws_bytes < decode_project_bwd_workspace_bytes(g->k, g->cap_rows, precision)) ||
+        (needs_ws && ws_bytes > 0 && (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0)))
         return GS_ERR_INVALID_ARG;
     return launch_decode_project_bwd(A, cams, vt, precision, g, sp, sgrad, out, ws, status, (cudaStream_t)stream);
 }

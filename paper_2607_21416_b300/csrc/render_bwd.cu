@@ -171,10 +171,36 @@ __device__ __forceinline__ float conic_grads(const LaneRole &r, float total, flo
     return fmaf(cs, total, co * other);
 }
 
+// Where the splat gradients go: candidate-major [C][9], or in row tiles
+// [tile of 128 rows][i < k][9][128] (GS_SGRAD_ROW_TILES).  The row of a
+// candidate id = row k + i comes from a multiply-high division by the
+// invariant k (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994, Fig. 4.1): t = umulhi(m, id), row = (t + ((id -
+// t) >> s1)) >> s2, with m, s1, s2 from the host.
+struct SgOut {
+    float *g;
+    int tiled;
+    uint32_t k, m, s1, s2;
+};
+__device__ __forceinline__ uint32_t sg_offset(const SgOut &o, uint32_t id)
+{
+    if (!o.tiled) return 9u * id;
+    const uint32_t t = __umulhi(o.m, id);
+    const uint32_t row = (t + ((id - t) >> o.s1)) >> o.s2, i = id - row * o.k;
+    return ((row >> 7) * o.k + i) * 9u * 128u + (row & 127u);
+}
+// The staged splats' ids become the offsets of their gradient entries.
+__device__ __forceinline__ void stage_offsets(WarpStage &W, int cnt, const SgOut &o)
+{
+    const int lane = threadIdx.x & 31;
+    if (lane < cnt) W.id[lane] = sg_offset(o, W.id[lane]);
+    __syncwarp();
+}
+
 // The 9 per-splat sums of a staged splat: reduced across the warp, turned
 // into the splat's gradient and added to its entry (one atomic per value).
 __device__ __forceinline__ void splat_sums_out(const float acc[9], const LaneRole &role, int vi, float4 a, float4 bb,
-                                               uint32_t id, float *__restrict__ sgrad)
+                                               uint32_t off, const SgOut &sg)
 {
     const int lane = threadIdx.x & 31;
     const float io = ex2_approx(-bb.y);   // 1 / opacity from the record's log2 opacity
@@ -182,9 +208,10 @@ __device__ __forceinline__ void splat_sums_out(const float acc[9], const LaneRol
     const float t9 = warp_sum(acc[8]);
     const float other = __shfl_xor_sync(0xffffffffu, t8, 4);
     const float g = conic_grads(role, t8, other, a, bb, io);
-    float *o = sgrad + 9 * (size_t)id;
-    if ((lane & 3) == 0) atomicAdd(o + vi, g);
-    if (lane == 1) atomicAdd(o + 8, t9);
+    float *o = sg.g + off;
+    const uint32_t stride = sg.tiled ? 128u : 1u;
+    if ((lane & 3) == 0) atomicAdd(o + stride * vi, g);
+    if (lane == 1) atomicAdd(o + stride * 8u, t9);
 }
 
 // Reverse pass of one work unit (block `warp` of item b).
@@ -207,7 +234,7 @@ __device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const u
                                          const uint32_t *__restrict__ ranges, const ViewTable &vt,
                                          const RenderPlan &plan, const float *__restrict__ image,
                                          const float *__restrict__ d_image, const int32_t *__restrict__ last_in,
-                                         float *__restrict__ sgrad, long long cap_cand, const gs_status *st, int b,
+                                         const SgOut &sg, long long cap_cand, const gs_status *st, int b,
                                          int warp, WarpStage &WSw)
 {
     Item it;
@@ -283,6 +310,7 @@ __device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const u
             const uint32_t pos = it.s0 + (jl >= 0 ? __ldg(bl + jl) : 0u);
             const int cnt = warp_stage<false>(WSw, rec, vals, pos, it.s0, jl >= 0,
                                                     cap_cand, st, 53, bx0, bx1, by0, by1);
+            stage_offsets(WSw, cnt, sg);
             for (int e = 0; e < cnt; ++e) {
                 const int p = WSw.pos[e];
                 const float4 a = WSw.a[e];
@@ -305,7 +333,7 @@ __device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const u
                 }
                 if (__any_sync(0xffffffffu, c0 && c1) && c0 && c1)   // a lane that composites it at both pixels
                     bwd_composite_b2f(p1.T, p1.Sp, p1.g0, p1.g1, p1.g2, bb, cb, dx1, dy1, ag1, acc);
-                splat_sums_out(acc, role, vi, a, bb, WSw.id[e], sgrad);
+                splat_sums_out(acc, role, vi, a, bb, WSw.id[e], sg);
             }
             __syncwarp();
         }
@@ -320,6 +348,7 @@ __device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const u
         const int pl = b0 + lane;
         const int cnt = warp_stage<true>(WSw, rec, vals, it.s0 + (uint32_t)pl, it.s0, pl < maxlim, cap_cand,
                                                st, 53, bx0, bx1, by0, by1);
+        stage_offsets(WSw, cnt, sg);
         for (int e = 0; e < cnt; ++e) {
             const int q1 = WSw.pos[e] + 1;
             const float4 a = WSw.a[e];
@@ -348,7 +377,7 @@ __device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const u
             }
             if (__any_sync(0xffffffffu, c0 && c1) && c0 && c1)   // a lane that composites it at both pixels
                 bwd_composite_f2b(p1.T, p1.Sp, p1.GC, p1.g0, p1.g1, p1.g2, bb, cb, dx1, dy1, ag1, acc);
-            splat_sums_out(acc, role, vi, a, bb, WSw.id[e], sgrad);
+            splat_sums_out(acc, role, vi, a, bb, WSw.id[e], sg);
         }
         __syncwarp();
         // pixels whose last position lies in this batch are finished
@@ -362,7 +391,7 @@ __device__ __forceinline__ void bwd_unit(const float4 *__restrict__ rec, const u
 __global__ void __launch_bounds__(kRThreads) render_bwd_kernel(
     const float4 *__restrict__ rec, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
     ViewTable vt, RenderPlan plan, const float *__restrict__ image, const float *__restrict__ d_image,
-    const int32_t *__restrict__ last_in, float *__restrict__ sgrad, long long cap_cand, const gs_status *st)
+    const int32_t *__restrict__ last_in, SgOut sg, long long cap_cand, const gs_status *st)
 {
     if (has_error(st)) return;
     __shared__ WarpStage WS[kRThreads / 32];
@@ -370,7 +399,7 @@ __global__ void __launch_bounds__(kRThreads) render_bwd_kernel(
     const int n_units = 4 * __ldg(plan.item_base + vt.total_tiles);
     int32_t *counter = plan.counters + 2;
     for (int u = next_unit(counter); u < n_units; u = next_unit(counter))
-        bwd_unit(rec, vals, ranges, vt, plan, image, d_image, last_in, sgrad, cap_cand, st, u >> 2, u & 3, W);
+        bwd_unit(rec, vals, ranges, vt, plan, image, d_image, last_in, sg, cap_cand, st, u >> 2, u & 3, W);
 }
 
 // Projection chain rule, one thread per candidate.
@@ -422,11 +451,13 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(ProjBwdArgs a, ViewTab
 // zeroing only the covering candidates would leave sectors shared with a
 // non-covering neighbour partly written, which costs DRAM read-modify-writes.
 __global__ void __launch_bounds__(256) zero_sgrad_kernel(const int32_t *__restrict__ view_start, int V, int k,
-                                                         long long cap_cand, float *__restrict__ sgrad,
+                                                         long long cap_rows, int tiled, float *__restrict__ sgrad,
                                                          const gs_status *st)
 {
     if (has_error(st)) return;
-    const long long n = 9 * std::min<long long>((long long)__ldg(view_start + V) * k, cap_cand);
+    long long rows = std::min<long long>(__ldg(view_start + V), cap_rows);
+    if (tiled) rows = (rows + 127) / 128 * 128;   // the whole last tile of rows
+    const long long n = 9 * rows * k;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if ((reinterpret_cast<uintptr_t>(sgrad) & 15) == 0) {
@@ -444,16 +475,29 @@ int launch_render_bwd(const gs_gauss3d *g, const gs_camera *cams, const gs_splat
                       cudaStream_t s)
 {
     const long long cap_cand = g->cap_rows * (long long)g->k;
+    const bool tiled = sgrad->layout == GS_SGRAD_ROW_TILES;
+    if (9ll * ((g->cap_rows + 127) / 128 * 128) * g->k >= (1ll << 32)) return GS_ERR_UNSUPPORTED;   // 32-bit offsets
+    SgOut sg;
+    sg.g = sgrad->g;
+    sg.tiled = tiled ? 1 : 0;
+    sg.k = (uint32_t)g->k;
+    {   // multiply-high division by k (see SgOut)
+        int l = 0;
+        while ((1u << l) < sg.k) ++l;
+        sg.m = (uint32_t)(((1ull << 32) * ((1ull << l) - sg.k)) / sg.k + 1);
+        sg.s1 = l > 0 ? 1u : 0u;
+        sg.s2 = l > 0 ? (uint32_t)(l - 1) : 0u;
+    }
     const int zgrid = (int)std::max<long long>(1, std::min<long long>((cap_cand + 255) / 256,
                                                                       (long long)sm_count() * 16));
-    zero_sgrad_kernel<<<zgrid, 256, 0, s>>>(g->view_start, vt.V, g->k, cap_cand, sgrad->g, st);
+    zero_sgrad_kernel<<<zgrid, 256, 0, s>>>(g->view_start, vt.V, g->k, g->cap_rows, sg.tiled, sgrad->g, st);
     count_launches(1);
     const float4 *rec = reinterpret_cast<const float4 *>(sp->rec);
     if (vt.total_tiles > 0) {
         const RenderPlan plan = render_plan(vt, bins->cap_pairs, L, ws);
         cudaMemsetAsync(plan.counters + 2, 0, sizeof(int32_t), s);
         render_bwd_kernel<<<persistent_grid((const void *)render_bwd_kernel, tuning().bwd_ctas_per_sm), kRThreads, 0, s>>>(
-            rec, bins->vals, bins->ranges, vt, plan, image, d_image, last, sgrad->g,
+            rec, bins->vals, bins->ranges, vt, plan, image, d_image, last, sg,
             std::min<long long>(sp->cap, cap_cand), st);
         count_launches(1);
     }

@@ -90,7 +90,11 @@ class RenderPass:
         self.bins = api.Bins.alloc(self.cap_pairs, self.views.total_tiles, dev, keys=self.want_keys)
         self.sort_ws = api.workspace(api.bin_sort_workspace(self.views, C_, self.cap_pairs), dev)
         self.render_ws = api.workspace(api.render_workspace(self.views, self.cap_pairs, self.chunk), dev)
-        self.sgrad = torch.zeros(max(C_, 1), 9, device=dev)
+        # the fused tensor-core reverse reads the splat gradients in row tiles, written so by render_bwd
+        self.sgrad_layout = (L.GS_SGRAD_ROW_TILES if self.anchors is not None and not self.gaussians_written
+                             else L.GS_SGRAD_CANDIDATE)
+        rows = self.cap_rows if self.sgrad_layout == L.GS_SGRAD_CANDIDATE else (self.cap_rows + 127) // 128 * 128
+        self.sgrad = torch.zeros(max(rows * self.k, 1), 9, device=dev)
         self.ggrad = None
 
     def set_explicit(self, g: api.Gauss3D):
@@ -144,9 +148,9 @@ class RenderPass:
         last = self.last if self.store_state else None
         if self.anchors is not None:
             api.render_bwd(self.g, self.splats, self.bins, self.views, self.image, dimg, self.sgrad, None,
-                           self.status, self.render_ws, self.chunk, last, stream)
+                           self.status, self.render_ws, self.chunk, last, stream, self.sgrad_layout)
             api.decode_project_bwd(self.anchors, self.views, self.g, self.splats, self.sgrad, self.agrad,
-                                   self.dpbwd_ws, self.status, self.precision, stream)
+                                   self.dpbwd_ws, self.status, self.precision, stream, self.sgrad_layout)
             return self.agrad
         if self.ggrad is None or self.ggrad.dmu.shape[0] != self.g.mu.shape[0]:
             self.ggrad = api.Gauss3DGrad.like(self.g)

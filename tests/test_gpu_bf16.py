@@ -180,6 +180,14 @@ def test_bf16_fused_projection_and_decode_bwd(make):
     fused = api.AnchorGrad.like(A)
     api.decode_project_bwd(A, vw, g, sp, sgrad, fused, api.workspace(api.decode_project_bwd_workspace(g, L.GS_PREC_BF16)),
                            st, L.GS_PREC_BF16)
+    # the same gradients in row tiles of 128 ([tile][i][9][128]): read in place, no workspace
+    nt = (cap + 127) // 128
+    sgt = np.zeros((nt * 128, s.k, 9), np.float32)
+    sgt[:cap] = to_np(sgrad).reshape(cap, s.k, 9)
+    sgt = np.ascontiguousarray(sgt.reshape(nt, 128, s.k, 9).transpose(0, 2, 3, 1))
+    tiled = api.AnchorGrad.like(A)
+    api.decode_project_bwd(A, vw, g, sp, torch.as_tensor(sgt).cuda(), tiled, None, st, L.GS_PREC_BF16, None,
+                           L.GS_SGRAD_ROW_TILES)
     dg = api.Gauss3DGrad.like(g)
     api.project_bwd(g, sp, vw, sgrad, dg, st)
     unfused = api.AnchorGrad.like(A)
@@ -201,3 +209,5 @@ def test_bf16_fused_projection_and_decode_bwd(make):
         print(f"[fused] {name}: cosine {cos:.6f} / {cos_u:.7f} (oracle / unfused), relative error {rel:.3e}")
         assert cos >= 0.999 and rel <= 3e-2, f"{name}: cosine {cos:.5f}, relative error {rel:.3e}"
         assert cos_u >= 0.9999, f"{name}: cosine to the unfused path {cos_u:.6f}"
+        t = to_np(getattr(tiled, name)).ravel().astype(np.float64)   # same sums, other atomic order
+        assert np.linalg.norm(t - a) <= 1e-5 * (np.linalg.norm(a) + 1e-30), f"{name}: row-tiled input differs"
