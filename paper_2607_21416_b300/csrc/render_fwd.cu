@@ -79,12 +79,14 @@ __global__ void __launch_bounds__(1024) plan_kernel(const uint32_t *__restrict__
 // The tile of every item (one thread per tile writes its items' entries), so
 // that a work unit finds its tile without a search.
 __global__ void __launch_bounds__(256) item_tiles_kernel(const int32_t *__restrict__ item_base, int T,
-                                                         int max_items, int32_t *__restrict__ item_tile)
+                                                         int max_items, int32_t *__restrict__ item_tile,
+                                                         int32_t *__restrict__ multi_list, int32_t *__restrict__ counters)
 {
     const int n = min(item_base[T], max_items);   // 0 when the plan overflowed (no item runs)
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
         const int b0 = item_base[t], b1 = t + 1 < T ? min(item_base[t + 1], n) : n;
         for (int b = max(b0, 0); b < b1; ++b) item_tile[b] = t;
+        if (b1 - b0 > 1) multi_list[atomicAdd(counters + 5, 1)] = t;   // tiles cut into several chunks
     }
 }
 
@@ -368,15 +370,11 @@ __global__ void __launch_bounds__(kRThreads) chunk_kernel(const float4 *__restri
 constexpr int kCombineAhead = 16;   // chunk states loaded per group by the combine walk
 
 template <bool COUNT>
-__global__ void __launch_bounds__(2 * kRThreads) combine_kernel(const uint32_t *__restrict__ ranges, ViewTable vt,
-                                                            RenderPlan plan, float bg0, float bg1, float bg2,
-                                                            float *__restrict__ image, float *__restrict__ T_final,
-                                                            int32_t *__restrict__ last,
-                                                            unsigned long long *__restrict__ n_eval,
-                                                            const gs_status *st)
+__device__ __forceinline__ void combine_tile(int t, const uint32_t *__restrict__ ranges, const ViewTable &vt,
+                                             const RenderPlan &plan, float bg0, float bg1, float bg2,
+                                             float *__restrict__ image, float *__restrict__ T_final,
+                                             int32_t *__restrict__ last, unsigned long long *__restrict__ n_eval)
 {
-    if (has_error(st)) return;
-    const int t = blockIdx.x;
     const int base = plan.item_base[t], nk = plan.item_base[t + 1] - base;
     if (nk <= 1) return;
     // one pixel per thread: tile thread (threadIdx & 127), pixel row half (threadIdx >> 7)
@@ -477,6 +475,30 @@ __global__ void __launch_bounds__(2 * kRThreads) combine_kernel(const uint32_t *
     if (COUNT) count_add(n_eval, nev, ncomp);
 }
 
+// One CTA per tile cut into several chunks, taken from the plan's list of
+// such tiles through a counter (CTAs that finish a short tile take the next).
+template <bool COUNT>
+__global__ void __launch_bounds__(2 * kRThreads) combine_kernel(const uint32_t *__restrict__ ranges, ViewTable vt,
+                                                            RenderPlan plan, float bg0, float bg1, float bg2,
+                                                            float *__restrict__ image, float *__restrict__ T_final,
+                                                            int32_t *__restrict__ last,
+                                                            unsigned long long *__restrict__ n_eval,
+                                                            const gs_status *st)
+{
+    if (has_error(st)) return;
+    __shared__ int s_j;
+    const int n_multi = *(volatile const int32_t *)(plan.counters + 5);
+    for (;;) {
+        __syncthreads();   // the previous tile's readers of s_j are done
+        if (threadIdx.x == 0) s_j = atomicAdd(plan.counters + 6, 1);
+        __syncthreads();
+        const int j = s_j;
+        if (j >= n_multi) break;
+        combine_tile<COUNT>(__ldg(plan.multi_list + j), ranges, vt, plan, bg0, bg1, bg2, image, T_final, last,
+                            n_eval);
+    }
+}
+
 int persistent_grid(const void *kernel, int cap_per_sm)
 {
     static int dev_smem = 0, dev_reserve = 0;
@@ -538,12 +560,13 @@ size_t render_workspace_bytes(const ViewTable &vt, long long cap_pairs, int L)
            2 * align_up(sizeof(int32_t) * (size_t)items, 256) +
            align_up(sizeof(float) * (size_t)items * kStateWords * kRT, 256) +
            align_up(sizeof(int32_t) * 4 * (size_t)items, 256) + align_up(sizeof(int32_t) * (size_t)items, 256) +
+           align_up(sizeof(int32_t) * (size_t)vt.total_tiles, 256) +
            align_up(sizeof(uint32_t) * 4 * (size_t)std::max<long long>(cap_pairs, 1), 256);
 }
 
 // Workspace: item_base [T + 1] | counters [8] | fix flags [max_items] | fix list [max_items] |
 // state [max_items][kStateWords][256] | block-list counts [max_items][4] | item tiles [max_items] |
-// block lists [4 cap_pairs]
+// multi-chunk tile list [T] | block lists [4 cap_pairs]
 RenderPlan render_plan(const ViewTable &vt, long long cap_pairs, int L, void *ws)
 {
     RenderPlan p;
@@ -555,7 +578,8 @@ RenderPlan render_plan(const ViewTable &vt, long long cap_pairs, int L, void *ws
     const size_t o2 = o1 + 2 * align_up(sizeof(int32_t) * (size_t)p.max_items, 256);
     const size_t o3 = o2 + align_up(sizeof(float) * (size_t)p.max_items * kStateWords * kRT, 256);
     const size_t o35 = o3 + align_up(sizeof(int32_t) * 4 * (size_t)p.max_items, 256);
-    const size_t o4 = o35 + align_up(sizeof(int32_t) * (size_t)p.max_items, 256);
+    const size_t o36 = o35 + align_up(sizeof(int32_t) * (size_t)p.max_items, 256);
+    const size_t o4 = o36 + align_up(sizeof(int32_t) * (size_t)vt.total_tiles, 256);
     p.item_base = reinterpret_cast<int32_t *>(w);
     p.counters = reinterpret_cast<int32_t *>(w + o0);
     p.fix = reinterpret_cast<int32_t *>(w + o1);
@@ -563,6 +587,7 @@ RenderPlan render_plan(const ViewTable &vt, long long cap_pairs, int L, void *ws
     p.state = reinterpret_cast<float *>(w + o2);
     p.bcnt = reinterpret_cast<int32_t *>(w + o3);
     p.item_tile = reinterpret_cast<int32_t *>(w + o35);
+    p.multi_list = reinterpret_cast<int32_t *>(w + o36);
     p.blist = reinterpret_cast<uint32_t *>(w + o4);
     return p;
 }
@@ -575,8 +600,8 @@ static void launch_items(const float4 *rec, const gs_bins *bins, const ViewTable
     chunk_kernel<COUNT, false><<<persistent_grid((const void *)chunk_kernel<COUNT, false>, tuning().fwd_ctas_per_sm), kRThreads, 0, s>>>(rec, bins->vals, bins->ranges, vt, plan, bg[0],
                                                                    bg[1], bg[2], image, T_final, last, n_eval, cap,
                                                                    st);
-    combine_kernel<COUNT><<<vt.total_tiles, 2 * kRThreads, 0, s>>>(bins->ranges, vt, plan, bg[0], bg[1], bg[2], image,
-                                                              T_final, last, n_eval, st);
+    combine_kernel<COUNT><<<(int)std::min<long long>(vt.total_tiles, (long long)sm_count() * 8), 2 * kRThreads, 0, s>>>(
+        bins->ranges, vt, plan, bg[0], bg[1], bg[2], image, T_final, last, n_eval, st);
     chunk_kernel<COUNT, true><<<persistent_grid((const void *)chunk_kernel<COUNT, true>, tuning().fwd_ctas_per_sm), kRThreads, 0, s>>>(rec, bins->vals, bins->ranges, vt, plan, bg[0],
                                                                   bg[1], bg[2], image, T_final, last, n_eval, cap,
                                                                   st);
@@ -592,7 +617,8 @@ int launch_render_fwd(const gs_splats *sp, const gs_bins *bins, const ViewTable 
     plan_kernel<<<1, 1024, 0, s>>>(bins->ranges, vt.total_tiles, L, plan.max_items,
                                    const_cast<int32_t *>(plan.item_base), plan.fix, plan.counters, st);
     item_tiles_kernel<<<(int)std::max<long long>(1, std::min<long long>((vt.total_tiles + 255) / 256, (long long)sm_count() * 4)),
-                        256, 0, s>>>(plan.item_base, vt.total_tiles, plan.max_items, plan.item_tile);
+                        256, 0, s>>>(plan.item_base, vt.total_tiles, plan.max_items, plan.item_tile, plan.multi_list,
+                                     plan.counters);
     block_lists_kernel<<<persistent_grid((const void *)block_lists_kernel), kRThreads, 0, s>>>(
         rec, bins->vals, bins->ranges, vt, plan, sp->cap, st);
     if (n_eval) {
