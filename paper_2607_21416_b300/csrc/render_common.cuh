@@ -237,7 +237,7 @@ __device__ __forceinline__ int next_unit(int32_t *counter)
 struct RenderPlan {
     const int32_t *item_base;   // [T+1]
     int32_t *counters;          // [8] work-unit counters: forward, fix-up, backward, fix count, block lists,
-                                //     multi-chunk tile count, combine
+                                //     long multi-chunk tiles, combine, other multi-chunk tiles
     int32_t *fix;               // [max_items] flags: items with pixels to composite again
     int32_t *fix_list;          // [max_items] those items, counters[3] of them
     float *state;               // [max_items][kStateWords][256]
@@ -248,7 +248,8 @@ struct RenderPlan {
     uint32_t *blist;            // [4 cap_pairs]
     int32_t *bcnt;              // [max_items][4]
     int32_t *item_tile;         // [max_items] tile of each item
-    int32_t *multi_list;        // [T] tiles cut into several chunks, counters[5] of them
+    int32_t *multi_list;        // [T] tiles cut into several chunks: counters[5] long ones from the front,
+                                //     counters[7] others from the back
     int L;
     int max_items;
 };

@@ -76,6 +76,8 @@ __global__ void __launch_bounds__(1024) plan_kernel(const uint32_t *__restrict__
     }
 }
 
+constexpr int kLongTile = 32;   // chunks above which the combine takes a tile first
+
 // The tile of every item (one thread per tile writes its items' entries), so
 // that a work unit finds its tile without a search.
 __global__ void __launch_bounds__(256) item_tiles_kernel(const int32_t *__restrict__ item_base, int T,
@@ -86,7 +88,10 @@ __global__ void __launch_bounds__(256) item_tiles_kernel(const int32_t *__restri
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
         const int b0 = item_base[t], b1 = t + 1 < T ? min(item_base[t + 1], n) : n;
         for (int b = max(b0, 0); b < b1; ++b) item_tile[b] = t;
-        if (b1 - b0 > 1) multi_list[atomicAdd(counters + 5, 1)] = t;   // tiles cut into several chunks
+        // tiles cut into several chunks: the long ones from the front of the list, the others from the
+        // back, so that the combine starts the longest walks first
+        if (b1 - b0 > kLongTile) multi_list[atomicAdd(counters + 5, 1)] = t;
+        else if (b1 - b0 > 1) multi_list[T - 1 - atomicAdd(counters + 7, 1)] = t;
     }
 }
 
@@ -487,15 +492,16 @@ __global__ void __launch_bounds__(2 * kRThreads) combine_kernel(const uint32_t *
 {
     if (has_error(st)) return;
     __shared__ int s_j;
-    const int n_multi = *(volatile const int32_t *)(plan.counters + 5);
+    const int n_long = *(volatile const int32_t *)(plan.counters + 5);
+    const int n_multi = n_long + *(volatile const int32_t *)(plan.counters + 7);
     for (;;) {
         __syncthreads();   // the previous tile's readers of s_j are done
         if (threadIdx.x == 0) s_j = atomicAdd(plan.counters + 6, 1);
         __syncthreads();
         const int j = s_j;
         if (j >= n_multi) break;
-        combine_tile<COUNT>(__ldg(plan.multi_list + j), ranges, vt, plan, bg0, bg1, bg2, image, T_final, last,
-                            n_eval);
+        const int t = __ldg(plan.multi_list + (j < n_long ? j : vt.total_tiles - 1 - (j - n_long)));
+        combine_tile<COUNT>(t, ranges, vt, plan, bg0, bg1, bg2, image, T_final, last, n_eval);
     }
 }
 
