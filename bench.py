@@ -653,7 +653,8 @@ def work_counts(rp):
             "examined_single_item_tiles": int(rp.n_eval[2].item()),
             "composited_single_item_tiles": int(rp.n_eval[3].item()),
             "reverse_examined": int(last64.sum().item()),
-            "examined_reverse_walk": int(rp.n_eval[2].item()) + int(last64[pix_multi].sum().item())}
+            "examined_reverse_walk": int(rp.n_eval[2].item()) + int(last64[pix_multi].sum().item()),
+            "covering_splats": int((rp.splats.tiles[:rp.n_rows() * rp.k] > 0).sum().item())}
 
 
 # -------------------------------------------------------------- CPU oracle
