@@ -293,8 +293,10 @@ int gs_decode_project(const gs_anchors *A, const gs_camera *cams, const gs_view 
  * its splats in depth order): one pair per (covered tile, splat), ordered by
  * (global tile, float bits of depth, splat id) -- exactly the order of a sort
  * on the 64-bit key (tile << 32 | depth bits) with ties broken by id.  Also
- * writes [start, end) per tile (empty tiles [0, 0)).  k and view_start as in
- * gs_gauss3d.  Capacity: bins->cap_pairs; overflow -> GS_ERR_CAPACITY with the
+ * writes [start, end) per tile (empty tiles [0, 0)).  The covering splats
+ * (tiles > 0) contribute the tiles of their rectangle (record floats 10-11);
+ * one whose rectangle is empty records GS_ERR_INVALID_ARG.  k and view_start
+ * as in gs_gauss3d.  Capacity: bins->cap_pairs; overflow -> GS_ERR_CAPACITY with the
  * pair count needed.  Workspace: gs_bin_sort_workspace bytes. */
 int gs_bin_sort(const gs_splats *sp, int32_t k, const int32_t *view_start, int64_t cap_rows,
                 const gs_view *views, int32_t V, gs_bins *bins, void *ws, size_t ws_bytes,

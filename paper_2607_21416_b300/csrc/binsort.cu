@@ -7,11 +7,12 @@
 //      candidate-id order;
 //   2. stable radix sort of those splats on their 32-bit depth bits (ties
 //      keep id order);
-//   3. scan the tile counts in depth order (per-splat pair offsets) and emit
+//   3. gather the splats' tile rectangles into depth order (once), scan
+//      their tile counts (per-splat pair offsets) and emit
 //      one (tile id, splat id) pair per covered tile, load-balanced: each
 //      CTA round writes 2048 consecutive pairs; the scan also records the
 //      splat that owns each round's first pair, and each pair finds its splat
-//      by binary search over the round's staged offsets;
+//      by a max-scan over the round's staged first positions;
 //   4. stable radix sort of the pairs on the tile id (only the bits the tile
 //      count needs), which keeps depth-then-id order inside each tile;
 //   5. tile ranges [start, end) and, on request, the 64-bit keys.
@@ -24,7 +25,7 @@ constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;   // 2048 elements
 constexpr int kRadixItems = 8;                          // keys per thread of a radix pass tile
-constexpr int kRadixTile = kSortThreads * kRadixItems;  // 4096 keys
+constexpr int kRadixTile = kSortThreads * kRadixItems;  // 2048 keys
 constexpr int kSortWarps = kSortThreads / 32;
 
 __device__ __forceinline__ unsigned lanemask_lt()
@@ -87,8 +88,16 @@ __global__ void __launch_bounds__(kSortThreads) radix_upsweep(const uint32_t *__
     block_tiles<kRadixTile>(n, blockIdx.x, gridDim.x, &t0, &t1);
     const int warp = threadIdx.x >> 5;
     const uint32_t e0 = t0 * kRadixTile, e1 = min(n, t1 * kRadixTile);
-    for (uint32_t i = e0 + threadIdx.x; i < e1; i += kSortThreads)
-        atomicAdd(&s_h[warp * 256 + ((keys[i] >> shift) & 0xffu)], 1u);
+    // eight keys per thread per step, their loads issued together
+    uint32_t i = e0 + threadIdx.x;
+    for (; i + 7 * kSortThreads < e1; i += 8 * kSortThreads) {
+        uint32_t kk[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) kk[j] = keys[i + j * kSortThreads];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) atomicAdd(&s_h[warp * 256 + ((kk[j] >> shift) & 0xffu)], 1u);
+    }
+    for (; i < e1; i += kSortThreads) atomicAdd(&s_h[warp * 256 + ((keys[i] >> shift) & 0xffu)], 1u);
     __syncthreads();
     uint32_t sum = 0;
 #pragma unroll
@@ -317,20 +326,24 @@ __global__ void __launch_bounds__(1024) scan_block_sums(uint32_t *__restrict__ s
     }
 }
 
-// Pass B: write the covering splats' ids and depth keys in id order.  Each
-// thread owns 8 consecutive candidates of a 2048-candidate tile (one block
-// scan per tile).
+// Pass B: the covering splats in id order: their depth keys, their tile
+// rectangles and ids (one 16-byte entry each; depth and rectangle come from
+// the 16 bytes of the record that hold both, one sector per splat) and their
+// compacted index (the value the depth sort carries).  Each thread owns 8
+// consecutive candidates of a 2048-candidate tile (one block scan per tile).
 __global__ void __launch_bounds__(kSortThreads) compact_valid_kernel(
     const int32_t *__restrict__ tiles, const float4 *__restrict__ rec,
     const int32_t *__restrict__ view_start, int V, int k, long long cap_cand,
-    const uint32_t *__restrict__ block_off, uint32_t *__restrict__ ids, uint32_t *__restrict__ dkeys,
-    const gs_status *st)
+    const uint32_t *__restrict__ block_off, uint32_t *__restrict__ dkeys, uint4 *__restrict__ crec,
+    uint32_t *__restrict__ cidx, const gs_status *st)
 {
     if (__syncthreads_or(has_error(st))) return;   // block-uniform exit
     const uint32_t C = (uint32_t)min((long long)__ldg(view_start + V) * k, cap_cand);
     uint32_t t0, t1;
     block_tiles(C, blockIdx.x, gridDim.x, &t0, &t1);
     __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_dk[kSortTile];
+    __shared__ uint4 s_rec[kSortTile];
     const bool vec = (reinterpret_cast<uintptr_t>(tiles) & 15) == 0;
     uint32_t base = block_off[blockIdx.x];
     for (uint32_t t = t0; t < t1; ++t) {
@@ -344,35 +357,59 @@ __global__ void __launch_bounds__(kSortThreads) compact_valid_kernel(
 #pragma unroll
             for (int j = 0; j < kSortItems; ++j) tl[j] = i0 + j < C ? __ldg(tiles + i0 + j) : 0;
         }
-        // depth keys of the covering candidates, all loads issued before the block scan
-        const float *recf = reinterpret_cast<const float *>(rec);
-        uint32_t dk[kSortItems];
+        // record floats 8..11 (colour b, depth, rectangle) of the covering candidates, all loads
+        // issued before the block scan
+        float4 r[kSortItems];
         uint32_t n = 0;
 #pragma unroll
         for (int j = 0; j < kSortItems; ++j) {
-            dk[j] = tl[j] > 0 ? __float_as_uint(__ldg(recf + 12 * (size_t)(i0 + j) + 9)) : 0u;
+            r[j] = tl[j] > 0 ? __ldg(rec + 3 * (size_t)(i0 + j) + 2) : make_float4(0.f, 0.f, 0.f, 0.f);
             n += tl[j] > 0;
         }
         uint32_t tot;
-        uint32_t off = base + scan256(n, s_warp, &tot);
+        uint32_t loc = scan256(n, s_warp, &tot);
+        // staged in shared memory by tile-local position, then written out with consecutive
+        // lanes on consecutive entries
 #pragma unroll
         for (int j = 0; j < kSortItems; ++j) {
             if (tl[j] > 0) {
-                if (idx_ok(st, (long long)off, C, 31)) {
-                    ids[off] = i0 + j;
-                    dkeys[off] = dk[j];
+                if (idx_ok(st, (long long)loc, kSortTile, 31)) {
+                    s_dk[loc] = __float_as_uint(r[j].y);
+                    s_rec[loc] = make_uint4(__float_as_uint(r[j].z), __float_as_uint(r[j].w), i0 + j, 0u);
                 }
-                ++off;
+                ++loc;
             }
         }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < tot; i += kSortThreads) {
+            const uint32_t o = base + i;
+            if (!idx_ok(st, (long long)o, C, 31)) break;
+            dkeys[o] = s_dk[i];
+            crec[o] = s_rec[i];
+            cidx[o] = o;
+        }
+        __syncthreads();   // the stage is rewritten by the next tile
         base += tot;
     }
 }
 
-// Pairs: per-block sums of tile counts in depth order.
+// Tile count of a packed rectangle (x0 | x1 << 16, y0 | y1 << 16).
+__device__ __forceinline__ uint32_t rect_area(uint2 r)
+{
+    const int w = (int)(r.x >> 16) - (int)(r.x & 0xffffu), h = (int)(r.y >> 16) - (int)(r.y & 0xffffu);
+    return w > 0 && h > 0 ? (uint32_t)(w * h) : 0u;
+}
+
+// Pairs: the covering splats' ids and tile rectangles gathered into depth
+// order (from the compacted entries, by the compacted index the depth sort
+// carried), read in order by the offsets and the emission, and per-block
+// sums of their tile counts.  A covering splat with
+// an empty rectangle is an inconsistent input (its tile count says
+// otherwise).
 __global__ void __launch_bounds__(kSortThreads) count_pairs_kernel(
-    const uint32_t *__restrict__ ids, const uint32_t *__restrict__ n_ptr, const int32_t *__restrict__ tiles,
-    uint32_t *__restrict__ block_sums, long long cap_cand, const gs_status *st)
+    const uint32_t *__restrict__ cidx_s, const uint32_t *__restrict__ n_ptr, const uint4 *__restrict__ crec,
+    uint32_t *__restrict__ ids, uint2 *__restrict__ rect,
+    uint32_t *__restrict__ block_sums, const gs_status *st)
 {
     if (__syncthreads_or(has_error(st))) return;   // block-uniform exit
     const uint32_t S = *n_ptr;
@@ -380,19 +417,30 @@ __global__ void __launch_bounds__(kSortThreads) count_pairs_kernel(
     block_tiles(S, blockIdx.x, gridDim.x, &t0, &t1);
     unsigned long long n = 0;
     for (uint32_t b = t0 * kSortTile; b < min(S, t1 * kSortTile); b += kSortThreads * kSortItems) {
-        uint32_t id[kSortItems];
-        int32_t c[kSortItems];
+        uint32_t q[kSortItems];
+        uint4 r[kSortItems];
 #pragma unroll
-        for (int j = 0; j < kSortItems; ++j) {   // the ids, then every tile count, loads issued together
+        for (int j = 0; j < kSortItems; ++j) {   // the compacted indices, then the gathers, loads issued together
             const uint32_t i = b + j * kSortThreads + threadIdx.x;
-            id[j] = i < S ? ids[i] : 0u;
+            q[j] = i < S ? cidx_s[i] : 0u;
         }
 #pragma unroll
-        for (int j = 0; j < kSortItems; ++j)
-            c[j] = (b + j * kSortThreads + threadIdx.x < S && id[j] < cap_cand) ? __ldg(tiles + id[j]) : 0;
+        for (int j = 0; j < kSortItems; ++j) {
+            const bool in = b + j * kSortThreads + threadIdx.x < S && q[j] < S;
+            r[j] = in ? crec[q[j]] : make_uint4(0u, 0u, 0u, 0u);
+        }
 #pragma unroll
-        for (int j = 0; j < kSortItems; ++j)
-            if (b + j * kSortThreads + threadIdx.x < S && idx_ok(st, id[j], cap_cand, 34)) n += (uint32_t)c[j];
+        for (int j = 0; j < kSortItems; ++j) {
+            const uint32_t i = b + j * kSortThreads + threadIdx.x;
+            if (i < S && idx_ok(st, q[j], S, 34)) {
+                const uint2 rr = make_uint2(r[j].x, r[j].y);
+                const uint32_t c = rect_area(rr);
+                if (c == 0) idx_ok(st, (long long)r[j].z, -1, 34);
+                rect[i] = rr;
+                ids[i] = r[j].z;
+                n += c;
+            }
+        }
     }
     // the per-block total fits 32 bits when the whole total does (checked later)
     __shared__ uint32_t s_warp[32];
@@ -405,13 +453,13 @@ constexpr int kEmitPairs = 2048;   // pairs written per CTA and round
 
 // Per-splat pair offsets in depth order: offs[i] = sum of the tile counts of
 // splats 0..i-1 (block prefixes from scan_block_sums), 8 splats per thread
-// and one block scan per 2048 splats.  Every splat owns >= 1 pair, so each
-// emission round r (pairs [2048 r, 2048 r + 2048)) starts inside exactly one
-// splat's range [offs[i], offs[i] + count): that splat writes round_first[r].
+// (their rectangles in four 16-byte loads) and one block scan per 2048
+// splats.  Every splat owns >= 1 pair, so each emission round r (pairs
+// [2048 r, 2048 r + 2048)) starts inside exactly one splat's range [offs[i],
+// offs[i] + count): that splat writes round_first[r].
 __global__ void __launch_bounds__(kSortThreads) pair_offsets_kernel(
-    const uint32_t *__restrict__ ids, const uint32_t *__restrict__ n_ptr, const int32_t *__restrict__ tiles,
-    const uint32_t *__restrict__ block_off, uint32_t *__restrict__ offs, uint32_t *__restrict__ round_first,
-    long long max_rounds, long long cap_cand, const gs_status *st)
+    const uint2 *__restrict__ rect, const uint32_t *__restrict__ n_ptr, const uint32_t *__restrict__ block_off,
+    uint32_t *__restrict__ offs, uint32_t *__restrict__ round_first, long long max_rounds, const gs_status *st)
 {
     if (__syncthreads_or(has_error(st))) return;   // block-uniform exit
     const uint32_t S = *n_ptr;
@@ -421,18 +469,24 @@ __global__ void __launch_bounds__(kSortThreads) pair_offsets_kernel(
     uint32_t base = block_off[blockIdx.x];
     for (uint32_t t = t0; t < t1; ++t) {
         const uint32_t i0 = t * kSortTile + threadIdx.x * kSortItems;
-        uint32_t cnt[kSortItems], id[kSortItems];
+        uint32_t cnt[kSortItems];
         uint32_t n = 0;
+        if (i0 + kSortItems <= S) {
+            const uint4 *r4 = reinterpret_cast<const uint4 *>(rect + i0);
+            uint4 u[kSortItems / 2];
 #pragma unroll
-        for (int j = 0; j < kSortItems; ++j) id[j] = i0 + j < S ? ids[i0 + j] : 0u;
+            for (int j = 0; j < kSortItems / 2; ++j) u[j] = r4[j];
 #pragma unroll
-        for (int j = 0; j < kSortItems; ++j)   // every tile count load issued before any is used
-            cnt[j] = (i0 + j < S && id[j] < cap_cand) ? (uint32_t)__ldg(tiles + id[j]) : 0u;
+            for (int j = 0; j < kSortItems / 2; ++j) {
+                cnt[2 * j] = rect_area(make_uint2(u[j].x, u[j].y));
+                cnt[2 * j + 1] = rect_area(make_uint2(u[j].z, u[j].w));
+            }
+        } else {
 #pragma unroll
-        for (int j = 0; j < kSortItems; ++j) {
-            if (i0 + j < S && !idx_ok(st, id[j], cap_cand, 35)) cnt[j] = 0;
-            n += cnt[j];
+            for (int j = 0; j < kSortItems; ++j) cnt[j] = i0 + j < S ? rect_area(rect[i0 + j]) : 0u;
         }
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) n += cnt[j];
         uint32_t tot;
         uint32_t off = base + scan256(n, s_warp, &tot);
 #pragma unroll
@@ -475,14 +529,14 @@ __device__ __forceinline__ uint32_t scanmax256_excl(uint32_t x, uint32_t *s_warp
 // pair of this round unless it starts exactly there) -- at most 2048 splats,
 // since every compacted splat owns >= 1 pair.  Every thread reads the two
 // bounds itself, and those of the CTA's next round are loaded while the
-// current round runs.  The staged splats keep their rectangle's first tile,
-// width and the view's tile row length (every thread's loads issued
-// together); each marks the round-local position of its first pair in s_own
+// current round runs.  The staged splats keep their rectangle's first tile
+// (the rectangles come in depth order from count_pairs_kernel, read beside
+// the ids), width and the view's tile row length; each marks the round-local position of its first pair in s_own
 // and a max-scan fills every pair's position with its owner.  Pair t of a
 // splat is tile (t % w, t / w) of its rectangle, row-major.
 __global__ void __launch_bounds__(kSortThreads) emit_pairs_kernel(
     const uint32_t *__restrict__ ids, const uint32_t *__restrict__ n_ptr, const uint32_t *__restrict__ np_ptr,
-    const uint32_t *__restrict__ offs, const uint32_t *__restrict__ round_first, const float4 *__restrict__ rec,
+    const uint32_t *__restrict__ offs, const uint32_t *__restrict__ round_first, const uint2 *__restrict__ rect,
     const int32_t *__restrict__ view_start, int k, uint32_t *__restrict__ tkeys, uint32_t *__restrict__ tvals,
     ViewTable vt, long long cap_cand, const gs_status *st)
 {
@@ -522,12 +576,11 @@ __global__ void __launch_bounds__(kSortThreads) emit_pairs_kernel(
             ov[u] = in ? offs[sa + j] : 0u;
             oe[u] = in ? (sa + j + 1 < S ? offs[sa + j + 1] : P) : 0u;
         }
-        float2 rv[kPer];
-        const float2 *rec2 = reinterpret_cast<const float2 *>(rec);
+        uint2 rv[kPer];
 #pragma unroll
-        for (int u = 0; u < kPer; ++u) {   // every rectangle load of the round issued before any is used
+        for (int u = 0; u < kPer; ++u) {   // the splats' rectangles, in depth order beside the ids
             const uint32_t j = tid + u * kSortThreads;
-            rv[u] = (j < ns && idv[u] < cap_cand) ? __ldg(rec2 + 6 * (size_t)idv[u] + 5) : make_float2(0.f, 0.f);
+            rv[u] = j < ns ? rect[sa + j] : make_uint2(0u, 0u);
         }
         __syncthreads();   // s_own cleared (the previous round's readers are done)
 #pragma unroll
@@ -538,7 +591,7 @@ __global__ void __launch_bounds__(kSortThreads) emit_pairs_kernel(
             const uint32_t o = ov[u];
             uint32_t t00 = 0, w = 1, tx = 1;
             if (idx_ok(st, id, cap_cand, 36)) {
-                const uint32_t rx = __float_as_uint(rv[u].x), ry = __float_as_uint(rv[u].y);
+                const uint32_t rx = rv[u].x, ry = rv[u].y;
                 const int x0 = rx & 0xffff, x1 = rx >> 16, y0 = ry & 0xffff, y1 = ry >> 16;
                 const int v = view_of_row(view_start, vt.V, (int)(id / (uint32_t)k));
                 // the splat's tile count from its offsets (no second read of tiles_touched)
@@ -612,7 +665,8 @@ __global__ void __launch_bounds__(256) keys_kernel(const uint32_t *__restrict__ 
 
 // ------------------------------------------------------------- host launch
 struct SortLayout {
-    size_t ids_a, ids_b, dk_a, dk_b, offs, rfirst, tk_a, tk_b, tv_b, hist, totals, sums, counts, total;
+    size_t ids_a, ids_b, dk_a, dk_b, crec, offs, rect, rfirst, tk_a, tk_b, tv_b, hist, totals, sums, counts,
+        total;
     long long max_rounds;
     int nb;
 };
@@ -634,7 +688,9 @@ static SortLayout layout(long long cap_cand, long long cap_pairs)
     L.ids_b = take(sizeof(uint32_t) * std::max<long long>(cap_cand, 1));
     L.dk_a = take(sizeof(uint32_t) * std::max<long long>(cap_cand, 1));
     L.dk_b = take(sizeof(uint32_t) * std::max<long long>(cap_cand, 1));
+    L.crec = take(sizeof(uint4) * std::max<long long>(cap_cand, 1));
     L.offs = take(sizeof(uint32_t) * std::max<long long>(cap_cand, 1));
+    L.rect = take(sizeof(uint2) * std::max<long long>(cap_cand, 1));
     L.max_rounds = std::max<long long>(cap_pairs, 0) / kEmitPairs + 2;
     L.rfirst = take(sizeof(uint32_t) * (size_t)L.max_rounds);
     L.tk_a = take(sizeof(uint32_t) * std::max<long long>(cap_pairs, 1));
@@ -695,6 +751,8 @@ int launch_bin_sort(const gs_splats *sp, int k, const int32_t *view_start, long 
     uint32_t *tk_a = (uint32_t *)(w + L.tk_a), *tk_b = (uint32_t *)(w + L.tk_b);
     uint32_t *tv_b = (uint32_t *)(w + L.tv_b), *offs = (uint32_t *)(w + L.offs);
     uint32_t *rfirst = (uint32_t *)(w + L.rfirst);
+    uint2 *rect = (uint2 *)(w + L.rect);
+    uint4 *crec = (uint4 *)(w + L.crec);
     uint32_t *hist = (uint32_t *)(w + L.hist), *totals = (uint32_t *)(w + L.totals);
     uint32_t *sums = (uint32_t *)(w + L.sums), *counts = (uint32_t *)(w + L.counts);
     const float4 *rec = reinterpret_cast<const float4 *>(sp->rec);
@@ -704,14 +762,15 @@ int launch_bin_sort(const gs_splats *sp, int k, const int32_t *view_start, long 
     // 1. compact covering splats
     count_valid_kernel<<<nb, kSortThreads, 0, s>>>(sp->tiles, view_start, vt.V, k, cap_cand, sums, st);
     scan_block_sums<<<1, 1024, 0, s>>>(sums, nb, n_splats, cap_cand, st, 3);
-    compact_valid_kernel<<<nb, kSortThreads, 0, s>>>(sp->tiles, rec, view_start, vt.V, k, cap_cand, sums,
-                                                     ids_a, dk_a, st);
+    compact_valid_kernel<<<nb, kSortThreads, 0, s>>>(sp->tiles, rec, view_start, vt.V, k, cap_cand, sums, dk_a, crec,
+                                                     ids_a, st);
     count_launches(3);
-    // 2. depth sort (32 bits)
-    uint32_t *dk_s, *ids_s;
-    radix_sort(dk_a, ids_a, dk_b, ids_b, n_splats, 32, hist, totals, nb, st, s, &dk_s, &ids_s);
-    // 3. pair emission in depth order
-    count_pairs_kernel<<<nb, kSortThreads, 0, s>>>(ids_s, n_splats, sp->tiles, sums, cap_cand, st);
+    // 2. depth sort (32 bits) of the compacted indices
+    uint32_t *dk_s, *ci_s;
+    radix_sort(dk_a, ids_a, dk_b, ids_b, n_splats, 32, hist, totals, nb, st, s, &dk_s, &ci_s);
+    // 3. pair emission in depth order (ids and rectangles gathered into it first)
+    uint32_t *ids_s = ci_s == ids_a ? ids_b : ids_a;
+    count_pairs_kernel<<<nb, kSortThreads, 0, s>>>(ci_s, n_splats, crec, ids_s, rect, sums, st);
     scan_block_sums<<<1, 1024, 0, s>>>(sums, nb, n_pairs, bins->cap_pairs, st, 3);
     int tile_bits = 1;
     while ((1ll << tile_bits) < (long long)vt.total_tiles) ++tile_bits;
@@ -719,10 +778,9 @@ int launch_bin_sort(const gs_splats *sp, int k, const int32_t *view_start, long 
     // choose the emission buffers so that the last pass lands in bins->vals
     uint32_t *ek = tk_a, *ev = (passes % 2 == 0) ? bins->vals : tv_b;
     uint32_t *ok = tk_b, *ov = (passes % 2 == 0) ? tv_b : bins->vals;
-    pair_offsets_kernel<<<nb, kSortThreads, 0, s>>>(ids_s, n_splats, sp->tiles, sums, offs, rfirst, L.max_rounds,
-                                                    cap_cand, st);
+    pair_offsets_kernel<<<nb, kSortThreads, 0, s>>>(rect, n_splats, sums, offs, rfirst, L.max_rounds, st);
     const int emit_per_sm = tuning().emit_ctas_per_sm > 0 ? std::min(tuning().emit_ctas_per_sm, 8) : 4;
-    emit_pairs_kernel<<<sm_count() * emit_per_sm, kSortThreads, 0, s>>>(ids_s, n_splats, n_pairs, offs, rfirst, rec,
+    emit_pairs_kernel<<<sm_count() * emit_per_sm, kSortThreads, 0, s>>>(ids_s, n_splats, n_pairs, offs, rfirst, rect,
                                                               view_start, k, ek, ev, vt, cap_cand, st);
     count_launches(4);
     // 4. stable sort on the tile id
