@@ -480,8 +480,178 @@ __device__ __forceinline__ void combine_tile(int t, const uint32_t *__restrict__
     if (COUNT) count_add(n_eval, nev, ncomp);
 }
 
-// One CTA per tile cut into several chunks, taken from the plan's list of
-// such tiles through a counter (CTAs that finish a short tile take the next).
+// A long multi-chunk tile (more than kLongTile chunks), one group of 32 of
+// its pixels per CTA: the chunk walk of combine_tile split over the CTA's 8
+// warps as a scan.  Chunk 0 is the exact start; chunks 1 .. nk-1 are cut into
+// 8 consecutive segments, warp w owning segment w for the group's pixels
+// (lane = pixel, so every plane access is one coalesced 128-byte row).
+//   1. each warp reduces its segment: P = the product of the chunks' own
+//      transmittances (running partial products Pk, in chunk order), Cs = sum
+//      of P(k-1) times the chunk's colour, and the last composited position;
+//   2. the entering state of segment w follows from chunk 0 and segments
+//      0 .. w-1: T_w+1 = T_w P_w, C_w+1 = C_w + T_w Cs_w;
+//   3. each warp walks its segment again: chunk k is entered with T_w P(k-1)
+//      and left with T_w P(k) -- one rounding each, the product that step 2
+//      forms at the segment's end -- so the stop (the first chunk left below
+//      1e-4) is found by exactly one warp, and the segments behind it are
+//      those entered below 1e-4.
+// The states written are those of combine_tile (entering and leaving
+// transmittance, colour prefix, last position; -1 and a fix-up mark where the
+// stop falls).
+constexpr int kLongSplit = 8;    // pixel groups (CTAs) per long tile
+constexpr int kLongAhead = 8;    // chunk states loaded per group by a segment walk
+
+template <bool COUNT>
+__device__ __forceinline__ void combine_long(int t, int grp, const uint32_t *__restrict__ ranges, const ViewTable &vt,
+                                             const RenderPlan &plan, float bg0, float bg1, float bg2,
+                                             float *__restrict__ image, float *__restrict__ T_final,
+                                             int32_t *__restrict__ last, unsigned long long *__restrict__ n_eval)
+{
+    __shared__ float s_P[kLongSplit][32], s_C[3][kLongSplit][32];
+    __shared__ int s_L[kLongSplit][32];
+    const int base = plan.item_base[t], nk = plan.item_base[t + 1] - base;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const TileCoord tc = tile_coord(vt, t, 0);
+    const int pix = grp * 32 + lane;
+    const int px = tc.x0 + (pix & (kTile - 1)), py = tc.y0 + pix / kTile;
+    const bool inside = px < vt.W[tc.v] && py < vt.H[tc.v];
+    const uint32_t s_start = ranges[2 * t], s_end = ranges[2 * t + 1];
+    const int m = nk - 1;
+    const int k0 = 1 + (w * m) / kLongSplit, k1 = 1 + ((w + 1) * m) / kLongSplit;
+    // ---- 1. segment reduction
+    {
+        float P = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+        int L = 0;
+        for (int kb = k0; kb < k1; kb += kLongAhead) {
+            float gT[kLongAhead], g0[kLongAhead], g1[kLongAhead], g2[kLongAhead];
+            int gl[kLongAhead];
+#pragma unroll
+            for (int g = 0; g < kLongAhead; ++g) {
+                gT[g] = 1.f; g0[g] = g1[g] = g2[g] = 0.f; gl[g] = 0;
+                if (kb + g < k1) {
+                    const int it = base + kb + g;
+                    gT[g] = state_plane(plan.state, it, 0)[pix];
+                    g0[g] = state_plane(plan.state, it, 2)[pix];
+                    g1[g] = state_plane(plan.state, it, 3)[pix];
+                    g2[g] = state_plane(plan.state, it, 4)[pix];
+                    gl[g] = reinterpret_cast<const int *>(state_plane(plan.state, it, 5))[pix];
+                }
+            }
+#pragma unroll
+            for (int g = 0; g < kLongAhead; ++g) {
+                if (kb + g >= k1) continue;
+                C0 = fmaf(P, g0[g], C0);
+                C1 = fmaf(P, g1[g], C1);
+                C2 = fmaf(P, g2[g], C2);
+                P = __fmul_rn(P, gT[g]);
+                if (gl[g] > 0) L = (kb + g) * plan.L + gl[g];
+            }
+        }
+        s_P[w][lane] = P;
+        s_C[0][w][lane] = C0;
+        s_C[1][w][lane] = C1;
+        s_C[2][w][lane] = C2;
+        s_L[w][lane] = L;
+    }
+    __syncthreads();
+    // ---- 2. entering state of the segment
+    float *t00 = state_plane(plan.state, base, 0);
+    const float Tp0 = t00[pix];   // chunk 0's own product (0: it stopped the pixel)
+    const bool stop0 = Tp0 == 0.f;
+    float C0 = state_plane(plan.state, base, 2)[pix];
+    float C1 = state_plane(plan.state, base, 3)[pix];
+    float C2 = state_plane(plan.state, base, 4)[pix];
+    const int l0 = reinterpret_cast<const int *>(state_plane(plan.state, base, 5))[pix];
+    int lastg = l0 > 0 ? l0 : 0;
+    float Tw = stop0 ? state_plane(plan.state, base, 1)[pix] : Tp0;
+    for (int u = 0; u < w; ++u) {
+        C0 = fmaf(Tw, s_C[0][u][lane], C0);
+        C1 = fmaf(Tw, s_C[1][u][lane], C1);
+        C2 = fmaf(Tw, s_C[2][u][lane], C2);
+        Tw = __fmul_rn(Tw, s_P[u][lane]);
+        if (s_L[u][lane] > 0) lastg = s_L[u][lane];
+    }
+    __syncthreads();   // chunk 0's planes are read by every warp before warp 0 marks it active
+    if (w == 0) t00[pix] = 1.f;   // chunk 0 is always active
+    // ---- 3. the segment's states
+    unsigned long long nev = 0, ncomp = 0;
+    bool marked = false;
+    int k = k0;
+    if (!stop0 && Tw >= kTMin) {
+        float P = 1.f;
+        bool go = true;
+        for (int kb = k0; go && kb < k1; kb += kLongAhead) {
+            float gT[kLongAhead], g0[kLongAhead], g1[kLongAhead], g2[kLongAhead];
+            int gl[kLongAhead], gc[kLongAhead];
+#pragma unroll
+            for (int g = 0; g < kLongAhead; ++g) {
+                gT[g] = 1.f; g0[g] = g1[g] = g2[g] = 0.f; gl[g] = gc[g] = 0;
+                if (kb + g < k1) {
+                    const int it = base + kb + g;
+                    gT[g] = state_plane(plan.state, it, 0)[pix];
+                    g0[g] = state_plane(plan.state, it, 2)[pix];
+                    g1[g] = state_plane(plan.state, it, 3)[pix];
+                    g2[g] = state_plane(plan.state, it, 4)[pix];
+                    gl[g] = reinterpret_cast<const int *>(state_plane(plan.state, it, 5))[pix];
+                    if (COUNT) gc[g] = reinterpret_cast<const int *>(state_plane(plan.state, it, 6))[pix];
+                }
+            }
+#pragma unroll
+            for (int g = 0; g < kLongAhead; ++g) {
+                const int kk = kb + g;
+                if (!go || kk >= k1) continue;
+                const int item = base + kk;
+                const float Tin = __fmul_rn(Tw, P);
+                const float Pn = __fmul_rn(P, gT[g]);
+                const float T1 = __fmul_rn(Tw, Pn);
+                state_plane(plan.state, item, 0)[pix] = Tin;
+                float *c0 = state_plane(plan.state, item, 2), *c1 = state_plane(plan.state, item, 3);
+                float *c2 = state_plane(plan.state, item, 4);
+                if (T1 >= kTMin) {   // no stop inside: the chunk's true contribution
+                    C0 = fmaf(Tin, g0[g], C0);
+                    C1 = fmaf(Tin, g1[g], C1);
+                    C2 = fmaf(Tin, g2[g], C2);
+                    c0[pix] = C0;
+                    c1[pix] = C1;
+                    c2[pix] = C2;
+                    state_plane(plan.state, item, 1)[pix] = T1;
+                    if (gl[g] > 0) lastg = kk * plan.L + gl[g];
+                    if (COUNT && inside) {
+                        nev += min((uint32_t)plan.L, s_end - (s_start + (uint32_t)kk * (uint32_t)plan.L));
+                        ncomp += gc[g];
+                    }
+                    P = Pn;
+                    k = kk + 1;
+                } else {             // the pixel's stop lies in chunk kk
+                    state_plane(plan.state, item, 1)[pix] = Tin;
+                    c0[pix] = C0;
+                    c1[pix] = C1;
+                    c2[pix] = C2;
+                    reinterpret_cast<int *>(state_plane(plan.state, item, 5))[pix] = -1;
+                    if (inside) {
+                        if (atomicExch(plan.fix + item, 1) == 0)
+                            plan.fix_list[atomicAdd(plan.counters + 3, 1)] = item;
+                        if (last) last[vt.pix_base[tc.v] + (long long)py * vt.W[tc.v] + px] = lastg;
+                    }
+                    marked = true;
+                    k = kk + 1;
+                    go = false;
+                }
+            }
+        }
+        // the pixel never stopped: the last segment holds its final colour
+        if (!marked && w == kLongSplit - 1 && inside)
+            write_image(vt, tc.v, px, py, C0, C1, C2, __fmul_rn(Tw, P), lastg, bg0, bg1, bg2, image, T_final, last);
+    } else if (stop0 && w == 0 && inside) {   // chunk 0 stopped the pixel: its state is final
+        write_image(vt, tc.v, px, py, C0, C1, C2, Tw, lastg, bg0, bg1, bg2, image, T_final, last);
+    }
+    for (; k < k1; ++k) state_plane(plan.state, base + k, 0)[pix] = 0.f;   // behind the stop: inactive
+    if (COUNT) count_add(n_eval, nev, ncomp);
+}
+
+// One CTA per tile cut into several chunks (per pixel group of a long one),
+// taken from the plan's list of such tiles through a counter: the long tiles'
+// units first, then the others (CTAs that finish a unit take the next).
 template <bool COUNT>
 __global__ void __launch_bounds__(2 * kRThreads) combine_kernel(const uint32_t *__restrict__ ranges, ViewTable vt,
                                                             RenderPlan plan, float bg0, float bg1, float bg2,
@@ -493,15 +663,21 @@ __global__ void __launch_bounds__(2 * kRThreads) combine_kernel(const uint32_t *
     if (has_error(st)) return;
     __shared__ int s_j;
     const int n_long = *(volatile const int32_t *)(plan.counters + 5);
-    const int n_multi = n_long + *(volatile const int32_t *)(plan.counters + 7);
+    const int n_split = kLongSplit * n_long;   // units of the long tiles, taken first
+    const int n_units = n_split + *(volatile const int32_t *)(plan.counters + 7);
     for (;;) {
-        __syncthreads();   // the previous tile's readers of s_j are done
+        __syncthreads();   // the previous unit's readers of s_j and of the shared segment states are done
         if (threadIdx.x == 0) s_j = atomicAdd(plan.counters + 6, 1);
         __syncthreads();
         const int j = s_j;
-        if (j >= n_multi) break;
-        const int t = __ldg(plan.multi_list + (j < n_long ? j : vt.total_tiles - 1 - (j - n_long)));
-        combine_tile<COUNT>(t, ranges, vt, plan, bg0, bg1, bg2, image, T_final, last, n_eval);
+        if (j >= n_units) break;
+        if (j < n_split) {
+            combine_long<COUNT>(__ldg(plan.multi_list + j / kLongSplit), j % kLongSplit, ranges, vt, plan, bg0, bg1,
+                                bg2, image, T_final, last, n_eval);
+        } else {
+            const int t = __ldg(plan.multi_list + vt.total_tiles - 1 - (j - n_split));
+            combine_tile<COUNT>(t, ranges, vt, plan, bg0, bg1, bg2, image, T_final, last, n_eval);
+        }
     }
 }
 
