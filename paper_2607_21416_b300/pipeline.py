@@ -211,8 +211,12 @@ class MappingStep:
     `step(target_host, cams_host)` is the end-to-end call: it copies the
     iteration's target images (and optionally cameras) from pinned host memory,
     replays the graph and reads back the loss and the status word (one stream
-    synchronisation).  A capacity overflow found there re-prepares the buffers
-    and repeats the iteration.
+    synchronisation).  With `next_target_host`, the next iteration's images are
+    copied into a second device buffer on a copy stream while this iteration
+    runs (the step returns once both are done; the next step then replays the
+    graph captured on that buffer), so the host-to-device copy overlaps the
+    compute; the next call must pass the same tensor, unchanged.  A capacity
+    overflow found there re-prepares the buffers and repeats the iteration.
     """
 
     def __init__(self, views: api.Views, anchors: api.Anchors, precision: int = L.GS_PREC_BF16,
@@ -225,8 +229,12 @@ class MappingStep:
                           loss=loss, lam=lam, fuse_projection=fuse_projection)
         self.rp = RenderPass(views, anchors, chunk=chunk, **self._args)
         self.target = torch.zeros(3 * views.total_pixels, device=device)
+        self._target_b = torch.zeros(3 * views.total_pixels, device=device)   # the prefetch buffer
         self.stream = torch.cuda.Stream(device=device)
+        self._copy_stream = torch.cuda.Stream(device=device)
         self.graph = None
+        self._graph_b = None   # the same iteration captured on the prefetch buffer
+        self._pending = None   # (host tensor, buffer index, event) of a prefetched target
         self.tune = bool(tune)
         self.tune_cache = tune_cache
         self.tuned = None      # the autotuner's pick and its measurements (tune=True)
@@ -281,7 +289,11 @@ class MappingStep:
             self.graph = torch.cuda.CUDAGraph()
             with torch.cuda.graph(self.graph, stream=self.stream):
                 self.rp.step(self.target)
+            self._graph_b = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self._graph_b, stream=self.stream):
+                self.rp.step(self._target_b)
             torch.cuda.synchronize()
+            self._pending = None
         finally:
             if self.tuning is not None:
                 api.set_tuning(prev)
@@ -292,25 +304,44 @@ class MappingStep:
             self.graph.replay()
         return self.rp.loss
 
-    def step(self, target_host, cams_host=None, retries=2):
+    def step(self, target_host, cams_host=None, next_target_host=None, retries=2):
         """End-to-end iteration from host inputs; returns the loss as a Python float."""
         if self.graph is None:
             self.prepare(target_host.to(self.target.device))
+        pend, self._pending = self._pending, None
         for _ in range(retries + 1):
+            buf = 0
             with torch.cuda.stream(self.stream):
-                self.target.copy_(target_host, non_blocking=True)
+                if pend is not None and pend[0] is target_host:   # copied during the previous step
+                    buf = pend[1]
+                    self.stream.wait_event(pend[2])
+                else:
+                    self.target.copy_(target_host, non_blocking=True)
                 if cams_host is not None:
                     self.views.cams.copy_(cams_host, non_blocking=True)
-                self.graph.replay()
+                (self._graph_b if buf else self.graph).replay()
                 self._loss_host.copy_(self.rp.loss[:1], non_blocking=True)
                 self._status_host.copy_(self.rp.status, non_blocking=True)
+            ev = None
+            if next_target_host is not None:
+                # the other buffer's last reader finished with the previous step (synchronised)
+                nxt = 1 - buf
+                with torch.cuda.stream(self._copy_stream):
+                    (self._target_b if nxt else self.target).copy_(next_target_host, non_blocking=True)
+                    ev = torch.cuda.Event()
+                    ev.record(self._copy_stream)
             self.stream.synchronize()
+            if ev is not None:
+                ev.synchronize()
             code = int(np.int32(int(self._status_host[0]) & 0xFFFFFFFF))
             if code == 0:
+                if ev is not None:
+                    self._pending = (next_target_host, nxt, ev)
                 return float(self._loss_host[0])
             if code != L.GS_ERR_CAPACITY:
                 raise L.GsError("mapping step", code)
             self.prepare()
+            pend = None
         raise L.GsError("mapping step: capacity", L.GS_ERR_CAPACITY)
 
     @property

@@ -135,3 +135,32 @@ def test_mapping_step_from_host_inputs_matches_render_pass():
     assert np.allclose(to_np(ms.rp.agrad.dfeat), dfeat, rtol=1e-4, atol=1e-6)
     got2 = ms.step(tgt_host)   # replay only
     assert got2 == pytest.approx(want, rel=1e-5, abs=1e-6)
+
+
+def test_mapping_step_prefetched_targets():
+    """Each step copying the next step's images into the second buffer during
+    its run: the losses are those of the images each step was given, through
+    both captured graphs, and a step given other images than the prefetched
+    ones copies its own."""
+    s = scenes.tiny_corridor(seed=0, n_anchors=4000, F=32, k=10, hidden=32)
+    views = api.Views(s.cams, s.wh)
+    A = api.Anchors.from_scene(s)
+    t0 = f32(O.targets_flat(s))
+    tgts = [torch.as_tensor(t0).pin_memory(), torch.as_tensor(f32(t0[::-1].copy())).pin_memory(),
+            torch.as_tensor(f32(0.5 * t0)).pin_memory()]
+    ref = pipeline.RenderPass(views, A, precision=L.GS_PREC_BF16, store_state=False)
+    assert ref.ensure_capacity(tgts[0].cuda()) == 0
+    want = []
+    for t in tgts:
+        ref.step(t.cuda())
+        torch.cuda.synchronize()
+        want.append(float(ref.loss.item()))
+    assert len(set(want)) == 3
+    ms = pipeline.MappingStep(views, A, precision=L.GS_PREC_BF16)
+    order = [0, 1, 2, 0, 1]
+    for i, j in enumerate(order):
+        nxt = tgts[order[i + 1]] if i + 1 < len(order) else None
+        assert ms.step(tgts[j], next_target_host=nxt) == pytest.approx(want[j], rel=1e-5, abs=1e-6)
+    # a prefetched buffer the next call does not use
+    assert ms.step(tgts[2], next_target_host=tgts[0]) == pytest.approx(want[2], rel=1e-5, abs=1e-6)
+    assert ms.step(tgts[1]) == pytest.approx(want[1], rel=1e-5, abs=1e-6)
