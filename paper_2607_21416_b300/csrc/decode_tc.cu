@@ -62,8 +62,12 @@ static TcShape tc_shape(int F, int k, int H)
     s.stage_floats = 32 * 4 * k;
     size_t b = 0;
     auto take = [&](size_t bytes) { uint32_t at = (uint32_t)b; b = align_up(b + bytes, 128); return at; };
-    s.o_U = take(2ull * kTRows * s.KP);
-    s.o_R = take(std::max<size_t>(2ull * kTRows * s.N1, 4ull * 4 * s.stage_floats));
+    // the layer-1 operand U, the hidden operand R and the output stages share one region: U is dead
+    // once the layer-1 MMA has completed, R once the layer-2 MMA has, and U is rebuilt for every
+    // partition pass (more resident CTAs: the kernel waits on global loads)
+    s.o_U = take(std::max<size_t>(std::max<size_t>(2ull * kTRows * s.KP, 2ull * kTRows * s.N1),
+                                  4ull * 4 * s.stage_floats));
+    s.o_R = s.o_U;
     s.o_W1 = take(2ull * s.N1 * s.KP);
     s.o_W2oc = take(2ull * s.Noc * 2 * H);
     s.o_W2cov = take(2ull * s.Ncov * H);
@@ -201,8 +205,9 @@ __global__ void __launch_bounds__(kTThreads) decode_tc_kernel(DecodeArgs a, TcSh
             d2 = __ldg(a.xyz + 3 * an + 2) - xc[2];
             dl = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
         }
-        {
-            // U row = [f_a, d / |d|, |d|, 0 ...] in BF16, 16-byte pieces of 8 columns
+        // U row = [f_a, d / |d|, |d|, 0 ...] in BF16, 16-byte pieces of 8 columns (rebuilt for every
+        // partition pass: its region is the hidden operand's)
+        auto build_u = [&]() {
             const float inv = 1.f / dl;
             const float *f = a.feat + (size_t)(an >= 0 ? an : 0) * s.F;
             auto put8 = [&](int kc, const float u[8]) {
@@ -247,7 +252,7 @@ __global__ void __launch_bounds__(kTThreads) decode_tc_kernel(DecodeArgs a, TcSh
                 }
                 put8(kc, u);
             }
-        }
+        };
         bool done = pm < 0;
         const int row0 = tile * kTRows + warp * 32;
         const int nval = max(0, min(32, rows - row0));
@@ -264,6 +269,7 @@ __global__ void __launch_bounds__(kTThreads) decode_tc_kernel(DecodeArgs a, TcSh
                 tc_stage_weights(s, sm, a.mlp + (size_t)p * P);
                 if (tid == 0) s_staged = p;
             }
+            build_u();   // every thread is past the previous pass's use of the region (two barriers above)
             // ---- layer 1
             tc::fence_async_smem();
             tc::fence_before_sync();
