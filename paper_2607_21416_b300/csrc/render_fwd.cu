@@ -708,11 +708,35 @@ __global__ void __launch_bounds__(256) l1_kernel(const float *__restrict__ image
     // a thread's elements increase, so its view (and the view's 1 / (3 pixels)) is carried along
     int v = 0;
     float inv = 1.f / (float)(3 * vt.pix_base[1]);
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    auto view_at = [&](long long i) {
         if (v + 1 < vt.V && 3 * vt.pix_base[v + 1] <= i) {
             while (v + 1 < vt.V && 3 * vt.pix_base[v + 1] <= i) ++v;
             inv = 1.f / (float)(3 * vt.pix_base[v + 1] - 3 * vt.pix_base[v]);
         }
+    };
+    const long long stride = (long long)gridDim.x * blockDim.x, t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long head = 0;   // elements handled four at a time (16-byte loads and stores)
+    if (((reinterpret_cast<uintptr_t>(image) | reinterpret_cast<uintptr_t>(target) |
+          reinterpret_cast<uintptr_t>(d_image)) & 15) == 0) {
+        head = n & ~3ll;
+        for (long long q = t0; 4 * q < head; q += stride) {
+            const float4 x = reinterpret_cast<const float4 *>(image)[q];
+            const float4 y = reinterpret_cast<const float4 *>(target)[q];
+            const float d[4] = {x.x - y.x, x.y - y.y, x.z - y.z, x.w - y.w};
+            float g[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                view_at(4 * q + e);
+                acc += fabsf(d[e]) * inv;
+                g[e] = d[e] > 0.f ? inv : (d[e] < 0.f ? -inv : 0.f);
+            }
+            reinterpret_cast<float4 *>(d_image)[q] = make_float4(g[0], g[1], g[2], g[3]);
+        }
+        v = 0;
+        inv = 1.f / (float)(3 * vt.pix_base[1]);
+    }
+    for (long long i = head + t0; i < n; i += stride) {
+        view_at(i);
         const float d = image[i] - target[i];
         acc += fabsf(d) * inv;
         d_image[i] = d > 0.f ? inv : (d < 0.f ? -inv : 0.f);
