@@ -565,8 +565,8 @@ __global__ void __launch_bounds__(kSortThreads) emit_pairs_kernel(
             ns = min(sc - sa + 1, (uint32_t)kEmitPairs);   // 2049 only if the last starts at p1
         else if (tid == 0)
             idx_ok(st, (long long)sc - (long long)sa, -1, 39);
-        own4[2 * tid] = make_uint4(0u, 0u, 0u, 0u);
-        own4[2 * tid + 1] = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int q = 0; q < kPer / 4; ++q) own4[kPer / 4 * tid + q] = make_uint4(0u, 0u, 0u, 0u);
         uint32_t idv[kPer], ov[kPer], oe[kPer];
 #pragma unroll
         for (int u = 0; u < kPer; ++u) {
@@ -613,17 +613,22 @@ __global__ void __launch_bounds__(kSortThreads) emit_pairs_kernel(
             s_own[at] = j;
         }
         __syncthreads();
-        {   // fill forward: thread t owns positions 8t .. 8t + 7
-            const uint4 lo = own4[2 * tid], hi = own4[2 * tid + 1];
-            uint32_t v[kPer] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+        {   // fill forward: thread t owns positions kPer t .. kPer t + kPer - 1
+            uint32_t v[kPer];
+#pragma unroll
+            for (int q = 0; q < kPer / 4; ++q) {
+                const uint4 x = own4[kPer / 4 * tid + q];
+                v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+            }
             uint32_t m = 0;
 #pragma unroll
             for (int u = 0; u < kPer; ++u) { m = max(m, v[u]); v[u] = m; }
             const uint32_t pre = scanmax256_excl(m, s_warp);
 #pragma unroll
             for (int u = 0; u < kPer; ++u) v[u] = max(v[u], pre);
-            own4[2 * tid] = make_uint4(v[0], v[1], v[2], v[3]);
-            own4[2 * tid + 1] = make_uint4(v[4], v[5], v[6], v[7]);
+#pragma unroll
+            for (int q = 0; q < kPer / 4; ++q)
+                own4[kPer / 4 * tid + q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
         }
         __syncthreads();
         for (uint32_t i = tid; ns > 0 && p0 + i < p1; i += kSortThreads) {
