@@ -439,3 +439,24 @@ def test_invalid_arguments_are_rejected_on_the_host():
     assert e.value.code == L.GS_ERR_INVALID_ARG
     with pytest.raises(ValueError):
         api.Views(np.zeros((0, 16)), np.zeros((0, 2)))
+
+
+def test_l1_ragged_views_match_oracle():
+    """Eq. 3's L1 term over views whose element counts are not multiples of
+    four (view boundaries inside the kernel's 16-byte groups) and an odd
+    total, against the oracle; the gradient is sign(d) / (3 H W) exactly."""
+    wh = np.array([[29, 31], [16, 16], [7, 5]], np.int32)
+    rng = np.random.default_rng(12)
+    n = int(3 * (wh[:, 0] * wh[:, 1]).sum())
+    x = rng.uniform(0, 1, n).astype(np.float32)
+    y = rng.uniform(0, 1, n).astype(np.float32)
+    y[::17] = x[::17]   # some exact zeros of the difference
+    cams = np.stack([scenes.camera(30.0, 30.0, 14.5, 15.5, (0.0, 0.0, 0.0))] * 3)
+    vw = api.Views(cams, wh)
+    loss = torch.zeros(1, device="cuda")
+    d = torch.zeros(n, device="cuda")
+    api.l1_loss(torch.as_tensor(x).cuda(), torch.as_tensor(y).cuda(), vw, loss, d)
+    torch.cuda.synchronize()
+    want_loss, want_d = O.l1(wh, x.astype(np.float64), y.astype(np.float64))
+    assert float(loss[0]) == pytest.approx(float(want_loss), rel=1e-5)
+    assert np.array_equal(to_np(d), f32(want_d))
