@@ -460,3 +460,20 @@ def test_l1_ragged_views_match_oracle():
     want_loss, want_d = O.l1(wh, x.astype(np.float64), y.astype(np.float64))
     assert float(loss[0]) == pytest.approx(float(want_loss), rel=1e-5)
     assert np.array_equal(to_np(d), f32(want_d))
+
+
+def test_bin_sort_bit_exact_three_tile_passes():
+    """More than 2^16 tiles (40 views of 1241x376: 74,880 tiles), so the tile
+    sort takes three 8-bit passes and the ranges come from the third."""
+    V, n = 40, 1500
+    s = scenes.explicit_frustum(seed=23, n=n, width=1241, height=376, fx=718.0, fy=718.0, cx=620.5, cy=188.0)
+    s.scale *= 0.1
+    s.cams = np.repeat(s.cams, V, axis=0)
+    s.wh = np.repeat(s.wh, V, axis=0)
+    for name in ("mu", "scale", "quat", "opacity", "colour"):
+        setattr(s, name, np.tile(getattr(s, name), (V, 1)) if getattr(s, name).ndim == 2
+                else np.tile(getattr(s, name), V))
+    vs = np.arange(V + 1, dtype=np.int64) * n
+    prj = O.project(s.mu, s.scale, s.quat, s.opacity, s.cams, s.wh, vs)
+    assert api.Views(s.cams, s.wh).total_tiles > (1 << 16)
+    _bin_sort_case(s, vs, 1, prj, s.opacity, s.colour)
